@@ -1,0 +1,104 @@
+"""Seeded synthetic inputs for the asynchrony-tolerant finite-difference workloads.
+
+This module holds no arithmetic of the method: it only draws the random initial-condition
+parameters (amplitudes A ~ U(0.5, 1), phases phi ~ U(0, 2 pi), Sec. 5.1 Eq. "IC"), encodes a delay
+probability vector {p_0..p_{L-1}} (Sec. 5.1) as integer bin thresholds, and names the workloads.
+Both the CUDA path and the oracle receive these values as inputs.
+
+Workloads (the paper's experiments use synthetic multi-sine fields only, so these are the inputs
+themselves, not stand-ins for a dataset):
+  1d_n256      1D, N=256,  8 PEs,    CD2 + (1,2,2)b/(2,2,2)b, L=3, 2000 steps
+  1d_n16m      1D, N=2^24, 4096 PEs, CD4 + (1,4,2)/(2,4,2),   L=4, 1000 steps
+  3d_512       3D, 512^3, 8x8x8 PEs,  order 2 or 4, L=3, 500 steps
+  ensemble     1024 1D realizations, N_r in {2^10..2^16}, P_r=N_r/64, L_r in {2,3,4}, 5000 steps
+  adjoint_256  3D 256^3, 4x4x4 PEs, order 4, L=3, 2000 steps
+"""
+from __future__ import annotations
+
+import math
+import numpy as np
+
+SYNC, ASYNC_STD, AT = 0, 1, 2
+TWO_PI = 2.0 * math.pi
+
+
+def ic_params(seed: int, dim: int, kappas) -> dict:
+    """Amplitudes and phases for Eq. "IC" on every axis (same wavenumbers per axis)."""
+    rng = np.random.default_rng(np.random.SeedSequence([int(seed), 0x1C]))
+    kap = np.asarray(list(kappas), dtype=np.int32)
+    m = kap.size
+    amp = rng.uniform(0.5, 1.0, size=(dim, m))
+    phase = rng.uniform(0.0, TWO_PI, size=(dim, m))
+    return {"nmodes": int(m), "amp": amp, "phase": phase, "kappa": np.tile(kap, (dim, 1))}
+
+
+def thresholds_from_probs(p) -> np.ndarray:
+    """Cumulative bin edges of {p_0..p_{L-1}} on the 32-bit uniform word: t_m = round(2^32 sum_{i<=m} p_i),
+    m = 0..L-2 (the last edge is 2^32 and is implicit)."""
+    p = np.asarray(p, dtype=np.float64)
+    if p.ndim != 1 or p.size < 1 or np.any(p < 0) or abs(p.sum() - 1.0) > 1e-12:
+        raise ValueError("probabilities must be non-negative and sum to 1")
+    cum = np.cumsum(p)[:-1]
+    return np.array([min(int(round(v * 2.0 ** 32)), 2 ** 32) for v in cum], dtype=np.uint64)
+
+
+def make(dim, n, pe, order, L, scheme, c, alpha, dt, seed, kappas, probs=None, ic_seed=None) -> dict:
+    spec = {"dim": dim, "n": list(n), "pe": list(pe), "order": order, "L": L, "scheme": scheme,
+            "c": list(c), "alpha": float(alpha), "dt": float(dt), "seed": int(seed),
+            "thresholds": None if probs is None else thresholds_from_probs(probs)}
+    spec.update(ic_params(seed if ic_seed is None else ic_seed, dim, kappas))
+    return spec
+
+
+def dx_of(n: int) -> float:
+    return TWO_PI / n
+
+
+def wl_1d(n, P, order, L, steps, seed, kappas, scheme=AT, c=1.0, alpha=0.1, r_alpha=0.1, probs=None):
+    dt = r_alpha * dx_of(n) ** 2 / alpha
+    return make(1, [n], [P], order, L, scheme, [c], alpha, dt, seed, kappas, probs), steps
+
+
+def wl_3d(n, P, order, L, steps, seed, scheme=AT, c=(1.0, 1.0, 1.0), alpha=0.05, dt=None, kappas=(1, 2, 3)):
+    nn = list(n) if hasattr(n, "__len__") else [n, n, n]
+    pp = list(P) if hasattr(P, "__len__") else [P, P, P]
+    if dt is None:
+        dt = 2.0 * dx_of(min(nn)) ** 2  # r_alpha = alpha dt / dx^2 = 0.1 per axis at alpha = 0.05
+    return make(3, nn, pp, order, L, scheme, list(c), alpha, dt, seed, kappas), steps
+
+
+def workload(name: str, scheme: int = AT):
+    """(spec, nsteps) of a named workload."""
+    if name == "1d_n256":
+        return wl_1d(256, 8, 2, 3, 2000, 1, range(1, 5), scheme)
+    if name == "1d_n16m":
+        return wl_1d(1 << 24, 4096, 4, 4, 1000, 2, range(1, 11), scheme)
+    if name == "3d_512_o2":
+        return wl_3d(512, 8, 2, 3, 500, 3, scheme)
+    if name == "3d_512_o4":
+        return wl_3d(512, 8, 4, 3, 500, 3, scheme)
+    if name == "adjoint_256":
+        return adjoint_spec(256, 4, 2000)
+    raise KeyError(name)
+
+
+def adjoint_spec(n=256, P=4, steps=2000, alpha=0.05, alpha_target=0.06, seed=5):
+    """3D order-4 AT problem of the adjoint workload; dt is fixed by r_alpha = 0.1 at alpha_target."""
+    dt = 0.1 * dx_of(n) ** 2 / alpha_target
+    spec, _ = wl_3d(n, P, 4, 3, steps, seed, AT, alpha=alpha, dt=dt)
+    return spec, steps
+
+
+def ensemble_members(count=1024, base_seed=1000, log2n=(10, 16), P_width=64, Ls=(2, 3, 4), order=4,
+                     steps=5000, kappas=range(1, 5), draw_seed=4):
+    """The realizations of the batched ensemble: N_r drawn from {2^lo..2^hi}, L_r from Ls,
+    seed_r = base_seed + r, each with its own initial-condition phases."""
+    rng = np.random.default_rng(np.random.SeedSequence([draw_seed, 0xE5]))
+    lo, hi = log2n
+    out = []
+    for r in range(count):
+        n = 1 << int(rng.integers(lo, hi + 1))
+        L = int(rng.choice(np.asarray(Ls)))
+        spec, _ = wl_1d(n, n // P_width, order, L, steps, base_seed + r, kappas)
+        out.append(spec)
+    return out, steps
