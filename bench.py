@@ -1,0 +1,298 @@
+#!/usr/bin/env python
+"""Throughput of the asynchrony-tolerant (AT) forward step on GB300: grid-point updates/s in FP64.
+
+Workload (default): 1D u_t + u_x = 0.1 u_xx on [0, 2 pi), N = 2^24 points in 4096 emulated PEs,
+4th-order central differences inside, (1,4,2)/(2,4,2) AT stencils at PE edges, L = 4 uniform delays,
+10-mode multi-sine initial condition, 1000 forward-Euler steps.  One bench step = one whole run:
+initial condition, 1000 fused steps (delay draw + halo extrapolation + stencil + Euler update in one
+kernel per step) and the error statistics against the analytic solution.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs one independent replica per rank (the emulated PEs live on one GPU; there is no data
+exchange between GPUs), so scaling is weak.  --impl reference times the FP64 CPU oracle on the host
+cores instead (rank 0 only).  One JSON line is printed by rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "grid-point updates/s (FP64)"
+PEAK_FP64_FLOPS = 152 * 2 * 2 * 2.07e9  # 152 SMs x 2 FP64 FMA lanes/clk x 2 flop x 2.07 GHz max clock
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def flops_per_update(spec) -> int:
+    """FP64 flops of the merged stencil per interior point: 1 multiply + 2*h*dim FMAs (2 flops each)."""
+    h = spec["order"] // 2
+    return 1 + 2 * (2 * h * spec["dim"])
+
+
+def cpu_sample(spec, nsteps: int, threads: int) -> float:
+    """Oracle updates/s on `nsteps` steps of the full-size grid, initial condition excluded."""
+    import oracle
+    cfg = oracle.Config(spec)
+    t0 = time.perf_counter()
+    oracle.run(cfg, 0, want_log=False, threads=threads)
+    t_ic = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.run(cfg, nsteps, want_log=False, threads=threads)
+    t = time.perf_counter() - t0 - t_ic
+    return cfg.ntot * nsteps / max(t, 1e-9)
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    spec, total_steps = W.workload(args.workload)
+    cores = os.cpu_count() or 1
+    sample_steps = args.ref_sample_steps
+    for _ in range(args.warmup):
+        cpu_sample(spec, 1, cores)
+    vals = [cpu_sample(spec, sample_steps, cores) for _ in range(args.steps)]
+    v = statistics.median(vals)
+    ntot = 1
+    for x in spec["n"]:
+        ntot *= x
+    ms = ntot * total_steps / v * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "points": ntot, "time_steps": total_steps},
+            "cpu_baseline": {"value": v, "unit": "updates/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{sample_steps} steps of the full {ntot}-point grid per bench step, "
+                                       f"initial condition excluded, OpenMP over points"},
+            "e2e": {"value": v, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="1d_n16m")
+    ap.add_argument("--ref-sample-steps", type=int, default=10)
+    ap.add_argument("--cpu-sample-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--time-steps", type=int, default=None, help="override the steps per run (profiling only)")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1702_00496_gb300 import Solver
+
+    spec, T = W.workload(args.workload)
+    if args.time_steps is not None:
+        T = args.time_steps
+    spec["seed"] = int(spec["seed"]) + rank  # independent replica per rank
+    ntot = 1
+    for x in spec["n"]:
+        ntot *= x
+    stream = torch.cuda.current_stream()
+    solver = Solver(spec, log_steps=0, device=f"cuda:{local}", stream=stream)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device=f"cuda:{local}")  # 512 MiB > L2
+    kern_ev = []
+
+    def one_step(record=False):
+        flush.zero_()
+        solver.reset()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solver.step(T)
+        e1.record(stream)
+        st = solver.error_stats()  # blocks
+        if record:
+            kern_ev.append((e0, e1))
+        return st
+
+    for _ in range(args.warmup):
+        one_step()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    barrier()
+    sampler.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    last = None
+    for _ in range(args.steps):
+        last = one_step(record=True)
+    t_end.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    ms = t_start.elapsed_time(t_end) / args.steps
+    kern_ms = sum(a.elapsed_time(b) for a, b in kern_ev) / (args.steps * T)
+    if world > 1:
+        tt = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{local}")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * ntot * T / (ms / 1e3)
+
+    # end to end through the public API: pinned host field in, final field and statistics out
+    solver.reset()
+    torch.cuda.synchronize()
+    u0_host = torch.empty(ntot, dtype=torch.float64, pin_memory=True)
+    u0_host.copy_(solver.field().reshape(-1))
+    out_host = torch.empty(ntot, dtype=torch.float64, pin_memory=True)
+    u0_dev = torch.empty(ntot, dtype=torch.float64, device=f"cuda:{local}")
+    e2e_steps = max(1, min(args.steps, 3))
+
+    def e2e_step():
+        flush.zero_()
+        u0_dev.copy_(u0_host, non_blocking=True)
+        solver.reset(u0_dev)
+        solver.step(T)
+        st = solver.error_stats()
+        out_host.copy_(solver.field().reshape(-1), non_blocking=True)
+        torch.cuda.synchronize()
+        return st
+
+    e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device=f"cuda:{local}")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e_value = world * ntot * T / e2e_s
+
+    peaks = measured_peaks()
+    flops_launch = flops_per_update(spec) * ntot
+    achieved = flops_launch / (kern_ms / 1e3)
+    bytes_launch = 16 * ntot  # read U^n, write U^{n+1}; halo reads of old levels add < 0.2 % at S = 4096
+    hbm = peaks.get("hbm_gbs")
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": PEAK_FP64_FLOPS / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / PEAK_FP64_FLOPS, "traffic": None,
+                "kernel": "forward_step_kernel<1,2>", "launch_ms": kern_ms,
+                "peak_source": "152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
+                "hbm_gbs": bytes_launch / (kern_ms / 1e3) / 1e9,
+                "hbm_frac_of_measured": (bytes_launch / (kern_ms / 1e3) / 1e9 / hbm) if hbm else None}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        v = cpu_sample(spec, args.cpu_sample_steps, cores)
+        cpu = {"value": v, "unit": "updates/s", "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_sample_steps} steps of the full {ntot}-point grid, initial condition excluded, "
+                         f"OpenMP over points"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload, "points": ntot, "pes": spec["pe"][0], "order": spec["order"],
+                           "L": spec["L"], "time_steps_per_step": T, "l2": "flushed (512 MiB write) each step",
+                           "replicas": world},
+                "e2e": {"value": e2e_value, "unit": "updates/s", "h2d_bytes_per_step": 8 * ntot,
+                        "d2h_bytes_per_step": 8 * ntot + 8 * 9},
+                "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+                "gpu_launches": args.steps * (T + 3),
+                "final_rms_error": last["rms"]}
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

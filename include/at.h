@@ -1,0 +1,168 @@
+/*
+ * at.h -- C ABI of the GB300 (sm_103a) implementation of the asynchrony-tolerant (AT)
+ * finite-difference method of Aditya & Donzis (arXiv:1702.00496).
+ *
+ * The hot path is the explicit forward-Euler step (Sec. 4.1, Eq. "time_disc" with one level) of
+ *     u_t + c . grad u = alpha lap u
+ * on a periodic box [0, 2 pi)^dim (Sec. 5.1), split into emulated processing elements (PEs,
+ * Sec. 2).  Interior points use central differences (Eq. "general_deriv_cds"); points within the
+ * stencil half-width of a PE boundary use AT stencils (Tables "atschemes-left/right"), which read
+ * the neighbouring PE's values at delayed time levels n-k, n-k-1, ... with k drawn per PE side per
+ * step (Sec. 5.1, "simulate delays").
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns an int status: AT_OK (0) or a negative AT_ERR_* code.  Nothing throws,
+ *     aborts or traps; at_last_error() gives a one-line message for the calling thread.
+ *   - Pointers named *_dev are CUDA device pointers, owned by the caller (e.g. torch tensors); the
+ *     library borrows them for the lifetime of the handle.  Pointers named *_host are host memory.
+ *   - Fields are FP64, row-major with x fastest: index (z*ny + y)*nx + x.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Work is enqueued
+ *     asynchronously unless the function says it blocks.
+ *   - A handle may be used by one host thread at a time.
+ */
+#ifndef ATFD_AT_H
+#define ATFD_AT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AT_OK 0
+#define AT_ERR_ARG (-1)          /* invalid argument, detected on the host before any launch */
+#define AT_ERR_SINGULAR (-2)     /* Sec. 3.2: rank(A) = rank(A|b) < N_A -- infinitely many schemes */
+#define AT_ERR_INCONSISTENT (-3) /* Sec. 3.2: rank(A) != rank(A|b) -- the stencil gives no scheme */
+#define AT_ERR_CUDA (-4)         /* a CUDA runtime call failed */
+#define AT_ERR_TIMEOUT (-5)      /* a bounded device wait ran out */
+#define AT_ERR_NONFINITE (-6)    /* a statistic came out NaN or Inf */
+#define AT_ERR_BOUNDS (-7)       /* a device-side index check failed */
+#define AT_ERR_STATE (-8)        /* call out of order, e.g. more steps than the delay log holds */
+
+/* Spatial scheme at PE boundaries. */
+#define AT_SYNC 0      /* every delay is 0: standard central differences everywhere (Eq. "general_deriv") */
+#define AT_ASYNC_STD 1 /* central differences read at the delayed level n-k (Eq. "general_deriv_async") */
+#define AT_AT 2        /* asynchrony-tolerant, time-expanded stencils ((1,2,2)b/(2,2,2)b, (1,4,2)/(2,4,2)) */
+
+/* ------------------------------------------------------------------ scheme coefficients */
+typedef struct {
+  int32_t deriv;  /* d: 1 or 2 */
+  int32_t order;  /* a: 2 or 4 (spatial order of accuracy) */
+  int32_t L;      /* delays take values 0..L-1, L <= 8 */
+  int32_t h;      /* half-width of the central stencil, a/2 */
+  int32_t T;      /* successive delayed levels read at a buffer point, 1 + #{q >= 1 : 2q < d + a} */
+  double cd[9];   /* per-point central weights for offsets j=-h..h at cd[j+h], in units of 1/dx^d */
+  int64_t cd_num[9], cd_den;   /* the same weights as exact fractions cd_num[j+h] / cd_den */
+  double phi[5];  /* stage-1 weights phi_0..phi_h on (u_{i+j} + (-1)^d u_{i-j}), Eq. "general_deriv_cds" */
+  double w[8][4]; /* stage-2 weights w[k][m] of the copy read at level n-k-m, m < T (Example 3) */
+  int64_t w_num[8][4], w_den[8]; /* w[k][m] = w_num[k][m] / w_den[k] exactly */
+} at_coeffs_t;
+
+/* Derive the AT scheme of derivative `deriv` and order `order` for delays 0..L-1 by the two-stage
+ * procedure of Sec. 3.3 (Example 3): stage 1 solves the symmetric-pair system of Eq. "general_deriv_cds"
+ * for the central weights, stage 2 solves, for each k, the time-level system that cancels the
+ * asynchronous Taylor terms u^(p,q), q >= 1, p + 2q < d + a (Eq. "cond", dt ~ dx^2).  Both systems are
+ * solved in exact rational arithmetic with the rank tests of Sec. 3.2, and the expanded coefficients
+ * are re-checked against every condition of Eq. "cond".  Host only; no CUDA call.
+ * Errors: AT_ERR_ARG (deriv not 1/2, order not 2/4, L outside 1..8, out NULL), AT_ERR_SINGULAR,
+ * AT_ERR_INCONSISTENT. */
+int at_coeffs(int32_t deriv, int32_t order, int32_t L, at_coeffs_t *out);
+
+/* Expanded taps c~_{j,l} (Eq. "general_deriv_at2") of derivative `deriv` at a point `pos` cells in
+ * from a PE edge (pos = 0 is the edge point) on side `side` (0: buffer points on the left, 1: on the
+ * right), for scheme AT_SYNC / AT_ASYNC_STD / AT_AT and effective delay k.  Coefficients are in units
+ * of 1/dx^d, taps with equal (j, l) merged.  Writes at most `cap` taps (j_out, l_out, c_out) and
+ * stores their number in *ntaps.  Host only.  Errors: AT_ERR_ARG. */
+int at_stencil_taps(int32_t deriv, int32_t order, int32_t scheme, int32_t k, int32_t pos, int32_t side,
+                    int32_t cap, int32_t *j_out, int32_t *l_out, double *c_out, int32_t *ntaps);
+
+/* The general single-system derivation of Sec. 3.1-3.2: impose Eq. "cond" (rows p + r q < d + a) on the
+ * stencil {(j_i, l_i)}, i < npts (point i+j read at level n-l), and solve A c = b exactly.
+ * On AT_OK, num_out[i]/den_out[i] and c_out[i] hold the unique coefficients (units 1/dx^d, dt = dx^r
+ * taken as 1 in the row scaling).  *rank_out receives rank(A) in every case.
+ * Errors: AT_ERR_ARG (npts outside 1..32, bad d/a/r), AT_ERR_SINGULAR (consistent, rank deficient),
+ * AT_ERR_INCONSISTENT (rank(A) != rank(A|b)).  Host only. */
+int at_solve_stencil(int32_t deriv, int32_t order, int32_t r, int32_t npts, const int32_t *j, const int32_t *l,
+                     int64_t *num_out, int64_t *den_out, double *c_out, int32_t *rank_out);
+
+/* ------------------------------------------------------------------ delay process */
+/* Raw delay of PE side `side` at step `step` (Sec. 5.1): the first word x0 of Philox4x32-10 with
+ * counter (step, side, 0, 0) and key (seed_lo, seed_hi) is binned -- uniformly, k = floor(x0 L / 2^32),
+ * when thresholds_host is NULL, else k = #{m < L-1 : thresholds_host[m] <= x0}.  Host-side copy of the
+ * generator the kernels run, for replay and tests.  Returns k >= 0, or AT_ERR_ARG. */
+int at_delay(uint64_t seed, int64_t step, int64_t side, int32_t L, const uint64_t *thresholds_host);
+
+/* ------------------------------------------------------------------ problem and handle */
+typedef struct {
+  int32_t dim;     /* 1 or 3 */
+  int32_t order;   /* 2 or 4 */
+  int32_t L;       /* delays 0..L-1, 1 <= L <= 8 */
+  int32_t scheme;  /* AT_SYNC, AT_ASYNC_STD or AT_AT */
+  int64_t n[3];    /* points per axis (axes beyond dim hold 1) */
+  int32_t pe[3];   /* PEs per axis; n[a] % pe[a] == 0 and n[a]/pe[a] >= order.  pe[a] == 1: no boundary */
+  int32_t nmodes;  /* initial-condition modes per axis, 1..16 */
+  double c[3];     /* advection speed per axis */
+  double alpha;    /* diffusivity */
+  double dt;       /* time step */
+  uint64_t seed;   /* delay-process key */
+  const uint64_t *thresholds; /* host, L-1 ascending values in [0, 2^32], or NULL for uniform delays */
+  const double *amp;          /* host [dim][nmodes]: A in Eq. "IC" */
+  const double *phase;        /* host [dim][nmodes]: phi in Eq. "IC" */
+  const int32_t *kappa;       /* host [dim][nmodes]: wavenumbers in Eq. "IC" */
+} at_config_t;
+
+typedef struct at_handle at_handle_t;
+
+/* Ring-buffer depth R = L + T (T from at_coeffs for this order and scheme; 1 for SYNC/ASYNC_STD) and
+ * the number of PE sides 2*dim*prod(pe).  Host only.  Errors: AT_ERR_ARG. */
+int at_ring_slots(const at_config_t *cfg, int32_t *R);
+int at_num_sides(const at_config_t *cfg, int64_t *sides);
+
+/* Create a solver on caller-owned device memory and write U^0 (Eq. "IC"; the 3D field is the product
+ * of per-axis sums) into ring slot 0.
+ *   ring_dev : R * n0*n1*n2 doubles (R from at_ring_slots); level m lives in slot m mod R.
+ *   log_dev  : log_steps * sides bytes, may be NULL when log_steps == 0; receives the raw delay of
+ *              every PE side at every step (step-major), so each run can be replayed and audited.
+ * The handle copies cfg and its host arrays and allocates a small scratch block for reductions.
+ * Errors: AT_ERR_ARG, AT_ERR_CUDA. */
+int at_init(const at_config_t *cfg, double *ring_dev, int64_t ring_len, uint8_t *log_dev, int64_t log_steps,
+            void *stream, at_handle_t **out);
+
+/* Advance nsteps forward-Euler steps (the hot path).  Each step draws the delays of every PE side,
+ * extrapolates the halo each side reads from the delayed ring slots, and applies the fused stencil.
+ * Enqueued on the handle's stream; returns without waiting.  Errors: AT_ERR_ARG, AT_ERR_STATE (the
+ * delay log would overflow), AT_ERR_CUDA. */
+int at_step(at_handle_t *hd, int64_t nsteps);
+
+/* Restart at step 0: write U^0 into ring slot 0 -- Eq. "IC" when u0_dev is NULL, else a copy of the
+ * caller's field u0_dev (n0*n1*n2 doubles, device) -- and rewind the step counter.  The delay process
+ * replays from step 0.  Enqueued on the handle's stream.  Errors: AT_ERR_ARG, AT_ERR_CUDA. */
+int at_reset(at_handle_t *hd, const double *u0_dev);
+
+/* Wait for the handle's stream and return its sticky device status (AT_OK, AT_ERR_BOUNDS, ...). Blocks. */
+int at_sync(at_handle_t *hd);
+
+/* Current step n and a device pointer to U^n inside the ring (valid until the next at_step). */
+int at_state(at_handle_t *hd, int64_t *step, double **field_dev);
+
+/* Sec. 4 / Sec. 5.1 error measures of E = U^n - u_a(x, n dt), where u_a is Eq. "ana_sol" read as
+ * sum A exp(-alpha kappa^2 t) sin(kappa (x - c t) + phi) (3D: product over axes).  rms is over all
+ * points, rms_I / rms_B over the interior set I_I and the PE-boundary set I_B (points within h of a
+ * boundary of a split axis).  Deterministic two-pass reduction.  Blocks.  Errors: AT_ERR_CUDA,
+ * AT_ERR_NONFINITE. */
+typedef struct {
+  double rms, max_abs, mean_abs, mean, rms_I, rms_B, ua_rms;
+  int64_t n_I, n_B, step;
+} at_stats_t;
+int at_error_stats(at_handle_t *hd, at_stats_t *out);
+
+/* Release the handle's scratch.  The caller's ring and log are untouched. */
+int at_destroy(at_handle_t *hd);
+
+/* One-line description of the last error on this thread ("" if none). */
+const char *at_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ATFD_AT_H */

@@ -86,6 +86,7 @@ def lib():
         L.orc_adjoint.argtypes = [C.POINTER(OrcCfg), C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
                                   C.POINTER(C.c_double)]
         L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_delay_log.argtypes = [C.POINTER(OrcCfg), C.c_int64, C.c_void_p]
         _lib = L
     return _lib
 
@@ -201,6 +202,14 @@ def run(cfg: Config, nsteps: int, want_log: bool = True, want_history: bool = Fa
         raise RuntimeError(f"orc_run failed ({rc})")
     return (u.reshape(cfg.shape), log,
             None if hist is None else hist.reshape((nsteps + 1,) + cfg.shape))
+
+
+def delay_log(cfg: Config, nsteps: int) -> np.ndarray:
+    """Raw delays [nsteps, sides] uint8 of the run, without the field computation."""
+    log = np.zeros((nsteps, cfg.num_sides), dtype=np.uint8)
+    if lib().orc_delay_log(C.byref(cfg.s), int(nsteps), log.ctypes.data) != 0:
+        raise RuntimeError("orc_delay_log failed")
+    return log
 
 
 STAT_NAMES = ("rms", "max_abs", "mean_abs", "mean", "rms_I", "rms_B", "ua_rms", "n_I", "n_B")

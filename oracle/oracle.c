@@ -333,13 +333,12 @@ static double eval_taps(const orc_cfg *g, const double *const *lev, int64_t x, i
  * lev[m] = U^{n-m} (m = 0.. as deep as the delays need), keff = effective delay of every PE side. */
 int orc_step(const orc_cfg *g, const double *const *lev, const int32_t *keff, double *out) {
   if (orc_check(g)) return -1;
-  const int64_t nx = g->n[0], ny = g->n[1], nz = g->n[2];
+  const int64_t nx = g->n[0], ny = g->n[1], N = ntot(g);
 #ifdef _OPENMP
-#pragma omp parallel for collapse(2) schedule(static) num_threads(g_threads)
+#pragma omp parallel for schedule(static) num_threads(g_threads)
 #endif
-  for (int64_t z = 0; z < nz; ++z)
-    for (int64_t y = 0; y < ny; ++y)
-      for (int64_t x = 0; x < nx; ++x) {
+  for (int64_t pt = 0; pt < N; ++pt) {
+        const int64_t x = pt % nx, y = (pt / nx) % ny, z = pt / (nx * ny);
         orc_tap taps[16];
         double f = 0.0;
         for (int a = 0; a < g->dim; ++a) {
@@ -349,9 +348,8 @@ int orc_step(const orc_cfg *g, const double *const *lev, const int32_t *keff, do
           double d2 = eval_taps(g, lev, x, y, z, a, taps, nt2);
           f = f + (-g->c[a] * d1 + g->alpha * d2);
         }
-        int64_t i = (z * ny + y) * nx + x;
-        out[i] = lev[0][i] + g->dt * f;
-      }
+        out[pt] = lev[0][pt] + g->dt * f;
+  }
   return 0;
 }
 
@@ -363,6 +361,18 @@ static void draw_delays(const orc_cfg *g, int64_t n, int T, uint8_t *raw_out, in
     if (raw_out) raw_out[b] = (uint8_t)k;
     keff[b] = orc_delay_effective(k, n, T);
   }
+}
+
+/* Raw delays of steps 0..nsteps-1 for every PE side (step-major), without running the solver. */
+int orc_delay_log(const orc_cfg *g, int64_t nsteps, uint8_t *log) {
+  if (orc_check(g) || nsteps < 0) return -1;
+  const int64_t nb = orc_num_sides(g);
+  const int T = orc_time_width(g->order, g->scheme);
+  int32_t *keff = (int32_t *)malloc(sizeof(int32_t) * (size_t)nb);
+  if (!keff) return -2;
+  for (int64_t n = 0; n < nsteps; ++n) draw_delays(g, n, T, log + n * nb, keff);
+  free(keff);
+  return 0;
 }
 
 /* Full run: initial condition (Eq. "IC", or u0 when given), then nsteps steps.  u_out receives U^{nsteps}.  delay_log (optional)

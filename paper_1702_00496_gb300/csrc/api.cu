@@ -1,0 +1,265 @@
+// api.cu -- the solver handle of the C ABI (include/at.h): configuration checks, merged stencil
+// coefficients, ring-buffer bookkeeping, step driver and error statistics.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/at.h"
+#include "internal.h"
+#include "philox.cuh"
+
+struct at_handle {
+  at_config_t cfg;
+  std::vector<uint64_t> thr;
+  StepParams sp;
+  WaveParams wp;
+  int64_t log_steps = 0;
+  int64_t step = 0;
+  cudaStream_t stream = nullptr;
+  // scratch owned by the handle: status word, reduction partials and result, 3D axis tables
+  void *scratch = nullptr;
+  int32_t *d_status = nullptr;
+  double *d_partials = nullptr;
+  double *d_result = nullptr;
+  double *d_tables = nullptr;
+};
+
+namespace {
+
+const double kTwoPi = 6.283185307179586476925286766559005768;
+
+int fail(int code, const char *msg) {
+  at_internal_set_error(msg);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where) {
+  char buf[200];
+  std::snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+  at_internal_set_error(buf);
+  return AT_ERR_CUDA;
+}
+
+int time_width(const at_config_t *c) { return c->scheme == AT_AT ? c->order / 2 + 1 : 1; }
+
+int check_config(const at_config_t *c) {
+  if (!c) return fail(AT_ERR_ARG, "config is NULL");
+  if (c->dim != 1 && c->dim != 3) return fail(AT_ERR_ARG, "dim must be 1 or 3");
+  if (c->order != 2 && c->order != 4) return fail(AT_ERR_ARG, "order must be 2 or 4");
+  if (c->scheme < AT_SYNC || c->scheme > AT_AT) return fail(AT_ERR_ARG, "scheme must be AT_SYNC, AT_ASYNC_STD or AT_AT");
+  if (c->L < 1 || c->L > AT_MAX_L) return fail(AT_ERR_ARG, "L must be in 1..8");
+  if (c->nmodes < 1 || c->nmodes > AT_MAX_MODES) return fail(AT_ERR_ARG, "nmodes must be in 1..16");
+  if (!c->amp || !c->phase || !c->kappa) return fail(AT_ERR_ARG, "amp, phase and kappa are required");
+  int64_t tot = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (c->n[a] < 1 || c->pe[a] < 1) return fail(AT_ERR_ARG, "n and pe must be positive");
+    if (a >= c->dim && (c->n[a] != 1 || c->pe[a] != 1)) return fail(AT_ERR_ARG, "unused axes must have n = pe = 1");
+    if (c->n[a] % c->pe[a]) return fail(AT_ERR_ARG, "n must be a multiple of pe on every axis");
+    if (a < c->dim && c->n[a] / c->pe[a] < c->order) return fail(AT_ERR_ARG, "PE width must be at least the order (2h)");
+    if (c->n[a] > (int64_t)1 << 30) return fail(AT_ERR_ARG, "n too large");
+    tot *= c->n[a];
+  }
+  if (tot > ((int64_t)1 << 31) - 1) return fail(AT_ERR_ARG, "more than 2^31-1 points");
+  if (!(c->dt > 0.0) || !std::isfinite(c->dt) || !std::isfinite(c->alpha)) return fail(AT_ERR_ARG, "dt must be positive and finite");
+  if (c->thresholds) {
+    for (int m = 0; m + 1 < c->L; ++m) {
+      if (c->thresholds[m] > ((uint64_t)1 << 32)) return fail(AT_ERR_ARG, "thresholds must lie in [0, 2^32]");
+      if (m > 0 && c->thresholds[m] < c->thresholds[m - 1]) return fail(AT_ERR_ARG, "thresholds must ascend");
+    }
+  }
+  return AT_OK;
+}
+
+int64_t sides_of(const at_config_t *c) { return 2 * (int64_t)c->dim * c->pe[0] * c->pe[1] * c->pe[2]; }
+
+}  // namespace
+
+extern "C" int at_ring_slots(const at_config_t *cfg, int32_t *R) {
+  int rc = check_config(cfg);
+  if (rc) return rc;
+  if (!R) return fail(AT_ERR_ARG, "R is NULL");
+  *R = cfg->L + time_width(cfg);
+  return AT_OK;
+}
+
+extern "C" int at_num_sides(const at_config_t *cfg, int64_t *sides) {
+  int rc = check_config(cfg);
+  if (rc) return rc;
+  if (!sides) return fail(AT_ERR_ARG, "sides is NULL");
+  *sides = sides_of(cfg);
+  return AT_OK;
+}
+
+extern "C" int at_delay(uint64_t seed, int64_t step, int64_t side, int32_t L, const uint64_t *thresholds_host) {
+  if (L < 1 || L > AT_MAX_L || step < 0 || side < 0) return fail(AT_ERR_ARG, "at_delay: bad argument");
+  return atfd::delay_draw(seed, (uint32_t)step, (uint32_t)side, L, thresholds_host);
+}
+
+extern "C" int at_init(const at_config_t *cfg, double *ring_dev, int64_t ring_len, uint8_t *log_dev,
+                       int64_t log_steps, void *stream, at_handle_t **out) {
+  int rc = check_config(cfg);
+  if (rc) return rc;
+  if (!out || !ring_dev) return fail(AT_ERR_ARG, "ring_dev and out are required");
+  if (log_steps < 0 || (log_steps > 0 && !log_dev)) return fail(AT_ERR_ARG, "log_dev required when log_steps > 0");
+  const int T = time_width(cfg);
+  const int R = cfg->L + T;
+  const int64_t ntot = cfg->n[0] * cfg->n[1] * cfg->n[2];
+  if (ring_len < (int64_t)R * ntot) return fail(AT_ERR_ARG, "ring_len < R * points");
+  const int h = cfg->order / 2;
+
+  at_coeffs_t c1, c2;
+  if ((rc = at_coeffs(1, cfg->order, cfg->L, &c1)) != AT_OK) return rc;
+  if ((rc = at_coeffs(2, cfg->order, cfg->L, &c2)) != AT_OK) return rc;
+  if (cfg->scheme == AT_AT && (c1.T != T || c2.T != T)) return fail(AT_ERR_INCONSISTENT, "time widths of D1 and D2 differ");
+
+  at_handle *hd = new (std::nothrow) at_handle();
+  if (!hd) return fail(AT_ERR_ARG, "out of host memory");
+  hd->cfg = *cfg;
+  if (cfg->thresholds) hd->thr.assign(cfg->thresholds, cfg->thresholds + (cfg->L - 1));
+  hd->cfg.thresholds = nullptr;
+  hd->cfg.amp = hd->cfg.phase = nullptr;
+  hd->cfg.kappa = nullptr;
+  hd->stream = (cudaStream_t)stream;
+  hd->log_steps = log_steps;
+
+  StepParams &p = hd->sp;
+  std::memset(&p, 0, sizeof(p));
+  p.ring = ring_dev;
+  p.log = log_steps > 0 ? log_dev : nullptr;
+  p.ntot = ntot;
+  p.nb = sides_of(cfg);
+  p.dim = cfg->dim; p.h = h; p.T = T; p.R = R; p.L = cfg->L; p.scheme = cfg->scheme;
+  p.seed = cfg->seed;
+  p.use_thr = cfg->thresholds != nullptr;
+  for (size_t m = 0; m < hd->thr.size(); ++m) p.thr[m] = hd->thr[m];
+  double s0 = 1.0;
+  for (int a = 0; a < 3; ++a) {
+    p.n[a] = (int32_t)cfg->n[a];
+    p.pe[a] = cfg->pe[a];
+    p.S[a] = (int32_t)(cfg->n[a] / cfg->pe[a]);
+    p.use_pe[a] = (a < cfg->dim && cfg->pe[a] > 1) ? 1 : 0;
+    if (a >= cfg->dim) continue;
+    const double dx = kTwoPi / (double)cfg->n[a];
+    for (int j = -h; j <= h; ++j) {
+      const double v = cfg->dt * (-cfg->c[a] * c1.cd[j + h] / dx + cfg->alpha * c2.cd[j + h] / (dx * dx));
+      if (j == 0) s0 += v; else p.s[a][j + h] = v;
+    }
+  }
+  p.s0 = s0;
+  for (int k = 0; k < cfg->L; ++k)
+    for (int m = 0; m < T; ++m)
+      p.w[k][m] = cfg->scheme == AT_AT ? c2.w[k][m] : (m == 0 ? 1.0 : 0.0);
+
+  WaveParams &w = hd->wp;
+  std::memset(&w, 0, sizeof(w));
+  w.dim = cfg->dim; w.nmodes = cfg->nmodes; w.alpha = cfg->alpha;
+  for (int a = 0; a < 3; ++a) {
+    w.n[a] = (int32_t)cfg->n[a];
+    w.dx[a] = kTwoPi / (double)cfg->n[a];
+    w.c[a] = cfg->c[a];
+    if (a >= cfg->dim) continue;
+    for (int q = 0; q < cfg->nmodes; ++q) {
+      w.amp[a][q] = cfg->amp[a * cfg->nmodes + q];
+      w.phase[a][q] = cfg->phase[a * cfg->nmodes + q];
+      w.kappa[a][q] = (double)cfg->kappa[a * cfg->nmodes + q];
+    }
+  }
+
+  const size_t n_tables = (size_t)(cfg->n[0] + cfg->n[1] + cfg->n[2]);
+  const size_t bytes = 256 + sizeof(double) * ((size_t)AT_STAT_BLOCKS * AT_STAT_FIELDS + 16 + n_tables);
+  cudaError_t e = cudaMalloc(&hd->scratch, bytes);
+  if (e != cudaSuccess) { delete hd; return cuda_fail(e, "at_init: cudaMalloc"); }
+  char *base = (char *)hd->scratch;
+  hd->d_status = (int32_t *)base;
+  hd->d_partials = (double *)(base + 256);
+  hd->d_result = hd->d_partials + (size_t)AT_STAT_BLOCKS * AT_STAT_FIELDS;
+  hd->d_tables = hd->d_result + 16;
+  p.status = hd->d_status;
+  if ((e = cudaMemsetAsync(hd->d_status, 0, sizeof(int32_t), hd->stream)) != cudaSuccess ||
+      (e = launch_wave_field(w, 0.0, hd->d_tables, ring_dev, hd->stream)) != cudaSuccess) {
+    cudaFree(hd->scratch);
+    delete hd;
+    return cuda_fail(e, "at_init: initial condition");
+  }
+  *out = hd;
+  return AT_OK;
+}
+
+extern "C" int at_step(at_handle_t *hd, int64_t nsteps) {
+  if (!hd || nsteps < 0) return fail(AT_ERR_ARG, "at_step: bad argument");
+  if (hd->sp.log && hd->step + nsteps > hd->log_steps) return fail(AT_ERR_STATE, "at_step: delay log is full");
+  if (hd->step + nsteps > 0xFFFFFFFFll) return fail(AT_ERR_STATE, "at_step: step counter exceeds 32 bits");
+  for (int64_t s = 0; s < nsteps; ++s) {
+    cudaError_t e = launch_forward_step(hd->sp, hd->step, hd->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "at_step: launch");
+    hd->step += 1;
+  }
+  return AT_OK;
+}
+
+extern "C" int at_reset(at_handle_t *hd, const double *u0_dev) {
+  if (!hd) return fail(AT_ERR_ARG, "at_reset: NULL handle");
+  cudaError_t e;
+  if (u0_dev)
+    e = cudaMemcpyAsync(hd->sp.ring, u0_dev, sizeof(double) * (size_t)hd->sp.ntot, cudaMemcpyDeviceToDevice,
+                        hd->stream);
+  else
+    e = launch_wave_field(hd->wp, 0.0, hd->d_tables, hd->sp.ring, hd->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "at_reset");
+  hd->step = 0;
+  return AT_OK;
+}
+
+extern "C" int at_sync(at_handle_t *hd) {
+  if (!hd) return fail(AT_ERR_ARG, "at_sync: NULL handle");
+  cudaError_t e = cudaStreamSynchronize(hd->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "at_sync");
+  int32_t st = 0;
+  e = cudaMemcpy(&st, hd->d_status, sizeof(st), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "at_sync: status");
+  if (st != 0) return fail(st, "at_sync: device status word set");
+  return AT_OK;
+}
+
+extern "C" int at_state(at_handle_t *hd, int64_t *step, double **field_dev) {
+  if (!hd) return fail(AT_ERR_ARG, "at_state: NULL handle");
+  if (step) *step = hd->step;
+  if (field_dev) *field_dev = hd->sp.ring + (hd->step % hd->sp.R) * hd->sp.ntot;
+  return AT_OK;
+}
+
+extern "C" int at_error_stats(at_handle_t *hd, at_stats_t *out) {
+  if (!hd || !out) return fail(AT_ERR_ARG, "at_error_stats: bad argument");
+  const double *u = hd->sp.ring + (hd->step % hd->sp.R) * hd->sp.ntot;
+  const double t = (double)hd->step * hd->cfg.dt;
+  cudaError_t e = launch_error_stats(hd->wp, hd->sp, u, t, hd->d_tables, hd->d_partials, hd->d_result, hd->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "at_error_stats: launch");
+  double r[AT_STAT_FIELDS];
+  if ((e = cudaMemcpyAsync(r, hd->d_result, sizeof(r), cudaMemcpyDeviceToHost, hd->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(hd->stream)) != cudaSuccess)
+    return cuda_fail(e, "at_error_stats: copy");
+  const double N = (double)hd->sp.ntot;
+  out->rms = std::sqrt(r[0] / N);
+  out->max_abs = r[1];
+  out->mean_abs = r[2] / N;
+  out->mean = r[3] / N;
+  out->rms_I = r[7] > 0 ? std::sqrt(r[4] / r[7]) : 0.0;
+  out->rms_B = r[8] > 0 ? std::sqrt(r[5] / r[8]) : 0.0;
+  out->ua_rms = std::sqrt(r[6] / N);
+  out->n_I = (int64_t)r[7];
+  out->n_B = (int64_t)r[8];
+  out->step = hd->step;
+  if (!std::isfinite(out->rms) || !std::isfinite(out->max_abs)) return fail(AT_ERR_NONFINITE, "at_error_stats: non-finite error");
+  return AT_OK;
+}
+
+extern "C" int at_destroy(at_handle_t *hd) {
+  if (!hd) return AT_OK;
+  cudaError_t e = cudaStreamSynchronize(hd->stream);
+  cudaFree(hd->scratch);
+  delete hd;
+  if (e != cudaSuccess) return cuda_fail(e, "at_destroy");
+  return AT_OK;
+}

@@ -1,0 +1,52 @@
+// internal.h -- declarations shared by the translation units of libatfd (not part of the C ABI).
+#pragma once
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#define AT_MAX_L 8
+#define AT_MAX_T 4
+#define AT_MAX_H 2
+#define AT_MAX_MODES 16
+#define AT_STAT_FIELDS 9
+#define AT_STAT_BLOCKS 1024
+
+void at_internal_set_error(const char *msg);
+
+// Everything one forward step needs, passed to the kernel by value.
+struct StepParams {
+  double *ring;           // R slots of ntot doubles; level m in slot m mod R
+  uint8_t *log;           // raw delays, step-major [log_steps][nb], or nullptr
+  int32_t *status;        // sticky device status word
+  int64_t ntot;           // points
+  int64_t nb;             // PE sides, 2 * dim * prod(pe)
+  int32_t n[3];           // points per axis
+  int32_t S[3];           // PE width per axis
+  int32_t pe[3];          // PEs per axis
+  int32_t use_pe[3];      // axis has PE boundaries (pe > 1)
+  int32_t dim, h, T, R, L, scheme;
+  int32_t use_thr;        // thresholds given (else uniform bins)
+  uint64_t seed;
+  uint64_t thr[AT_MAX_L]; // L-1 bin edges on the 32-bit word
+  double s0;              // merged centre coefficient: 1 + dt sum_a (-c_a cd1_0/dx_a + alpha cd2_0/dx_a^2)
+  double s[3][2 * AT_MAX_H + 1];  // merged off-centre coefficients per axis (index j+h)
+  double w[AT_MAX_L][AT_MAX_T];   // halo extrapolation weights w[k][m] of level n-k-m
+};
+
+// Initial-condition / analytic-solution parameters.
+struct WaveParams {
+  int32_t dim, nmodes;
+  int32_t n[3];
+  double dx[3];
+  double c[3];
+  double alpha;
+  double amp[3][AT_MAX_MODES];
+  double phase[3][AT_MAX_MODES];
+  double kappa[3][AT_MAX_MODES];
+};
+
+// Launchers (return cudaGetLastError()).
+cudaError_t launch_forward_step(const StepParams &p, int64_t n, cudaStream_t st);
+cudaError_t launch_wave_field(const WaveParams &w, double t, double *tables, double *out, cudaStream_t st);
+cudaError_t launch_error_stats(const WaveParams &w, const StepParams &p, const double *u, double t,
+                               double *tables, double *partials, double *result, cudaStream_t st);

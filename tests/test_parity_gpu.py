@@ -1,0 +1,160 @@
+"""GPU parity: the sm_103a forward path against the FP64 CPU oracle on the same seeded inputs.
+
+Bars: delay logs bit-exact; fields within 1e-12 relative L2 (and elementwise within 1e-12 of the
+field's max norm) after the full run; statistics within round-off of the oracle's on the same field.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+TOL = 1e-12
+THREADS = os.cpu_count() or 1
+
+
+def _gpu_run(spec, nsteps, log=True):
+    from paper_1702_00496_gb300 import Solver
+    s = Solver(spec, log_steps=nsteps if log else 0)
+    s.step(nsteps)
+    s.sync()
+    u = s.field().cpu().numpy().copy()
+    d = s.delays().cpu().numpy().copy() if log else None
+    st = s.error_stats()
+    s.close()
+    return u, d, st
+
+
+def _compare(spec, nsteps, stats=True):
+    u, d, st = _gpu_run(spec, nsteps)
+    cfg = oracle.Config(spec)
+    ref, dref, _ = oracle.run(cfg, nsteps, threads=THREADS)
+    assert np.array_equal(d, dref), "delay logs differ"
+    rel = np.linalg.norm(u - ref) / np.linalg.norm(ref)
+    assert rel <= TOL, rel
+    assert np.abs(u - ref).max() <= TOL * np.abs(ref).max()
+    if stats:
+        so = oracle.error_stats(cfg, u, nsteps)
+        for key in ("rms", "max_abs", "mean_abs", "rms_I", "rms_B", "ua_rms"):
+            assert st[key] == pytest.approx(so[key], rel=1e-9, abs=1e-300), key
+        assert abs(st["mean"] - so["mean"]) <= 1e-9 * so["mean_abs"] + 1e-300
+        assert (st["n_I"], st["n_B"], st["step"]) == (so["n_I"], so["n_B"], nsteps)
+    return u, ref
+
+
+def test_1d_n256_order2_full_run():
+    spec, steps = W.workload("1d_n256")
+    _compare(spec, steps)
+
+
+@pytest.mark.parametrize("scheme", [W.SYNC, W.ASYNC_STD, W.AT])
+@pytest.mark.parametrize("order", [2, 4])
+def test_1d_schemes_ragged_tiles(order, scheme):
+    # 12000 points in 30 PEs of 400: several thread blocks and a ragged last block
+    spec, _ = W.wl_1d(12000, 30, order, 4, 0, 77, range(1, 11), scheme=scheme)
+    _compare(spec, 300)
+
+
+def test_1d_binned_delays_fig_at_sol1():
+    spec, _ = W.wl_1d(128, 4, 2, 3, 0, 9, (2, 3, 5), probs=[0.5, 0.3, 0.2])
+    _compare(spec, 1500)
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_1d_minimum_pe_width(order):
+    spec, _ = W.wl_1d(64 * order, 64, order, 3, 0, 5, (1, 3))  # S = order = 2h
+    _compare(spec, 200)
+
+
+def test_single_delay_level_equals_synchronous_run():
+    spec, _ = W.wl_1d(512, 8, 4, 1, 0, 6, (1, 2))
+    u_at, d, _ = _gpu_run(spec, 100)
+    assert not d.any()
+    spec["scheme"] = W.SYNC
+    u_sync, _, _ = _gpu_run(spec, 100)
+    assert np.array_equal(u_at, u_sync)
+
+
+def test_zero_steps_is_the_initial_condition():
+    spec, _ = W.wl_1d(1000, 10, 4, 3, 0, 8, range(1, 5))
+    u, _, st = _gpu_run(spec, 0, log=False)
+    ref = oracle.initial(oracle.Config(spec))
+    assert np.abs(u - ref).max() <= 4e-16 * np.abs(ref).max()
+    assert st["rms"] <= 1e-15 and st["step"] == 0
+
+
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("scheme", [W.SYNC, W.ASYNC_STD, W.AT])
+def test_3d_small(order, scheme):
+    spec, _ = W.wl_3d([24, 20, 16], [3, 2, 4], order, 3, 0, 31, scheme=scheme, c=(1.0, -0.7, 0.4))
+    _compare(spec, 40)
+
+
+def test_3d_unsplit_axis_and_binned_delays():
+    spec, _ = W.wl_3d([16, 12, 20], [2, 1, 5], 4, 3, 0, 32)
+    spec["thresholds"] = W.thresholds_from_probs([0.2, 0.5, 0.3])
+    _compare(spec, 30)
+
+
+# ------------------------------------------------------------ full-size workloads
+def _closed_form_sync_1d(spec, nsteps, idx):
+    n = spec["n"][0]
+    dx = 2 * np.pi / n
+    x = idx * dx
+    u = np.zeros(len(idx))
+    for A, ph, kap in zip(spec["amp"][0], spec["phase"][0], spec["kappa"][0]):
+        th = kap * dx
+        s1 = (8 * np.sin(th) - np.sin(2 * th)) / (6 * dx)
+        s2 = (-2 * np.cos(2 * th) + 32 * np.cos(th) - 30) / (12 * dx ** 2)
+        G = 1 + spec["dt"] * (-spec["c"][0] * 1j * s1 + spec["alpha"] * s2)
+        u += A * np.imag(G ** nsteps * np.exp(1j * (kap * x + ph)))
+    return u
+
+
+def test_full_size_1d_n16m_delays_and_field():
+    """N = 2^24, 4096 PEs, order 4, L = 4: the whole 1000-step delay log bit-exact, the field after a
+    100-step prefix against the oracle, and the 1000-step synchronous field against its closed form."""
+    spec, steps = W.workload("1d_n16m")
+    cfg = oracle.Config(spec)
+    from paper_1702_00496_gb300 import Solver
+    s = Solver(spec, log_steps=steps)
+    s.step(100)
+    s.sync()
+    u100 = s.field().cpu().numpy().copy()
+    s.step(steps - 100)
+    s.sync()
+    assert np.array_equal(s.delays().cpu().numpy(), oracle.delay_log(cfg, steps))
+    s.close()
+    ref, _, _ = oracle.run(cfg, 100, want_log=False, threads=THREADS)
+    assert np.linalg.norm(u100 - ref) / np.linalg.norm(ref) <= TOL
+    spec["scheme"] = W.SYNC
+    u, _, _ = _gpu_run(spec, steps, log=False)
+    idx = np.random.default_rng(0).choice(spec["n"][0], 4096, replace=False)
+    want = _closed_form_sync_1d(spec, steps, idx)
+    assert np.abs(u[idx] - want).max() <= TOL * np.abs(want).max()
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_full_size_3d_512_prefix(order):
+    """512^3 in 8^3 PEs: delay log of the 500-step run bit-exact; field after a 6-step prefix vs oracle."""
+    spec, steps = W.workload(f"3d_512_o{order}")
+    cfg = oracle.Config(spec)
+    from paper_1702_00496_gb300 import Solver
+    s = Solver(spec, log_steps=steps)
+    s.step(6)
+    s.sync()
+    u = s.field().cpu().numpy().copy()
+    s.step(steps - 6)
+    s.sync()
+    assert np.array_equal(s.delays().cpu().numpy(), oracle.delay_log(cfg, steps))
+    st = s.error_stats()
+    s.close()
+    ref, _, _ = oracle.run(cfg, 6, want_log=False, threads=THREADS)
+    assert np.linalg.norm(u - ref) / np.linalg.norm(ref) <= TOL
+    assert np.isfinite(st["rms"]) and st["rms"] < 1e-2 * st["ua_rms"]
