@@ -40,10 +40,13 @@ def _compare(spec, nsteps, stats=True):
     assert rel <= TOL, rel
     assert np.abs(u - ref).max() <= TOL * np.abs(ref).max()
     if stats:
+        # Both sides evaluate u_a with their own sin/exp (a few ulp of |u_a| apart), so E = U - u_a agrees to
+        # ~1e-15 |u_a| absolutely; relative agreement of tiny errors is not expected.
         so = oracle.error_stats(cfg, u, nsteps)
-        for key in ("rms", "max_abs", "mean_abs", "rms_I", "rms_B", "ua_rms"):
-            assert st[key] == pytest.approx(so[key], rel=1e-9, abs=1e-300), key
-        assert abs(st["mean"] - so["mean"]) <= 1e-9 * so["mean_abs"] + 1e-300
+        atol = 1e-13 * so["ua_rms"]
+        for key in ("rms", "max_abs", "mean_abs", "mean", "rms_I", "rms_B"):
+            assert abs(st[key] - so[key]) <= 1e-9 * abs(so[key]) + atol, key
+        assert st["ua_rms"] == pytest.approx(so["ua_rms"], rel=1e-13)
         assert (st["n_I"], st["n_B"], st["step"]) == (so["n_I"], so["n_B"], nsteps)
     return u, ref
 
@@ -85,8 +88,8 @@ def test_zero_steps_is_the_initial_condition():
     spec, _ = W.wl_1d(1000, 10, 4, 3, 0, 8, range(1, 5))
     u, _, st = _gpu_run(spec, 0, log=False)
     ref = oracle.initial(oracle.Config(spec))
-    assert np.abs(u - ref).max() <= 4e-16 * np.abs(ref).max()
-    assert st["rms"] <= 1e-15 and st["step"] == 0
+    assert np.abs(u - ref).max() <= 4e-15 * np.abs(ref).max()
+    assert st["rms"] <= 1e-14 * st["ua_rms"] and st["step"] == 0
 
 
 @pytest.mark.parametrize("order", [2, 4])
