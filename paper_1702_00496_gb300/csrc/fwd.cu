@@ -37,64 +37,160 @@ __device__ __forceinline__ double halo_value(const StepParams &p, int64_t cell, 
   return acc;
 }
 
+// Updated value of point i (linear index) with coordinates c: the general path, used for points within h
+// of a PE edge, points whose stencil wraps around the periodic domain, and ragged groups.
 template <int DIM, int H>
-__global__ void __launch_bounds__(256) forward_step_kernel(const StepParams p, const int64_t n) {
+__device__ __noinline__ double point_update(const StepParams &p, const double *__restrict__ un, int64_t n, int64_t i,
+                                            const int c[3]) {
+  const int64_t stride[3] = {1, (int64_t)p.n[0], (int64_t)p.n[0] * p.n[1]};
+  int pos[3], pidx[3];
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    pidx[a] = c[a] / p.S[a];
+    pos[a] = c[a] - pidx[a] * p.S[a];
+  }
+  double acc = p.s0 * __ldg(un + i);
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    const int S = p.S[a];
+    const bool lo = pos[a] < H, hi = pos[a] >= S - H;
+    const bool edge = p.use_pe[a] && (lo || hi);
+    int k = 0;
+    if (lo || hi) {
+      int pe_id = pidx[0];
+      if (DIM == 3) pe_id = (pidx[2] * p.pe[1] + pidx[1]) * p.pe[0] + pidx[0];
+      const int64_t side = 2 * (int64_t)DIM * pe_id + 2 * a + (lo ? 0 : 1);
+      int raw = 0;
+      if (p.scheme != 0) raw = atfd::delay_draw(p.seed, (uint32_t)n, (uint32_t)side, p.L, p.use_thr ? p.thr : nullptr);
+      k = atfd::delay_clamp(raw, n, p.T);
+      // the log writer of this side: the edge point of the side with the other coordinates at the PE origin
+      bool writer = lo ? (pos[a] == 0) : (pos[a] == S - 1);
+#pragma unroll
+      for (int b = 0; b < DIM; ++b)
+        if (b != a && pos[b] != 0) writer = false;
+      if (writer && p.log != nullptr) p.log[n * p.nb + side] = (uint8_t)raw;
+    }
+#pragma unroll
+    for (int j = -H; j <= H; ++j) {
+      if (j == 0) continue;
+      const int cj = wrap_coord(c[a] + j, p.n[a]);
+      const int64_t cell = i + (int64_t)(cj - c[a]) * stride[a];
+      double v;
+      if (edge && (pos[a] + j < 0 || pos[a] + j >= S))
+        v = halo_value(p, cell, n, k);
+      else
+        v = __ldg(un + cell);
+      acc = fma(p.s[a][j + H], v, acc);
+    }
+  }
+  return acc;
+}
+
+__device__ __forceinline__ double2 ld2(const double *ptr) { return __ldg(reinterpret_cast<const double2 *>(ptr)); }
+
+// Merged stencil of one point from the values of its line along one axis (v[H + j] = u_{i+j}).
+template <int H>
+__device__ __forceinline__ double axis_taps(const double (&s)[2 * AT_MAX_H + 1], const double *v, double acc) {
+#pragma unroll
+  for (int j = -H; j <= H; ++j)
+    if (j != 0) acc = fma(s[j + H], v[H + j], acc);
+  return acc;
+}
+
+// 1D: each thread updates four consecutive points with 16-byte loads and stores.  A group that lies inside
+// one PE, at least h from its edges and from the ends of the domain, takes the straight FMA path with four
+// independent accumulation chains; any other group takes the general path point by point.
+template <int H>
+__global__ void __launch_bounds__(256) forward_1d_kernel(const StepParams p, const int64_t n) {
+  const double *__restrict__ un = p.ring + (n % p.R) * p.ntot;
+  double *__restrict__ out = p.ring + ((n + 1) % p.R) * p.ntot;
+  const int N = p.n[0], S = p.S[0];
+  const int groups = (N + 3) >> 2;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += gridDim.x * blockDim.x) {
+    const int i0 = g << 2;
+    const int pos0 = i0 % S;
+    const bool inside = (i0 >= 2) && (i0 + 6 <= N) && (!p.use_pe[0] || (pos0 >= H && pos0 + 3 < S - H));
+    if (inside) {
+      const double2 a = ld2(un + i0 - 2), b = ld2(un + i0), c = ld2(un + i0 + 2), d = ld2(un + i0 + 4);
+      const double v[8] = {a.x, a.y, b.x, b.y, c.x, c.y, d.x, d.y};  // u[i0-2 .. i0+5]
+      double r[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) r[q] = axis_taps<H>(p.s[0], v + q + 2 - H, p.s0 * v[q + 2]);
+      reinterpret_cast<double2 *>(out + i0)[0] = make_double2(r[0], r[1]);
+      reinterpret_cast<double2 *>(out + i0)[1] = make_double2(r[2], r[3]);
+    } else {
+      for (int q = 0; q < 4 && i0 + q < N; ++q) {
+        const int c[3] = {i0 + q, 0, 0};
+        out[i0 + q] = point_update<1, H>(p, un, n, i0 + q, c);
+      }
+    }
+  }
+}
+
+// 3D: each thread updates four consecutive x points of one (y, z) row.  Rows y +- j and z +- j are read with
+// the same 16-byte alignment (nx is a multiple of 4 on this path).
+template <int H>
+__global__ void __launch_bounds__(256) forward_3d_kernel(const StepParams p, const int64_t n) {
+  const double *__restrict__ un = p.ring + (n % p.R) * p.ntot;
+  double *__restrict__ out = p.ring + ((n + 1) % p.R) * p.ntot;
+  const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
+  const int gx = nx >> 2;
+  const int64_t groups = (int64_t)gx * ny * nz;
+  const int64_t sy = nx, sz = (int64_t)nx * ny;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = g / gx;
+    const int x0 = (int)(g - row * gx) << 2;
+    const int z = (int)(row / ny), y = (int)(row - (int64_t)z * ny);
+    const int px = x0 % p.S[0], py = y % p.S[1], pz = z % p.S[2];
+    const bool inx = (x0 >= 2) && (x0 + 6 <= nx) && (!p.use_pe[0] || (px >= H && px + 3 < p.S[0] - H));
+    const bool iny = (y >= H) && (y + H < ny) && (!p.use_pe[1] || (py >= H && py < p.S[1] - H));
+    const bool inz = (z >= H) && (z + H < nz) && (!p.use_pe[2] || (pz >= H && pz < p.S[2] - H));
+    const int64_t i0 = row * nx + x0;
+    if (inx && iny && inz) {
+      const double2 a = ld2(un + i0 - 2), b = ld2(un + i0), c = ld2(un + i0 + 2), d = ld2(un + i0 + 4);
+      const double v[8] = {a.x, a.y, b.x, b.y, c.x, c.y, d.x, d.y};
+      double r[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) r[q] = axis_taps<H>(p.s[0], v + q + 2 - H, p.s0 * v[q + 2]);
+#pragma unroll
+      for (int ax = 1; ax < 3; ++ax) {
+        const int64_t st = ax == 1 ? sy : sz;
+#pragma unroll
+        for (int j = -H; j <= H; ++j) {
+          if (j == 0) continue;
+          const double2 e = ld2(un + i0 + j * st), f = ld2(un + i0 + j * st + 2);
+          r[0] = fma(p.s[ax][j + H], e.x, r[0]);
+          r[1] = fma(p.s[ax][j + H], e.y, r[1]);
+          r[2] = fma(p.s[ax][j + H], f.x, r[2]);
+          r[3] = fma(p.s[ax][j + H], f.y, r[3]);
+        }
+      }
+      reinterpret_cast<double2 *>(out + i0)[0] = make_double2(r[0], r[1]);
+      reinterpret_cast<double2 *>(out + i0)[1] = make_double2(r[2], r[3]);
+    } else {
+      for (int q = 0; q < 4; ++q) {
+        const int c[3] = {x0 + q, y, z};
+        out[i0 + q] = point_update<3, H>(p, un, n, i0 + q, c);
+      }
+    }
+  }
+}
+
+// Fallback for shapes the grouped kernels do not take (odd point counts, nx not a multiple of 4).
+template <int DIM, int H>
+__global__ void __launch_bounds__(256) forward_point_kernel(const StepParams p, const int64_t n) {
   const double *__restrict__ un = p.ring + (n % p.R) * p.ntot;
   double *__restrict__ out = p.ring + ((n + 1) % p.R) * p.ntot;
   const int nx = p.n[0], ny = DIM == 3 ? p.n[1] : 1;
-  const int64_t stride[3] = {1, (int64_t)nx, (int64_t)nx * ny};
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.ntot;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    int c[3];
-    if (DIM == 1) {
-      c[0] = (int)i; c[1] = 0; c[2] = 0;
-    } else {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.ntot; i += (int64_t)gridDim.x * blockDim.x) {
+    int c[3] = {(int)i, 0, 0};
+    if (DIM == 3) {
       const int64_t yz = i / nx;
       c[0] = (int)(i - yz * nx);
       c[2] = (int)(yz / ny);
       c[1] = (int)(yz - (int64_t)c[2] * ny);
     }
-    int pos[3], pidx[3];
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-      pidx[a] = c[a] / p.S[a];
-      pos[a] = c[a] - pidx[a] * p.S[a];
-    }
-    double acc = p.s0 * __ldg(un + i);
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-      const int S = p.S[a];
-      const bool lo = pos[a] < H, hi = pos[a] >= S - H;
-      const bool edge = p.use_pe[a] && (lo || hi);
-      int k = 0;
-      if (lo || hi) {
-        int pe_id = pidx[0];
-        if (DIM == 3) pe_id = (pidx[2] * p.pe[1] + pidx[1]) * p.pe[0] + pidx[0];
-        const int64_t side = 2 * (int64_t)DIM * pe_id + 2 * a + (lo ? 0 : 1);
-        int raw = 0;
-        if (p.scheme != 0) raw = atfd::delay_draw(p.seed, (uint32_t)n, (uint32_t)side, p.L, p.use_thr ? p.thr : nullptr);
-        k = atfd::delay_clamp(raw, n, p.T);
-        // the log writer of this side: the edge point of the side with the other coordinates at the PE origin
-        bool writer = lo ? (pos[a] == 0) : (pos[a] == S - 1);
-#pragma unroll
-        for (int b = 0; b < DIM; ++b)
-          if (b != a && pos[b] != 0) writer = false;
-        if (writer && p.log != nullptr) p.log[n * p.nb + side] = (uint8_t)raw;
-      }
-#pragma unroll
-      for (int j = -H; j <= H; ++j) {
-        if (j == 0) continue;
-        const int cj = wrap_coord(c[a] + j, p.n[a]);
-        const int64_t cell = i + (int64_t)(cj - c[a]) * stride[a];
-        double v;
-        if (edge && (pos[a] + j < 0 || pos[a] + j >= S))
-          v = halo_value(p, cell, n, k);
-        else
-          v = __ldg(un + cell);
-        acc = fma(p.s[a][j + H], v, acc);
-      }
-    }
-    out[i] = acc;
+    out[i] = point_update<DIM, H>(p, un, n, i, c);
   }
 }
 
@@ -102,14 +198,27 @@ __global__ void __launch_bounds__(256) forward_step_kernel(const StepParams p, c
 
 cudaError_t launch_forward_step(const StepParams &p, int64_t n, cudaStream_t st) {
   const int threads = 256;
-  int64_t blocks = (p.ntot + threads - 1) / threads;
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  const int max_blocks = 152 * 8 * 4;
+  auto grid = [&](int64_t work) { int64_t b = (work + threads - 1) / threads; return (int)(b < max_blocks ? b : max_blocks); };
+  const bool even = (p.ntot % 2) == 0 && (reinterpret_cast<uintptr_t>(p.ring) % 16) == 0;
   if (p.dim == 1) {
-    if (p.h == 1) forward_step_kernel<1, 1><<<(int)blocks, threads, 0, st>>>(p, n);
-    else forward_step_kernel<1, 2><<<(int)blocks, threads, 0, st>>>(p, n);
+    if (even) {
+      const int64_t groups = (p.ntot + 3) / 4;
+      if (p.h == 1) forward_1d_kernel<1><<<grid(groups), threads, 0, st>>>(p, n);
+      else forward_1d_kernel<2><<<grid(groups), threads, 0, st>>>(p, n);
+    } else {
+      if (p.h == 1) forward_point_kernel<1, 1><<<grid(p.ntot), threads, 0, st>>>(p, n);
+      else forward_point_kernel<1, 2><<<grid(p.ntot), threads, 0, st>>>(p, n);
+    }
   } else {
-    if (p.h == 1) forward_step_kernel<3, 1><<<(int)blocks, threads, 0, st>>>(p, n);
-    else forward_step_kernel<3, 2><<<(int)blocks, threads, 0, st>>>(p, n);
+    if (p.n[0] % 4 == 0 && even) {
+      const int64_t groups = p.ntot / 4;
+      if (p.h == 1) forward_3d_kernel<1><<<grid(groups), threads, 0, st>>>(p, n);
+      else forward_3d_kernel<2><<<grid(groups), threads, 0, st>>>(p, n);
+    } else {
+      if (p.h == 1) forward_point_kernel<3, 1><<<grid(p.ntot), threads, 0, st>>>(p, n);
+      else forward_point_kernel<3, 2><<<grid(p.ntot), threads, 0, st>>>(p, n);
+    }
   }
   return cudaGetLastError();
 }

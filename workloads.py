@@ -9,7 +9,7 @@ Workloads (the paper's experiments use synthetic multi-sine fields only, so thes
 themselves, not stand-ins for a dataset):
   1d_n256      1D, N=256,  8 PEs,    CD2 + (1,2,2)b/(2,2,2)b, L=3, 2000 steps
   1d_n16m      1D, N=2^24, 4096 PEs, CD4 + (1,4,2)/(2,4,2),   L=4, 1000 steps
-  3d_512       3D, 512^3, 8x8x8 PEs,  order 2 or 4, L=3, 500 steps
+  3d_512_o2/4  3D, 512^3, 8x8x8 PEs,  order 2 or 4, L=3, dt = dx^2, 500 steps
   ensemble     1024 1D realizations, N_r in {2^10..2^16}, P_r=N_r/64, L_r in {2,3,4}, 5000 steps
   adjoint_256  3D 256^3, 4x4x4 PEs, order 4, L=3, 2000 steps
 """
@@ -63,7 +63,10 @@ def wl_3d(n, P, order, L, steps, seed, scheme=AT, c=(1.0, 1.0, 1.0), alpha=0.05,
     nn = list(n) if hasattr(n, "__len__") else [n, n, n]
     pp = list(P) if hasattr(P, "__len__") else [P, P, P]
     if dt is None:
-        dt = 2.0 * dx_of(min(nn)) ** 2  # r_alpha = alpha dt / dx^2 = 0.1 per axis at alpha = 0.05
+        # dt = dx^2 as in the 1D workloads: r_alpha = alpha dt / dx^2 = 0.05 per axis at alpha = 0.05.  With
+        # forward Euler the order-4 AT stencils in 3D need r_alpha <= 1/16 per axis: their halo extrapolates
+        # old levels, which amplifies the modes whose per-step factor 1 - 3 r_alpha 64/12 turns negative.
+        dt = dx_of(max(nn)) ** 2
     return make(3, nn, pp, order, L, scheme, list(c), alpha, dt, seed, kappas), steps
 
 
@@ -83,8 +86,9 @@ def workload(name: str, scheme: int = AT):
 
 
 def adjoint_spec(n=256, P=4, steps=2000, alpha=0.05, alpha_target=0.06, seed=5):
-    """3D order-4 AT problem of the adjoint workload; dt is fixed by r_alpha = 0.1 at alpha_target."""
-    dt = 0.1 * dx_of(n) ** 2 / alpha_target
+    """3D order-4 AT problem of the adjoint workload; dt is fixed by r_alpha = 0.05 at alpha_target (the 3D
+    order-4 AT limit is 1/16 per axis), so both alpha values share one dt."""
+    dt = 0.05 * dx_of(n) ** 2 / alpha_target
     spec, _ = wl_3d(n, P, 4, 3, steps, seed, AT, alpha=alpha, dt=dt)
     return spec, steps
 
