@@ -143,6 +143,70 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+def run_ensemble(args, rank: int, world: int, local: int):
+    """1024 1D realizations (N_r in 2^10..2^16, L_r in 2..4, 5000 steps) in one persistent graph launch, against
+    the same realizations run one problem at a time through the single-problem path (graph-captured steps)."""
+    import torch
+    import torch.distributed as dist
+    from paper_1702_00496_gb300 import Ensemble, Solver
+
+    specs, T = W.ensemble_members()
+    if args.time_steps is not None:
+        T = args.time_steps
+    for s in specs:
+        s["seed"] = int(s["seed"]) + 100000 * rank
+    updates = sum(s["n"][0] for s in specs) * T
+    stream = torch.cuda.current_stream()
+    ens = Ensemble(specs, T, threads=args.threads, ctas_per_sm=args.ctas_per_sm, device=f"cuda:{local}", stream=stream)
+    for _ in range(args.warmup):
+        ens.run()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ens.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    per, groups = ens.stats()
+    if world > 1:
+        tt = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{local}")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    # the same realizations one problem at a time: reset, T steps, statistics, in sequence
+    one = None
+    if not args.skip_one_at_a_time:
+        solvers = [Solver(s, device=f"cuda:{local}", stream=stream) for s in specs]
+        for sv in solvers[:8]:
+            sv.step(T)
+            sv.reset()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for sv in solvers:
+            sv.reset()
+            sv.step(T)
+            sv.error_stats()
+        torch.cuda.synchronize()
+        one = (time.perf_counter() - t0) * 1e3
+        for sv in solvers:
+            sv.close()
+    ens.close()
+    if rank == 0:
+        line = {"metric": METRIC + " -- batched ensemble", "value": world * updates / (ms / 1e3), "unit": "updates/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "ensemble", "members": len(specs), "time_steps": T,
+                           "total_points": sum(s["n"][0] for s in specs)},
+                "one_at_a_time_ms": one, "speedup_vs_one_at_a_time": (one / ms) if one else None,
+                "groups": groups, "clocks": clocks, "gpu_launches": args.steps * 3}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -154,6 +218,9 @@ def main():
     ap.add_argument("--cpu-sample-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--time-steps", type=int, default=None, help="override the steps per run (profiling only)")
+    ap.add_argument("--threads", type=int, default=0, help="ensemble: threads per CTA (0: library default)")
+    ap.add_argument("--ctas-per-sm", type=int, default=0, help="ensemble: CTAs per SM (0: occupancy limit)")
+    ap.add_argument("--skip-one-at-a-time", action="store_true")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -168,6 +235,8 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.workload == "ensemble":
+        return run_ensemble(args, rank, world, local)
 
     from paper_1702_00496_gb300 import Solver
 

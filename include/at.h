@@ -159,6 +159,34 @@ int at_error_stats(at_handle_t *hd, at_stats_t *out);
 /* Release the handle's scratch.  The caller's ring and log are untouched. */
 int at_destroy(at_handle_t *hd);
 
+/* ------------------------------------------------------------------ batched ensemble */
+/* The error of an AT scheme is a statistical quantity (Sec. 4: ensemble average over delay realizations,
+ * Eq. "aveE_split"; Sec. 5.1: averages over runs with random phases).  An ensemble runs `count` independent
+ * 1D problems -- each with its own n[0] (a multiple of 4), PEs, L, seed, initial condition and dt -- for
+ * `nsteps` steps each, inside one persistent kernel captured in a CUDA graph: CTAs take realizations from a
+ * work counter in longest-first order, so uneven grid sizes balance over the SMs.
+ *
+ * at_ensemble_sizes: doubles of ring and bytes of delay log the members need (members stored one after
+ * another, member r's ring holding its own R_r slots).
+ * at_ensemble_create: members are copied; ring_dev (ring_len doubles) and the optional log_dev (log_len bytes,
+ * NULL for no log) are borrowed.  threads per CTA is 64, 128 or 256 (0: 256); ctas_per_sm <= 0 takes the
+ * occupancy limit.  Errors: AT_ERR_ARG (non-1D member, n[0] % 4 != 0, sizes), AT_ERR_CUDA.
+ * at_ensemble_run: one graph launch on the ensemble's stream (asynchronous).
+ * at_ensemble_stats: blocks; per_member[r] (up to cap entries) receives member r's error statistics at its
+ * final step (the at_error_stats fields); for each distinct grid size g < *ngroups (ascending, up to cap):
+ * group_n[g], the ensemble mean group_mean[g] and unbiased variance group_var[g] of the members' RMS
+ * errors, and the member count group_count[g].  Any output pointer may be NULL.
+ * Errors: AT_ERR_CUDA, AT_ERR_NONFINITE. */
+typedef struct at_ensemble at_ensemble_t;
+int at_ensemble_sizes(const at_config_t *members, int32_t count, int64_t nsteps, int64_t *ring_len, int64_t *log_len);
+int at_ensemble_create(const at_config_t *members, int32_t count, int64_t nsteps, double *ring_dev, int64_t ring_len,
+                       uint8_t *log_dev, int64_t log_len, int32_t threads, int32_t ctas_per_sm, void *stream,
+                       at_ensemble_t **out);
+int at_ensemble_run(at_ensemble_t *ens);
+int at_ensemble_stats(at_ensemble_t *ens, at_stats_t *per_member, int32_t cap, int32_t *ngroups, int64_t *group_n,
+                      double *group_mean, double *group_var, int32_t *group_count);
+int at_ensemble_destroy(at_ensemble_t *ens);
+
 /* One-line description of the last error on this thread ("" if none). */
 const char *at_last_error(void);
 

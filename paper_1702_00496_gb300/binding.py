@@ -22,6 +22,7 @@ AT_SYNC, AT_ASYNC_STD, AT_AT = 0, 1, 2
 EXPORTS = (
     "at_coeffs", "at_stencil_taps", "at_solve_stencil", "at_delay", "at_ring_slots", "at_num_sides",
     "at_init", "at_step", "at_reset", "at_sync", "at_state", "at_error_stats", "at_destroy", "at_last_error",
+    "at_ensemble_sizes", "at_ensemble_create", "at_ensemble_run", "at_ensemble_stats", "at_ensemble_destroy",
 )
 
 
@@ -88,6 +89,12 @@ def load(build_if_missing: bool = True):
     L.at_error_stats.argtypes = [vp, C.POINTER(at_stats_t)]
     L.at_destroy.argtypes = [vp]
     L.at_last_error.restype = C.c_char_p
+    L.at_ensemble_sizes.argtypes = [C.POINTER(at_config_t), i32, i64, C.POINTER(i64), C.POINTER(i64)]
+    L.at_ensemble_create.argtypes = [C.POINTER(at_config_t), i32, i64, vp, i64, vp, i64, i32, i32, vp, C.POINTER(vp)]
+    L.at_ensemble_run.argtypes = [vp]
+    L.at_ensemble_stats.argtypes = [vp, C.POINTER(at_stats_t), i32, C.POINTER(i32), C.POINTER(i64), dp, dp,
+                                    C.POINTER(i32)]
+    L.at_ensemble_destroy.argtypes = [vp]
     _lib = L
     return L
 
@@ -224,3 +231,50 @@ def at_error_stats(h) -> dict:
 
 def at_destroy(h) -> None:
     _check(load().at_destroy(h), "at_destroy")
+
+
+def _config_array(cfgs):
+    arr = (at_config_t * len(cfgs))()
+    for i, c in enumerate(cfgs):
+        arr[i] = c.s
+    return arr
+
+
+def at_ensemble_sizes(cfgs, nsteps: int):
+    """(ring doubles, log bytes) the members need."""
+    arr = _config_array(cfgs)
+    ring, log = C.c_int64(), C.c_int64()
+    _check(load().at_ensemble_sizes(arr, len(cfgs), int(nsteps), C.byref(ring), C.byref(log)), "at_ensemble_sizes")
+    return ring.value, log.value
+
+
+def at_ensemble_create(cfgs, nsteps, ring, log=None, threads=0, ctas_per_sm=0, stream=None):
+    arr = _config_array(cfgs)
+    h = C.c_void_p()
+    _check(load().at_ensemble_create(arr, len(cfgs), int(nsteps), C.c_void_p(ring.data_ptr()), ring.numel(),
+                                     C.c_void_p(log.data_ptr()) if log is not None else None,
+                                     log.numel() if log is not None else 0, int(threads), int(ctas_per_sm),
+                                     _stream_ptr(stream), C.byref(h)), "at_ensemble_create")
+    return h
+
+
+def at_ensemble_run(h) -> None:
+    _check(load().at_ensemble_run(h), "at_ensemble_run")
+
+
+def at_ensemble_stats(h, count: int):
+    """Returns (per-member stats dicts, groups: list of dicts with n, mean, var, count)."""
+    per = (at_stats_t * count)()
+    cap = max(count, 64)
+    ng = C.c_int32()
+    gn = (C.c_int64 * cap)()
+    gm = (C.c_double * cap)()
+    gv = (C.c_double * cap)()
+    gc = (C.c_int32 * cap)()
+    _check(load().at_ensemble_stats(h, per, count, C.byref(ng), gn, gm, gv, gc), "at_ensemble_stats")
+    groups = [{"n": gn[g], "mean": gm[g], "var": gv[g], "count": gc[g]} for g in range(ng.value)]
+    return [per[r].as_dict() for r in range(count)], groups
+
+
+def at_ensemble_destroy(h) -> None:
+    _check(load().at_ensemble_destroy(h), "at_ensemble_destroy")

@@ -24,7 +24,13 @@ struct at_handle {
   double *d_partials = nullptr;
   double *d_result = nullptr;
   double *d_tables = nullptr;
+  int64_t *d_step = nullptr;  // step base read by the captured graph
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
 };
+
+// Steps per captured graph: long runs replay one graph of kGraphSteps kernel nodes plus a counter update.
+static const int64_t kGraphSteps = 50;
 
 namespace {
 
@@ -97,43 +103,26 @@ extern "C" int at_delay(uint64_t seed, int64_t step, int64_t side, int32_t L, co
   return atfd::delay_draw(seed, (uint32_t)step, (uint32_t)side, L, thresholds_host);
 }
 
-extern "C" int at_init(const at_config_t *cfg, double *ring_dev, int64_t ring_len, uint8_t *log_dev,
-                       int64_t log_steps, void *stream, at_handle_t **out) {
+int at_prepare_params(const at_config_t *cfg, double *ring_dev, uint8_t *log_dev, StepParams *out) {
   int rc = check_config(cfg);
   if (rc) return rc;
-  if (!out || !ring_dev) return fail(AT_ERR_ARG, "ring_dev and out are required");
-  if (log_steps < 0 || (log_steps > 0 && !log_dev)) return fail(AT_ERR_ARG, "log_dev required when log_steps > 0");
   const int T = time_width(cfg);
-  const int R = cfg->L + T;
-  const int64_t ntot = cfg->n[0] * cfg->n[1] * cfg->n[2];
-  if (ring_len < (int64_t)R * ntot) return fail(AT_ERR_ARG, "ring_len < R * points");
   const int h = cfg->order / 2;
-
   at_coeffs_t c1, c2;
   if ((rc = at_coeffs(1, cfg->order, cfg->L, &c1)) != AT_OK) return rc;
   if ((rc = at_coeffs(2, cfg->order, cfg->L, &c2)) != AT_OK) return rc;
   if (cfg->scheme == AT_AT && (c1.T != T || c2.T != T)) return fail(AT_ERR_INCONSISTENT, "time widths of D1 and D2 differ");
-
-  at_handle *hd = new (std::nothrow) at_handle();
-  if (!hd) return fail(AT_ERR_ARG, "out of host memory");
-  hd->cfg = *cfg;
-  if (cfg->thresholds) hd->thr.assign(cfg->thresholds, cfg->thresholds + (cfg->L - 1));
-  hd->cfg.thresholds = nullptr;
-  hd->cfg.amp = hd->cfg.phase = nullptr;
-  hd->cfg.kappa = nullptr;
-  hd->stream = (cudaStream_t)stream;
-  hd->log_steps = log_steps;
-
-  StepParams &p = hd->sp;
+  StepParams &p = *out;
   std::memset(&p, 0, sizeof(p));
   p.ring = ring_dev;
-  p.log = log_steps > 0 ? log_dev : nullptr;
-  p.ntot = ntot;
+  p.log = log_dev;
+  p.ntot = cfg->n[0] * cfg->n[1] * cfg->n[2];
   p.nb = sides_of(cfg);
-  p.dim = cfg->dim; p.h = h; p.T = T; p.R = R; p.L = cfg->L; p.scheme = cfg->scheme;
+  p.dim = cfg->dim; p.h = h; p.T = T; p.R = cfg->L + T; p.L = cfg->L; p.scheme = cfg->scheme;
   p.seed = cfg->seed;
   p.use_thr = cfg->thresholds != nullptr;
-  for (size_t m = 0; m < hd->thr.size(); ++m) p.thr[m] = hd->thr[m];
+  if (cfg->thresholds)
+    for (int m = 0; m + 1 < cfg->L; ++m) p.thr[m] = cfg->thresholds[m];
   double s0 = 1.0;
   for (int a = 0; a < 3; ++a) {
     p.n[a] = (int32_t)cfg->n[a];
@@ -151,6 +140,34 @@ extern "C" int at_init(const at_config_t *cfg, double *ring_dev, int64_t ring_le
   for (int k = 0; k < cfg->L; ++k)
     for (int m = 0; m < T; ++m)
       p.w[k][m] = cfg->scheme == AT_AT ? c2.w[k][m] : (m == 0 ? 1.0 : 0.0);
+  return AT_OK;
+}
+
+extern "C" int at_init(const at_config_t *cfg, double *ring_dev, int64_t ring_len, uint8_t *log_dev,
+                       int64_t log_steps, void *stream, at_handle_t **out) {
+  int rc = check_config(cfg);
+  if (rc) return rc;
+  if (!out || !ring_dev) return fail(AT_ERR_ARG, "ring_dev and out are required");
+  if (log_steps < 0 || (log_steps > 0 && !log_dev)) return fail(AT_ERR_ARG, "log_dev required when log_steps > 0");
+  const int T = time_width(cfg);
+  const int R = cfg->L + T;
+  const int64_t ntot = cfg->n[0] * cfg->n[1] * cfg->n[2];
+  if (ring_len < (int64_t)R * ntot) return fail(AT_ERR_ARG, "ring_len < R * points");
+
+  at_handle *hd = new (std::nothrow) at_handle();
+  if (!hd) return fail(AT_ERR_ARG, "out of host memory");
+  if ((rc = at_prepare_params(cfg, ring_dev, log_steps > 0 ? log_dev : nullptr, &hd->sp)) != AT_OK) {
+    delete hd;
+    return rc;
+  }
+  hd->cfg = *cfg;
+  if (cfg->thresholds) hd->thr.assign(cfg->thresholds, cfg->thresholds + (cfg->L - 1));
+  hd->cfg.thresholds = nullptr;
+  hd->cfg.amp = hd->cfg.phase = nullptr;
+  hd->cfg.kappa = nullptr;
+  hd->stream = (cudaStream_t)stream;
+  hd->log_steps = log_steps;
+  StepParams &p = hd->sp;
 
   WaveParams &w = hd->wp;
   std::memset(&w, 0, sizeof(w));
@@ -168,12 +185,13 @@ extern "C" int at_init(const at_config_t *cfg, double *ring_dev, int64_t ring_le
   }
 
   const size_t n_tables = (size_t)(cfg->n[0] + cfg->n[1] + cfg->n[2]);
-  const size_t bytes = 256 + sizeof(double) * ((size_t)AT_STAT_BLOCKS * AT_STAT_FIELDS + 16 + n_tables);
+  const size_t bytes = 512 + sizeof(double) * ((size_t)AT_STAT_BLOCKS * AT_STAT_FIELDS + 16 + n_tables);
   cudaError_t e = cudaMalloc(&hd->scratch, bytes);
   if (e != cudaSuccess) { delete hd; return cuda_fail(e, "at_init: cudaMalloc"); }
   char *base = (char *)hd->scratch;
   hd->d_status = (int32_t *)base;
-  hd->d_partials = (double *)(base + 256);
+  hd->d_step = (int64_t *)(base + 256);
+  hd->d_partials = (double *)(base + 512);
   hd->d_result = hd->d_partials + (size_t)AT_STAT_BLOCKS * AT_STAT_FIELDS;
   hd->d_tables = hd->d_result + 16;
   p.status = hd->d_status;
@@ -187,13 +205,48 @@ extern "C" int at_init(const at_config_t *cfg, double *ring_dev, int64_t ring_le
   return AT_OK;
 }
 
+static int build_graph(at_handle *hd) {
+  cudaStream_t cap;
+  cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "at_step: capture stream");
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  for (int64_t g = 0; g < kGraphSteps && e == cudaSuccess; ++g) e = launch_forward_step(hd->sp, g, hd->d_step, cap);
+  if (e == cudaSuccess) e = launch_step_counter(hd->d_step, kGraphSteps, false, cap);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&hd->exec, graph, 0);
+  cudaStreamDestroy(cap);
+  if (e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    hd->exec = nullptr;
+    return cuda_fail(e, "at_step: graph");
+  }
+  hd->graph = graph;
+  return AT_OK;
+}
+
 extern "C" int at_step(at_handle_t *hd, int64_t nsteps) {
   if (!hd || nsteps < 0) return fail(AT_ERR_ARG, "at_step: bad argument");
   if (hd->sp.log && hd->step + nsteps > hd->log_steps) return fail(AT_ERR_STATE, "at_step: delay log is full");
   if (hd->step + nsteps > 0xFFFFFFFFll) return fail(AT_ERR_STATE, "at_step: step counter exceeds 32 bits");
-  for (int64_t s = 0; s < nsteps; ++s) {
-    cudaError_t e = launch_forward_step(hd->sp, hd->step, hd->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "at_step: launch");
+  cudaError_t e;
+  const int64_t chunks = nsteps / kGraphSteps;
+  if (chunks > 0) {
+    if (!hd->exec) {
+      int rc = build_graph(hd);
+      if (rc) return rc;
+    }
+    if ((e = launch_step_counter(hd->d_step, hd->step, true, hd->stream)) != cudaSuccess)
+      return cuda_fail(e, "at_step: counter");
+    for (int64_t c = 0; c < chunks; ++c) {
+      if ((e = cudaGraphLaunch(hd->exec, hd->stream)) != cudaSuccess) return cuda_fail(e, "at_step: graph launch");
+      hd->step += kGraphSteps;
+    }
+  }
+  for (int64_t s = chunks * kGraphSteps; s < nsteps; ++s) {
+    if ((e = launch_forward_step(hd->sp, hd->step, nullptr, hd->stream)) != cudaSuccess)
+      return cuda_fail(e, "at_step: launch");
     hd->step += 1;
   }
   return AT_OK;
@@ -258,6 +311,8 @@ extern "C" int at_error_stats(at_handle_t *hd, at_stats_t *out) {
 extern "C" int at_destroy(at_handle_t *hd) {
   if (!hd) return AT_OK;
   cudaError_t e = cudaStreamSynchronize(hd->stream);
+  if (hd->exec) cudaGraphExecDestroy(hd->exec);
+  if (hd->graph) cudaGraphDestroy(hd->graph);
   cudaFree(hd->scratch);
   delete hd;
   if (e != cudaSuccess) return cuda_fail(e, "at_destroy");

@@ -1,0 +1,363 @@
+// ensemble.cu -- many independent delay realizations of the 1D problem in one persistent launch.
+//
+// The accuracy claims of the paper are statistical: Sec. 4 defines the error through an ensemble average
+// over delay realizations (the overline of Eq. "aveE_split"), and Sec. 5.1 averages runs with different
+// initial phases.  This engine runs `count` 1D realizations (each with its own grid size, PE count, delay
+// range L, seed and initial condition) to completion inside ONE persistent kernel:
+//   - a fixed grid of CTAs pulls realizations from an atomic work counter in longest-first order (the host
+//     sorts by cost N * steps), so uneven grid sizes balance across the 152 SMs;
+//   - a CTA owns its realization for the whole run: it writes U^0 (Eq. "IC"), advances every step with the
+//     same fused stencil as the per-step kernel (delay draw, halo extrapolation, merged taps), separated by
+//     __syncthreads, and finally reduces E = U - u_a (Eq. "ana_sol") into the realization's statistics;
+//   - a second small kernel forms, per grid size, the ensemble mean and unbiased variance of the RMS error.
+// Both kernels and the counter reset are captured once in a CUDA graph; one run is one graph launch.
+// Each realization keeps its own R-slot ring in global memory (level m in slot m mod R); small rings stay
+// in L1/L2.  Reads use plain coherent loads because the kernel reads back levels it wrote itself.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "../../include/at.h"
+#include "stencil.cuh"
+
+namespace {
+
+struct MemberParams {
+  StepParams p;
+  double amp[AT_MAX_MODES];        // A of Eq. "IC"
+  double amp_final[AT_MAX_MODES];  // A exp(-alpha kappa^2 t_final)
+  double phase[AT_MAX_MODES];
+  double kappa[AT_MAX_MODES];
+  double dx, shift_final;          // grid spacing, c * t_final
+  int32_t nmodes, group;
+};
+
+constexpr int kStatFields = AT_STAT_FIELDS;
+
+__device__ double wave_1d(const MemberParams &m, const double *amp, double shift, int i) {
+  const double x = (double)i * m.dx;
+  double s = 0.0;
+  for (int q = 0; q < m.nmodes; ++q) s += amp[q] * sin(m.kappa[q] * (x - shift) + m.phase[q]);
+  return s;
+}
+
+template <int H>
+__device__ void run_member(const MemberParams &m, int64_t nsteps) {
+  const StepParams &p = m.p;
+  const int groups = p.n[0] >> 2;
+  for (int64_t n = 0; n < nsteps; ++n) {
+    const double *un = p.ring + (n % p.R) * p.ntot;
+    double *out = p.ring + ((n + 1) % p.R) * p.ntot;
+    for (int g = threadIdx.x; g < groups; g += blockDim.x) atfd::group_1d<H, atfd::LdCoherent>(p, un, out, n, g << 2);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256) ensemble_kernel(const MemberParams *__restrict__ members,
+                                                       const int32_t *__restrict__ order, int32_t count, int64_t nsteps,
+                                                       int32_t *counter, double *__restrict__ member_stats) {
+  __shared__ MemberParams m;
+  __shared__ int32_t item;
+  __shared__ double red[kStatFields][256];
+  for (;;) {
+    if (threadIdx.x == 0) item = atomicAdd(counter, 1);
+    __syncthreads();
+    if (item >= count) break;
+    const int32_t r = order[item];
+    {
+      const int words = (int)(sizeof(MemberParams) / sizeof(int32_t));
+      const int32_t *src = reinterpret_cast<const int32_t *>(members + r);
+      int32_t *dst = reinterpret_cast<int32_t *>(&m);
+      for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
+    }
+    __syncthreads();
+    const int N = m.p.n[0];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) m.p.ring[i] = wave_1d(m, m.amp, 0.0, i);
+    __syncthreads();
+    if (m.p.h == 1) run_member<1>(m, nsteps);
+    else run_member<2>(m, nsteps);
+    // statistics of E = U^nsteps - u_a(x, nsteps dt), as in the single-problem reduction
+    const double *u = m.p.ring + (nsteps % m.p.R) * m.p.ntot;
+    double acc[kStatFields];
+#pragma unroll
+    for (int f = 0; f < kStatFields; ++f) acc[f] = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      const double ua = wave_1d(m, m.amp_final, m.shift_final, i);
+      const int pos = i % m.p.S[0];
+      const bool inB = m.p.use_pe[0] && (pos < m.p.h || pos >= m.p.S[0] - m.p.h);
+      const double e = u[i] - ua;
+      acc[0] += e * e;
+      acc[1] = fmax(acc[1], fabs(e));
+      acc[2] += fabs(e);
+      acc[3] += e;
+      if (inB) { acc[5] += e * e; acc[8] += 1.0; } else { acc[4] += e * e; acc[7] += 1.0; }
+      acc[6] += ua * ua;
+      if (e != e) acc[1] = e;
+    }
+#pragma unroll
+    for (int f = 0; f < kStatFields; ++f) red[f][threadIdx.x] = acc[f];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if ((int)threadIdx.x < s) {
+#pragma unroll
+        for (int f = 0; f < kStatFields; ++f) {
+          const double o = red[f][threadIdx.x + s];
+          red[f][threadIdx.x] = (f == 1) ? ((o != o) ? o : fmax(red[f][threadIdx.x], o)) : red[f][threadIdx.x] + o;
+        }
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x < kStatFields) member_stats[(int64_t)r * kStatFields + threadIdx.x] = red[threadIdx.x][0];
+    __syncthreads();
+  }
+}
+
+// Per grid size g: mean and unbiased variance of the members' RMS errors, summed in member order.
+__global__ void summary_kernel(const double *__restrict__ member_stats, const MemberParams *__restrict__ members,
+                               int32_t count, int32_t ngroups, double *__restrict__ out /* [ngroups][3] */) {
+  for (int g = threadIdx.x; g < ngroups; g += blockDim.x) {
+    double s = 0.0, c = 0.0;
+    for (int r = 0; r < count; ++r)
+      if (members[r].group == g) {
+        s += sqrt(member_stats[(int64_t)r * kStatFields] / (double)members[r].p.ntot);
+        c += 1.0;
+      }
+    const double mean = c > 0 ? s / c : 0.0;
+    double v = 0.0;
+    for (int r = 0; r < count; ++r)
+      if (members[r].group == g) {
+        const double d = sqrt(member_stats[(int64_t)r * kStatFields] / (double)members[r].p.ntot) - mean;
+        v += d * d;
+      }
+    out[3 * g] = mean;
+    out[3 * g + 1] = c > 1 ? v / (c - 1.0) : 0.0;
+    out[3 * g + 2] = c;
+  }
+}
+
+__global__ void reset_counter(int32_t *c) { *c = 0; }
+
+int fail(int code, const char *msg) {
+  at_internal_set_error(msg);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where) {
+  char buf[200];
+  std::snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+  at_internal_set_error(buf);
+  return AT_ERR_CUDA;
+}
+
+const double kTwoPi = 6.283185307179586476925286766559005768;
+
+}  // namespace
+
+struct at_ensemble {
+  int32_t count = 0, ngroups = 0;
+  int64_t nsteps = 0;
+  cudaStream_t stream = nullptr;
+  void *scratch = nullptr;
+  MemberParams *d_members = nullptr;
+  int32_t *d_order = nullptr;
+  int32_t *d_counter = nullptr;
+  double *d_member_stats = nullptr;
+  double *d_summary = nullptr;
+  std::vector<int64_t> group_n;
+  std::vector<int64_t> member_n;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int threads = 256, blocks = 0;
+};
+
+// Ring and log sizes (in doubles and bytes) the members need, laid out member after member.
+extern "C" int at_ensemble_sizes(const at_config_t *members, int32_t count, int64_t nsteps, int64_t *ring_len,
+                                 int64_t *log_len) {
+  if (!members || count < 1 || nsteps < 0 || !ring_len || !log_len) return fail(AT_ERR_ARG, "at_ensemble_sizes: bad argument");
+  int64_t ring = 0, log = 0;
+  for (int r = 0; r < count; ++r) {
+    int32_t R;
+    int64_t nb;
+    int rc = at_ring_slots(members + r, &R);
+    if (rc) return rc;
+    if ((rc = at_num_sides(members + r, &nb))) return rc;
+    if (members[r].dim != 1 || members[r].n[0] % 4) return fail(AT_ERR_ARG, "ensemble members must be 1D with N % 4 == 0");
+    ring += (int64_t)R * members[r].n[0];
+    log += nsteps * nb;
+  }
+  *ring_len = ring;
+  *log_len = log;
+  return AT_OK;
+}
+
+extern "C" int at_ensemble_create(const at_config_t *members, int32_t count, int64_t nsteps, double *ring_dev,
+                                  int64_t ring_len, uint8_t *log_dev, int64_t log_len, int32_t threads,
+                                  int32_t ctas_per_sm, void *stream, at_ensemble_t **out) {
+  int64_t need_ring, need_log;
+  int rc = at_ensemble_sizes(members, count, nsteps, &need_ring, &need_log);
+  if (rc) return rc;
+  if (!out || !ring_dev || ring_len < need_ring) return fail(AT_ERR_ARG, "at_ensemble_create: ring too small");
+  if (log_dev && log_len < need_log) return fail(AT_ERR_ARG, "at_ensemble_create: log too small");
+  if (nsteps > 0xFFFFFFFFll) return fail(AT_ERR_ARG, "at_ensemble_create: step counter exceeds 32 bits");
+  if (threads == 0) threads = 256;
+  if (threads != 64 && threads != 128 && threads != 256) return fail(AT_ERR_ARG, "threads must be 64, 128 or 256");
+
+  std::vector<MemberParams> host(count);
+  std::map<int64_t, int> groups;
+  for (int r = 0; r < count; ++r) groups[members[r].n[0]] = 0;
+  int gi = 0;
+  for (auto &kv : groups) kv.second = gi++;
+  at_ensemble *e = new (std::nothrow) at_ensemble();
+  if (!e) return fail(AT_ERR_ARG, "out of host memory");
+  int64_t ring_off = 0, log_off = 0;
+  for (int r = 0; r < count; ++r) {
+    const at_config_t &c = members[r];
+    // merged taps, extrapolation weights and delay parameters exactly as for a single problem
+    int32_t R;
+    int64_t nb;
+    at_ring_slots(&c, &R);
+    at_num_sides(&c, &nb);
+    MemberParams &m = host[r];
+    std::memset(&m, 0, sizeof(m));
+    rc = at_prepare_params(&c, ring_dev + ring_off, log_dev ? log_dev + log_off : nullptr, &m.p);
+    if (rc) { delete e; return rc; }
+    m.nmodes = c.nmodes;
+    m.dx = kTwoPi / (double)c.n[0];
+    const double tf = (double)nsteps * c.dt;
+    m.shift_final = c.c[0] * tf;
+    for (int q = 0; q < c.nmodes; ++q) {
+      m.amp[q] = c.amp[q];
+      m.phase[q] = c.phase[q];
+      m.kappa[q] = (double)c.kappa[q];
+      m.amp_final[q] = tf == 0.0 ? c.amp[q] : c.amp[q] * std::exp(-c.alpha * m.kappa[q] * m.kappa[q] * tf);
+    }
+    m.group = groups[c.n[0]];
+    e->member_n.push_back(c.n[0]);
+    ring_off += (int64_t)R * c.n[0];
+    log_off += nsteps * nb;
+  }
+  for (auto &kv : groups) e->group_n.push_back(kv.first);
+  e->count = count;
+  e->ngroups = (int32_t)groups.size();
+  e->nsteps = nsteps;
+  e->stream = (cudaStream_t)stream;
+  e->threads = threads;
+  // longest first (cost ~ N * steps, equal steps): largest grids start first
+  std::vector<int32_t> order(count);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return members[a].n[0] > members[b].n[0]; });
+
+  const size_t b_members = sizeof(MemberParams) * (size_t)count;
+  const size_t b_order = sizeof(int32_t) * (size_t)count;
+  const size_t b_stats = sizeof(double) * (size_t)count * kStatFields;
+  const size_t b_sum = sizeof(double) * 3 * (size_t)e->ngroups;
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  cudaError_t err = cudaMalloc(&e->scratch, up(b_members) + up(b_order) + 256 + up(b_stats) + up(b_sum));
+  if (err != cudaSuccess) { delete e; return cuda_fail(err, "at_ensemble_create: cudaMalloc"); }
+  char *base = (char *)e->scratch;
+  e->d_members = (MemberParams *)base; base += up(b_members);
+  e->d_order = (int32_t *)base; base += up(b_order);
+  e->d_counter = (int32_t *)base; base += 256;
+  e->d_member_stats = (double *)base; base += up(b_stats);
+  e->d_summary = (double *)base;
+  if ((err = cudaMemcpy(e->d_members, host.data(), b_members, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (err = cudaMemcpy(e->d_order, order.data(), b_order, cudaMemcpyHostToDevice)) != cudaSuccess) {
+    cudaFree(e->scratch); delete e;
+    return cuda_fail(err, "at_ensemble_create: upload");
+  }
+  int dev = 0, sms = 0, fit = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, ensemble_kernel, threads, 0);
+  if (ctas_per_sm <= 0) ctas_per_sm = fit;
+  if (ctas_per_sm > fit) ctas_per_sm = fit;
+  if (ctas_per_sm < 1) ctas_per_sm = 1;
+  e->blocks = sms * ctas_per_sm;
+  if (e->blocks > count) e->blocks = count;
+  // capture: counter reset, persistent kernel, summary
+  cudaStream_t cap;
+  if ((err = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) {
+    cudaFree(e->scratch); delete e;
+    return cuda_fail(err, "at_ensemble_create: stream");
+  }
+  err = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (err == cudaSuccess) {
+    reset_counter<<<1, 1, 0, cap>>>(e->d_counter);
+    ensemble_kernel<<<e->blocks, threads, 0, cap>>>(e->d_members, e->d_order, count, nsteps, e->d_counter,
+                                                    e->d_member_stats);
+    summary_kernel<<<1, 128, 0, cap>>>(e->d_member_stats, e->d_members, count, e->ngroups, e->d_summary);
+    err = cudaStreamEndCapture(cap, &e->graph);
+  }
+  if (err == cudaSuccess) err = cudaGraphInstantiate(&e->exec, e->graph, 0);
+  cudaStreamDestroy(cap);
+  if (err != cudaSuccess) {
+    if (e->graph) cudaGraphDestroy(e->graph);
+    cudaFree(e->scratch); delete e;
+    return cuda_fail(err, "at_ensemble_create: graph");
+  }
+  *out = e;
+  return AT_OK;
+}
+
+extern "C" int at_ensemble_run(at_ensemble_t *e) {
+  if (!e) return fail(AT_ERR_ARG, "at_ensemble_run: NULL handle");
+  cudaError_t err = cudaGraphLaunch(e->exec, e->stream);
+  if (err != cudaSuccess) return cuda_fail(err, "at_ensemble_run");
+  return AT_OK;
+}
+
+extern "C" int at_ensemble_stats(at_ensemble_t *e, at_stats_t *per_member, int32_t cap, int32_t *ngroups,
+                                 int64_t *group_n, double *group_mean, double *group_var, int32_t *group_count) {
+  if (!e || !ngroups) return fail(AT_ERR_ARG, "at_ensemble_stats: bad argument");
+  std::vector<double> ms((size_t)e->count * kStatFields), sum(3 * (size_t)e->ngroups);
+  cudaError_t err;
+  if ((err = cudaMemcpyAsync(ms.data(), e->d_member_stats, ms.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                             e->stream)) != cudaSuccess ||
+      (err = cudaMemcpyAsync(sum.data(), e->d_summary, sum.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                             e->stream)) != cudaSuccess ||
+      (err = cudaStreamSynchronize(e->stream)) != cudaSuccess)
+    return cuda_fail(err, "at_ensemble_stats");
+  *ngroups = e->ngroups;
+  if (per_member) {
+    for (int r = 0; r < e->count && r < cap; ++r) {
+      const double *s = &ms[(size_t)r * kStatFields];
+      const double N = (double)e->member_n[r];
+      at_stats_t &o = per_member[r];
+      o.rms = std::sqrt(s[0] / N);
+      o.max_abs = s[1];
+      o.mean_abs = s[2] / N;
+      o.mean = s[3] / N;
+      o.rms_I = s[7] > 0 ? std::sqrt(s[4] / s[7]) : 0.0;
+      o.rms_B = s[8] > 0 ? std::sqrt(s[5] / s[8]) : 0.0;
+      o.ua_rms = std::sqrt(s[6] / N);
+      o.n_I = (int64_t)s[7];
+      o.n_B = (int64_t)s[8];
+      o.step = e->nsteps;
+    }
+  }
+  for (int g = 0; g < e->ngroups && g < cap; ++g) {
+    if (group_n) group_n[g] = e->group_n[g];
+    if (group_mean) group_mean[g] = sum[3 * g];
+    if (group_var) group_var[g] = sum[3 * g + 1];
+    if (group_count) group_count[g] = (int32_t)sum[3 * g + 2];
+  }
+  for (double v : ms)
+    if (!std::isfinite(v)) return fail(AT_ERR_NONFINITE, "at_ensemble_stats: non-finite statistic");
+  return AT_OK;
+}
+
+extern "C" int at_ensemble_destroy(at_ensemble_t *e) {
+  if (!e) return AT_OK;
+  cudaError_t err = cudaStreamSynchronize(e->stream);
+  if (e->exec) cudaGraphExecDestroy(e->exec);
+  if (e->graph) cudaGraphDestroy(e->graph);
+  cudaFree(e->scratch);
+  delete e;
+  if (err != cudaSuccess) return cuda_fail(err, "at_ensemble_destroy");
+  return AT_OK;
+}

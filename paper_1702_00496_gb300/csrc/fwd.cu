@@ -15,122 +15,34 @@
 // drawn in-kernel from Philox (Sec. 5.1) keyed by (seed, step, side) and clamped so that no level before
 // 0 is read; one designated thread per side writes the raw draw to the delay log.
 //
-// The kernel is FP64-FMA bound on GB300 (2 FP64 FMA lanes per SM per clock): loads go through L1, the
-// DFMA chain per point is the minimum 1 + 2 h dim operations.
-#include "internal.h"
-#include "philox.cuh"
+// The kernel is bound by the FP64 pipe on GB300 (2 FP64 FMA lanes per SM per clock nominal; about 1.6 per
+// clock sustained for dependent FMA chains): each point costs the minimum 1 + 2 h dim FP64 operations, all of
+// them FMAs -- the chain starts with fma(s0, u_i, +0) on a runtime zero, because a DMUL occupies the FP64
+// pipe longer than a DFMA and the result is the same rounded product.
+#include "stencil.cuh"
 
 namespace {
 
-__device__ __forceinline__ int wrap_coord(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
-
-// Halo value of `cell` seen across a PE side with effective delay k (T successive levels).
-__device__ __forceinline__ double halo_value(const StepParams &p, int64_t cell, int64_t n, int k) {
-  if (k == 0) return __ldg(p.ring + (n % p.R) * p.ntot + cell);
-  double acc = 0.0;
-#pragma unroll
-  for (int m = 0; m < AT_MAX_T; ++m) {
-    if (m >= p.T) break;
-    const int64_t lev = n - k - m;
-    acc = fma(p.w[k][m], __ldg(p.ring + (lev % p.R) * p.ntot + cell), acc);
-  }
-  return acc;
-}
-
-// Updated value of point i (linear index) with coordinates c: the general path, used for points within h
-// of a PE edge, points whose stencil wraps around the periodic domain, and ragged groups.
-template <int DIM, int H>
-__device__ __noinline__ double point_update(const StepParams &p, const double *__restrict__ un, int64_t n, int64_t i,
-                                            const int c[3]) {
-  const int64_t stride[3] = {1, (int64_t)p.n[0], (int64_t)p.n[0] * p.n[1]};
-  int pos[3], pidx[3];
-#pragma unroll
-  for (int a = 0; a < DIM; ++a) {
-    pidx[a] = c[a] / p.S[a];
-    pos[a] = c[a] - pidx[a] * p.S[a];
-  }
-  double acc = p.s0 * __ldg(un + i);
-#pragma unroll
-  for (int a = 0; a < DIM; ++a) {
-    const int S = p.S[a];
-    const bool lo = pos[a] < H, hi = pos[a] >= S - H;
-    const bool edge = p.use_pe[a] && (lo || hi);
-    int k = 0;
-    if (lo || hi) {
-      int pe_id = pidx[0];
-      if (DIM == 3) pe_id = (pidx[2] * p.pe[1] + pidx[1]) * p.pe[0] + pidx[0];
-      const int64_t side = 2 * (int64_t)DIM * pe_id + 2 * a + (lo ? 0 : 1);
-      int raw = 0;
-      if (p.scheme != 0) raw = atfd::delay_draw(p.seed, (uint32_t)n, (uint32_t)side, p.L, p.use_thr ? p.thr : nullptr);
-      k = atfd::delay_clamp(raw, n, p.T);
-      // the log writer of this side: the edge point of the side with the other coordinates at the PE origin
-      bool writer = lo ? (pos[a] == 0) : (pos[a] == S - 1);
-#pragma unroll
-      for (int b = 0; b < DIM; ++b)
-        if (b != a && pos[b] != 0) writer = false;
-      if (writer && p.log != nullptr) p.log[n * p.nb + side] = (uint8_t)raw;
-    }
-#pragma unroll
-    for (int j = -H; j <= H; ++j) {
-      if (j == 0) continue;
-      const int cj = wrap_coord(c[a] + j, p.n[a]);
-      const int64_t cell = i + (int64_t)(cj - c[a]) * stride[a];
-      double v;
-      if (edge && (pos[a] + j < 0 || pos[a] + j >= S))
-        v = halo_value(p, cell, n, k);
-      else
-        v = __ldg(un + cell);
-      acc = fma(p.s[a][j + H], v, acc);
-    }
-  }
-  return acc;
-}
-
-__device__ __forceinline__ double2 ld2(const double *ptr) { return __ldg(reinterpret_cast<const double2 *>(ptr)); }
-
-// Merged stencil of one point from the values of its line along one axis (v[H + j] = u_{i+j}).
-template <int H>
-__device__ __forceinline__ double axis_taps(const double (&s)[2 * AT_MAX_H + 1], const double *v, double acc) {
-#pragma unroll
-  for (int j = -H; j <= H; ++j)
-    if (j != 0) acc = fma(s[j + H], v[H + j], acc);
-  return acc;
-}
+using namespace atfd;
 
 // 1D: each thread updates four consecutive points with 16-byte loads and stores.  A group that lies inside
 // one PE, at least h from its edges and from the ends of the domain, takes the straight FMA path with four
 // independent accumulation chains; any other group takes the general path point by point.
 template <int H>
-__global__ void __launch_bounds__(256) forward_1d_kernel(const StepParams p, const int64_t n) {
+__global__ void __launch_bounds__(256) forward_1d_kernel(const StepParams p, const int64_t n_off, const int64_t *n_base) {
+  const int64_t n = n_off + (n_base ? *n_base : 0);
   const double *__restrict__ un = p.ring + (n % p.R) * p.ntot;
   double *__restrict__ out = p.ring + ((n + 1) % p.R) * p.ntot;
-  const int N = p.n[0], S = p.S[0];
-  const int groups = (N + 3) >> 2;
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += gridDim.x * blockDim.x) {
-    const int i0 = g << 2;
-    const int pos0 = i0 % S;
-    const bool inside = (i0 >= 2) && (i0 + 6 <= N) && (!p.use_pe[0] || (pos0 >= H && pos0 + 3 < S - H));
-    if (inside) {
-      const double2 a = ld2(un + i0 - 2), b = ld2(un + i0), c = ld2(un + i0 + 2), d = ld2(un + i0 + 4);
-      const double v[8] = {a.x, a.y, b.x, b.y, c.x, c.y, d.x, d.y};  // u[i0-2 .. i0+5]
-      double r[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) r[q] = axis_taps<H>(p.s[0], v + q + 2 - H, p.s0 * v[q + 2]);
-      reinterpret_cast<double2 *>(out + i0)[0] = make_double2(r[0], r[1]);
-      reinterpret_cast<double2 *>(out + i0)[1] = make_double2(r[2], r[3]);
-    } else {
-      for (int q = 0; q < 4 && i0 + q < N; ++q) {
-        const int c[3] = {i0 + q, 0, 0};
-        out[i0 + q] = point_update<1, H>(p, un, n, i0 + q, c);
-      }
-    }
-  }
+  const int groups = (p.n[0] + 3) >> 2;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += gridDim.x * blockDim.x)
+    group_1d<H, LdgNC>(p, un, out, n, g << 2);
 }
 
 // 3D: each thread updates four consecutive x points of one (y, z) row.  Rows y +- j and z +- j are read with
 // the same 16-byte alignment (nx is a multiple of 4 on this path).
 template <int H>
-__global__ void __launch_bounds__(256) forward_3d_kernel(const StepParams p, const int64_t n) {
+__global__ void __launch_bounds__(256) forward_3d_kernel(const StepParams p, const int64_t n_off, const int64_t *n_base) {
+  const int64_t n = n_off + (n_base ? *n_base : 0);
   const double *__restrict__ un = p.ring + (n % p.R) * p.ntot;
   double *__restrict__ out = p.ring + ((n + 1) % p.R) * p.ntot;
   const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
@@ -147,18 +59,18 @@ __global__ void __launch_bounds__(256) forward_3d_kernel(const StepParams p, con
     const bool inz = (z >= H) && (z + H < nz) && (!p.use_pe[2] || (pz >= H && pz < p.S[2] - H));
     const int64_t i0 = row * nx + x0;
     if (inx && iny && inz) {
-      const double2 a = ld2(un + i0 - 2), b = ld2(un + i0), c = ld2(un + i0 + 2), d = ld2(un + i0 + 4);
+      const double2 a = LdgNC::ld2(un + i0 - 2), b = LdgNC::ld2(un + i0), c = LdgNC::ld2(un + i0 + 2), d = LdgNC::ld2(un + i0 + 4);
       const double v[8] = {a.x, a.y, b.x, b.y, c.x, c.y, d.x, d.y};
       double r[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) r[q] = axis_taps<H>(p.s[0], v + q + 2 - H, p.s0 * v[q + 2]);
+      for (int q = 0; q < 4; ++q) r[q] = axis_taps<H>(p.s[0], v + q + 2 - H, fma(p.s0, v[q + 2], p.zero));
 #pragma unroll
       for (int ax = 1; ax < 3; ++ax) {
         const int64_t st = ax == 1 ? sy : sz;
 #pragma unroll
         for (int j = -H; j <= H; ++j) {
           if (j == 0) continue;
-          const double2 e = ld2(un + i0 + j * st), f = ld2(un + i0 + j * st + 2);
+          const double2 e = LdgNC::ld2(un + i0 + j * st), f = LdgNC::ld2(un + i0 + j * st + 2);
           r[0] = fma(p.s[ax][j + H], e.x, r[0]);
           r[1] = fma(p.s[ax][j + H], e.y, r[1]);
           r[2] = fma(p.s[ax][j + H], f.x, r[2]);
@@ -170,7 +82,7 @@ __global__ void __launch_bounds__(256) forward_3d_kernel(const StepParams p, con
     } else {
       for (int q = 0; q < 4; ++q) {
         const int c[3] = {x0 + q, y, z};
-        out[i0 + q] = point_update<3, H>(p, un, n, i0 + q, c);
+        out[i0 + q] = point_update<3, H, LdgNC>(p, un, n, i0 + q, c);
       }
     }
   }
@@ -178,7 +90,8 @@ __global__ void __launch_bounds__(256) forward_3d_kernel(const StepParams p, con
 
 // Fallback for shapes the grouped kernels do not take (odd point counts, nx not a multiple of 4).
 template <int DIM, int H>
-__global__ void __launch_bounds__(256) forward_point_kernel(const StepParams p, const int64_t n) {
+__global__ void __launch_bounds__(256) forward_point_kernel(const StepParams p, const int64_t n_off, const int64_t *n_base) {
+  const int64_t n = n_off + (n_base ? *n_base : 0);
   const double *__restrict__ un = p.ring + (n % p.R) * p.ntot;
   double *__restrict__ out = p.ring + ((n + 1) % p.R) * p.ntot;
   const int nx = p.n[0], ny = DIM == 3 ? p.n[1] : 1;
@@ -190,13 +103,22 @@ __global__ void __launch_bounds__(256) forward_point_kernel(const StepParams p, 
       c[2] = (int)(yz / ny);
       c[1] = (int)(yz - (int64_t)c[2] * ny);
     }
-    out[i] = point_update<DIM, H>(p, un, n, i, c);
+    out[i] = point_update<DIM, H, LdgNC>(p, un, n, i, c);
   }
+}
+
+__global__ void add_steps_kernel(int64_t *n_base, int64_t v, int set) {
+  if (set) *n_base = v; else *n_base += v;
 }
 
 }  // namespace
 
-cudaError_t launch_forward_step(const StepParams &p, int64_t n, cudaStream_t st) {
+cudaError_t launch_step_counter(int64_t *n_base, int64_t v, bool set, cudaStream_t st) {
+  add_steps_kernel<<<1, 1, 0, st>>>(n_base, v, set ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_forward_step(const StepParams &p, int64_t n, const int64_t *n_base, cudaStream_t st) {
   const int threads = 256;
   const int max_blocks = 152 * 8 * 4;
   auto grid = [&](int64_t work) { int64_t b = (work + threads - 1) / threads; return (int)(b < max_blocks ? b : max_blocks); };
@@ -204,20 +126,20 @@ cudaError_t launch_forward_step(const StepParams &p, int64_t n, cudaStream_t st)
   if (p.dim == 1) {
     if (even) {
       const int64_t groups = (p.ntot + 3) / 4;
-      if (p.h == 1) forward_1d_kernel<1><<<grid(groups), threads, 0, st>>>(p, n);
-      else forward_1d_kernel<2><<<grid(groups), threads, 0, st>>>(p, n);
+      if (p.h == 1) forward_1d_kernel<1><<<grid(groups), threads, 0, st>>>(p, n, n_base);
+      else forward_1d_kernel<2><<<grid(groups), threads, 0, st>>>(p, n, n_base);
     } else {
-      if (p.h == 1) forward_point_kernel<1, 1><<<grid(p.ntot), threads, 0, st>>>(p, n);
-      else forward_point_kernel<1, 2><<<grid(p.ntot), threads, 0, st>>>(p, n);
+      if (p.h == 1) forward_point_kernel<1, 1><<<grid(p.ntot), threads, 0, st>>>(p, n, n_base);
+      else forward_point_kernel<1, 2><<<grid(p.ntot), threads, 0, st>>>(p, n, n_base);
     }
   } else {
     if (p.n[0] % 4 == 0 && even) {
       const int64_t groups = p.ntot / 4;
-      if (p.h == 1) forward_3d_kernel<1><<<grid(groups), threads, 0, st>>>(p, n);
-      else forward_3d_kernel<2><<<grid(groups), threads, 0, st>>>(p, n);
+      if (p.h == 1) forward_3d_kernel<1><<<grid(groups), threads, 0, st>>>(p, n, n_base);
+      else forward_3d_kernel<2><<<grid(groups), threads, 0, st>>>(p, n, n_base);
     } else {
-      if (p.h == 1) forward_point_kernel<3, 1><<<grid(p.ntot), threads, 0, st>>>(p, n);
-      else forward_point_kernel<3, 2><<<grid(p.ntot), threads, 0, st>>>(p, n);
+      if (p.h == 1) forward_point_kernel<3, 1><<<grid(p.ntot), threads, 0, st>>>(p, n, n_base);
+      else forward_point_kernel<3, 2><<<grid(p.ntot), threads, 0, st>>>(p, n, n_base);
     }
   }
   return cudaGetLastError();

@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include "../../include/at.h"
+
 #define AT_MAX_L 8
 #define AT_MAX_T 4
 #define AT_MAX_H 2
@@ -28,6 +30,7 @@ struct StepParams {
   int32_t use_thr;        // thresholds given (else uniform bins)
   uint64_t seed;
   uint64_t thr[AT_MAX_L]; // L-1 bin edges on the 32-bit word
+  double zero;            // +0.0, kept opaque so the compiler issues an FMA rather than a multiply
   double s0;              // merged centre coefficient: 1 + dt sum_a (-c_a cd1_0/dx_a + alpha cd2_0/dx_a^2)
   double s[3][2 * AT_MAX_H + 1];  // merged off-centre coefficients per axis (index j+h)
   double w[AT_MAX_L][AT_MAX_T];   // halo extrapolation weights w[k][m] of level n-k-m
@@ -45,8 +48,16 @@ struct WaveParams {
   double kappa[3][AT_MAX_MODES];
 };
 
+// Validate cfg and fill the step parameters (merged taps, extrapolation weights, delay process) for a problem
+// whose ring starts at ring_dev; log_dev may be null.  Host only, no CUDA call.
+int at_prepare_params(const at_config_t *cfg, double *ring_dev, uint8_t *log_dev, StepParams *out);
+
 // Launchers (return cudaGetLastError()).
-cudaError_t launch_forward_step(const StepParams &p, int64_t n, cudaStream_t st);
+// One forward step n = n_off + (*n_base if n_base else 0): reading the base from device memory lets a
+// captured graph of consecutive steps be replayed at any step.
+cudaError_t launch_forward_step(const StepParams &p, int64_t n_off, const int64_t *n_base, cudaStream_t st);
+// *n_base = v (set) or *n_base += v.
+cudaError_t launch_step_counter(int64_t *n_base, int64_t v, bool set, cudaStream_t st);
 cudaError_t launch_wave_field(const WaveParams &w, double t, double *tables, double *out, cudaStream_t st);
 cudaError_t launch_error_stats(const WaveParams &w, const StepParams &p, const double *u, double t,
                                double *tables, double *partials, double *result, cudaStream_t st);

@@ -7,19 +7,27 @@
 //                      sum E, sum E^2 on I_I and I_B, sum u_a^2, |I_I|, |I_B|.  Fixed grid of
 //                      AT_STAT_BLOCKS blocks, per-block partials, then one block reduces them in a fixed
 //                      order, so the result is deterministic.
+#include <cmath>
+
 #include "internal.h"
 
 namespace {
 
+// w.amp holds A exp(-alpha kappa^2 t) for the time t of the launch (scaled on the host).
 __device__ __forceinline__ double axis_sum(const WaveParams &w, int a, int i, double t) {
   const double x = (double)i * w.dx[a];
+  const double shift = w.c[a] * t;
   double s = 0.0;
-  for (int q = 0; q < w.nmodes; ++q) {
-    const double kap = w.kappa[a][q];
-    const double decay = t == 0.0 ? 1.0 : exp(-w.alpha * kap * kap * t);
-    s += w.amp[a][q] * decay * sin(kap * (x - w.c[a] * t) + w.phase[a][q]);
-  }
+  for (int q = 0; q < w.nmodes; ++q) s += w.amp[a][q] * sin(w.kappa[a][q] * (x - shift) + w.phase[a][q]);
   return s;
+}
+
+WaveParams at_time(const WaveParams &w0, double t) {
+  WaveParams w = w0;
+  for (int a = 0; a < w.dim; ++a)
+    for (int q = 0; q < w.nmodes; ++q)
+      if (t != 0.0) w.amp[a][q] = w0.amp[a][q] * std::exp(-w0.alpha * w0.kappa[a][q] * w0.kappa[a][q] * t);
+  return w;
 }
 
 __global__ void axis_table_kernel(const WaveParams w, double t, double *tables) {
@@ -113,7 +121,8 @@ __global__ void __launch_bounds__(AT_STAT_BLOCKS) stats_final_kernel(const doubl
 
 }  // namespace
 
-cudaError_t launch_wave_field(const WaveParams &w, double t, double *tables, double *out, cudaStream_t st) {
+cudaError_t launch_wave_field(const WaveParams &w0, double t, double *tables, double *out, cudaStream_t st) {
+  const WaveParams w = at_time(w0, t);
   if (w.dim == 1) {
     const int64_t blocks = (w.n[0] + 255) / 256;
     field_1d_kernel<<<(int)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, st>>>(w, t, out);
@@ -126,8 +135,9 @@ cudaError_t launch_wave_field(const WaveParams &w, double t, double *tables, dou
   return cudaGetLastError();
 }
 
-cudaError_t launch_error_stats(const WaveParams &w, const StepParams &p, const double *u, double t, double *tables,
+cudaError_t launch_error_stats(const WaveParams &w0, const StepParams &p, const double *u, double t, double *tables,
                                double *partials, double *result, cudaStream_t st) {
+  const WaveParams w = at_time(w0, t);
   if (w.dim == 1) {
     stats_partial_kernel<1><<<AT_STAT_BLOCKS, 256, 0, st>>>(w, p, u, t, tables, partials);
   } else {

@@ -68,3 +68,57 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+class Ensemble:
+    """Many independent 1D realizations advanced in one persistent, graph-captured launch."""
+
+    def __init__(self, specs, nsteps: int, log: bool = False, threads: int = 0, ctas_per_sm: int = 0,
+                 device: str | torch.device = "cuda", stream=None):
+        B.load()
+        self.cfgs = [B.Config(s) for s in specs]
+        self.nsteps = int(nsteps)
+        self.device = torch.device(device)
+        ring_len, log_len = B.at_ensemble_sizes(self.cfgs, self.nsteps)
+        self.ring = torch.empty(ring_len, dtype=torch.float64, device=self.device)
+        self.log = torch.zeros(log_len, dtype=torch.uint8, device=self.device) if log else None
+        self.R = [B.at_ring_slots(c) for c in self.cfgs]
+        self.sides = [B.at_num_sides(c) for c in self.cfgs]
+        self.ring_off, self.log_off = [], []
+        ro = lo = 0
+        for c, R, nb in zip(self.cfgs, self.R, self.sides):
+            self.ring_off.append(ro)
+            self.log_off.append(lo)
+            ro += R * c.ntot
+            lo += self.nsteps * nb
+        self.h = B.at_ensemble_create(self.cfgs, self.nsteps, self.ring, self.log, threads, ctas_per_sm, stream)
+
+    def run(self) -> None:
+        B.at_ensemble_run(self.h)
+
+    def stats(self):
+        return B.at_ensemble_stats(self.h, len(self.cfgs))
+
+    def field(self, r: int) -> torch.Tensor:
+        """Member r's field at its final step (valid after run())."""
+        c = self.cfgs[r]
+        slot = self.nsteps % self.R[r]
+        o = self.ring_off[r] + slot * c.ntot
+        return self.ring[o:o + c.ntot]
+
+    def delays(self, r: int) -> torch.Tensor:
+        if self.log is None:
+            raise RuntimeError("ensemble was created without a delay log")
+        o = self.log_off[r]
+        return self.log[o:o + self.nsteps * self.sides[r]].view(self.nsteps, self.sides[r])
+
+    def close(self) -> None:
+        if self.h is not None:
+            B.at_ensemble_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
