@@ -103,7 +103,7 @@ extern "C" int at_delay(uint64_t seed, int64_t step, int64_t side, int32_t L, co
   return atfd::delay_draw(seed, (uint32_t)step, (uint32_t)side, L, thresholds_host);
 }
 
-int at_prepare_params(const at_config_t *cfg, double *ring_dev, uint8_t *log_dev, StepParams *out) {
+int at_prepare_params(const at_config_t *cfg, double *ring_dev, uint8_t *log_dev, int64_t log_steps, StepParams *out) {
   int rc = check_config(cfg);
   if (rc) return rc;
   const int T = time_width(cfg);
@@ -116,6 +116,7 @@ int at_prepare_params(const at_config_t *cfg, double *ring_dev, uint8_t *log_dev
   std::memset(&p, 0, sizeof(p));
   p.ring = ring_dev;
   p.log = log_dev;
+  p.log_steps = log_dev ? log_steps : 0;
   p.ntot = cfg->n[0] * cfg->n[1] * cfg->n[2];
   p.nb = sides_of(cfg);
   p.dim = cfg->dim; p.h = h; p.T = T; p.R = cfg->L + T; p.L = cfg->L; p.scheme = cfg->scheme;
@@ -156,7 +157,7 @@ extern "C" int at_init(const at_config_t *cfg, double *ring_dev, int64_t ring_le
 
   at_handle *hd = new (std::nothrow) at_handle();
   if (!hd) return fail(AT_ERR_ARG, "out of host memory");
-  if ((rc = at_prepare_params(cfg, ring_dev, log_steps > 0 ? log_dev : nullptr, &hd->sp)) != AT_OK) {
+  if ((rc = at_prepare_params(cfg, ring_dev, log_steps > 0 ? log_dev : nullptr, log_steps, &hd->sp)) != AT_OK) {
     delete hd;
     return rc;
   }
@@ -185,18 +186,21 @@ extern "C" int at_init(const at_config_t *cfg, double *ring_dev, int64_t ring_le
   }
 
   const size_t n_tables = (size_t)(cfg->n[0] + cfg->n[1] + cfg->n[2]);
-  const size_t bytes = 512 + sizeof(double) * ((size_t)AT_STAT_BLOCKS * AT_STAT_FIELDS + 16 + n_tables);
+  const size_t keff_bytes = (size_t)(2 * p.nb + 255) / 256 * 256;
+  const size_t bytes = 512 + keff_bytes + sizeof(double) * ((size_t)AT_STAT_BLOCKS * AT_STAT_FIELDS + 16 + n_tables);
   cudaError_t e = cudaMalloc(&hd->scratch, bytes);
   if (e != cudaSuccess) { delete hd; return cuda_fail(e, "at_init: cudaMalloc"); }
   char *base = (char *)hd->scratch;
   hd->d_status = (int32_t *)base;
   hd->d_step = (int64_t *)(base + 256);
-  hd->d_partials = (double *)(base + 512);
+  p.keff = (uint8_t *)(base + 512);
+  hd->d_partials = (double *)(base + 512 + keff_bytes);
   hd->d_result = hd->d_partials + (size_t)AT_STAT_BLOCKS * AT_STAT_FIELDS;
   hd->d_tables = hd->d_result + 16;
   p.status = hd->d_status;
   if ((e = cudaMemsetAsync(hd->d_status, 0, sizeof(int32_t), hd->stream)) != cudaSuccess ||
-      (e = launch_wave_field(w, 0.0, hd->d_tables, ring_dev, hd->stream)) != cudaSuccess) {
+      (e = launch_wave_field(w, 0.0, hd->d_tables, ring_dev, hd->stream)) != cudaSuccess ||
+      (e = launch_draw_delays(p, 0, hd->stream)) != cudaSuccess) {
     cudaFree(hd->scratch);
     delete hd;
     return cuda_fail(e, "at_init: initial condition");
@@ -260,6 +264,7 @@ extern "C" int at_reset(at_handle_t *hd, const double *u0_dev) {
                         hd->stream);
   else
     e = launch_wave_field(hd->wp, 0.0, hd->d_tables, hd->sp.ring, hd->stream);
+  if (e == cudaSuccess) e = launch_draw_delays(hd->sp, 0, hd->stream);
   if (e != cudaSuccess) return cuda_fail(e, "at_reset");
   hd->step = 0;
   return AT_OK;

@@ -46,24 +46,31 @@ __device__ double wave_1d(const MemberParams &m, const double *amp, double shift
   return s;
 }
 
+// One realization, all steps: the delays of step n+1 are drawn (into the other half of the shared delay
+// buffer) while step n is computed; one barrier per step publishes both the new level and the new delays.
 template <int H>
-__device__ void run_member(const MemberParams &m, int64_t nsteps) {
-  const StepParams &p = m.p;
+__device__ void run_member(const StepParams &p, uint8_t *keff_sh, int64_t nsteps) {
   const int groups = p.n[0] >> 2;
+  atfd::draw_sides(p, 0, threadIdx.x, blockDim.x, keff_sh);
+  __syncthreads();
   for (int64_t n = 0; n < nsteps; ++n) {
     const double *un = p.ring + (n % p.R) * p.ntot;
     double *out = p.ring + ((n + 1) % p.R) * p.ntot;
-    for (int g = threadIdx.x; g < groups; g += blockDim.x) atfd::group_1d<H, atfd::LdCoherent>(p, un, out, n, g << 2);
+    if (n + 1 < nsteps) atfd::draw_sides(p, n + 1, threadIdx.x, blockDim.x, keff_sh + ((n + 1) & 1) * p.nb);
+    const uint8_t *keff = keff_sh + (n & 1) * p.nb;
+    for (int g = threadIdx.x; g < groups; g += blockDim.x)
+      atfd::group_update<1, H, atfd::LdCoherent>(p, keff, un, out, n, g << 2, 0, 0);
     __syncthreads();
   }
 }
 
-__global__ void __launch_bounds__(256) ensemble_kernel(const MemberParams *__restrict__ members,
+__global__ void __launch_bounds__(256, 4) ensemble_kernel(const MemberParams *__restrict__ members,
                                                        const int32_t *__restrict__ order, int32_t count, int64_t nsteps,
                                                        int32_t *counter, double *__restrict__ member_stats) {
   __shared__ MemberParams m;
   __shared__ int32_t item;
   __shared__ double red[kStatFields][256];
+  extern __shared__ uint8_t keff_sh[];  // two buffers of the largest member's side count
   for (;;) {
     if (threadIdx.x == 0) item = atomicAdd(counter, 1);
     __syncthreads();
@@ -79,8 +86,8 @@ __global__ void __launch_bounds__(256) ensemble_kernel(const MemberParams *__res
     const int N = m.p.n[0];
     for (int i = threadIdx.x; i < N; i += blockDim.x) m.p.ring[i] = wave_1d(m, m.amp, 0.0, i);
     __syncthreads();
-    if (m.p.h == 1) run_member<1>(m, nsteps);
-    else run_member<2>(m, nsteps);
+    if (m.p.h == 1) run_member<1>(m.p, keff_sh, nsteps);
+    else run_member<2>(m.p, keff_sh, nsteps);
     // statistics of E = U^nsteps - u_a(x, nsteps dt), as in the single-problem reduction
     const double *u = m.p.ring + (nsteps % m.p.R) * m.p.ntot;
     double acc[kStatFields];
@@ -173,6 +180,7 @@ struct at_ensemble {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int threads = 256, blocks = 0;
+  size_t dyn_smem = 0;
 };
 
 // Ring and log sizes (in doubles and bytes) the members need, laid out member after member.
@@ -214,7 +222,7 @@ extern "C" int at_ensemble_create(const at_config_t *members, int32_t count, int
   for (auto &kv : groups) kv.second = gi++;
   at_ensemble *e = new (std::nothrow) at_ensemble();
   if (!e) return fail(AT_ERR_ARG, "out of host memory");
-  int64_t ring_off = 0, log_off = 0;
+  int64_t ring_off = 0, log_off = 0, max_nb = 1;
   for (int r = 0; r < count; ++r) {
     const at_config_t &c = members[r];
     // merged taps, extrapolation weights and delay parameters exactly as for a single problem
@@ -224,7 +232,8 @@ extern "C" int at_ensemble_create(const at_config_t *members, int32_t count, int
     at_num_sides(&c, &nb);
     MemberParams &m = host[r];
     std::memset(&m, 0, sizeof(m));
-    rc = at_prepare_params(&c, ring_dev + ring_off, log_dev ? log_dev + log_off : nullptr, &m.p);
+    rc = at_prepare_params(&c, ring_dev + ring_off, log_dev ? log_dev + log_off : nullptr, nsteps, &m.p);
+    max_nb = std::max<int64_t>(max_nb, nb);
     if (rc) { delete e; return rc; }
     m.nmodes = c.nmodes;
     m.dx = kTwoPi / (double)c.n[0];
@@ -273,7 +282,13 @@ extern "C" int at_ensemble_create(const at_config_t *members, int32_t count, int
   int dev = 0, sms = 0, fit = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, ensemble_kernel, threads, 0);
+  const size_t dyn_smem = (size_t)(2 * max_nb + 15) / 16 * 16;
+  if (dyn_smem > 48 * 1024) {
+    delete e;
+    return fail(AT_ERR_ARG, "at_ensemble_create: a member has too many PE sides");
+  }
+  e->dyn_smem = dyn_smem;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, ensemble_kernel, threads, dyn_smem);
   if (ctas_per_sm <= 0) ctas_per_sm = fit;
   if (ctas_per_sm > fit) ctas_per_sm = fit;
   if (ctas_per_sm < 1) ctas_per_sm = 1;
@@ -288,7 +303,7 @@ extern "C" int at_ensemble_create(const at_config_t *members, int32_t count, int
   err = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   if (err == cudaSuccess) {
     reset_counter<<<1, 1, 0, cap>>>(e->d_counter);
-    ensemble_kernel<<<e->blocks, threads, 0, cap>>>(e->d_members, e->d_order, count, nsteps, e->d_counter,
+    ensemble_kernel<<<e->blocks, threads, e->dyn_smem, cap>>>(e->d_members, e->d_order, count, nsteps, e->d_counter,
                                                     e->d_member_stats);
     summary_kernel<<<1, 128, 0, cap>>>(e->d_member_stats, e->d_members, count, e->ngroups, e->d_summary);
     err = cudaStreamEndCapture(cap, &e->graph);

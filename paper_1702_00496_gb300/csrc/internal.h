@@ -19,6 +19,8 @@ void at_internal_set_error(const char *msg);
 struct StepParams {
   double *ring;           // R slots of ntot doubles; level m in slot m mod R
   uint8_t *log;           // raw delays, step-major [log_steps][nb], or nullptr
+  uint8_t *keff;          // effective delays, two buffers of nb: step n uses keff + (n & 1) * nb
+  int64_t log_steps;      // rows of the log
   int32_t *status;        // sticky device status word
   int64_t ntot;           // points
   int64_t nb;             // PE sides, 2 * dim * prod(pe)
@@ -49,8 +51,8 @@ struct WaveParams {
 };
 
 // Validate cfg and fill the step parameters (merged taps, extrapolation weights, delay process) for a problem
-// whose ring starts at ring_dev; log_dev may be null.  Host only, no CUDA call.
-int at_prepare_params(const at_config_t *cfg, double *ring_dev, uint8_t *log_dev, StepParams *out);
+// whose ring starts at ring_dev; log_dev (log_steps rows) may be null.  The caller sets keff.  Host only.
+int at_prepare_params(const at_config_t *cfg, double *ring_dev, uint8_t *log_dev, int64_t log_steps, StepParams *out);
 
 // Launchers (return cudaGetLastError()).
 // One forward step n = n_off + (*n_base if n_base else 0): reading the base from device memory lets a
@@ -58,6 +60,8 @@ int at_prepare_params(const at_config_t *cfg, double *ring_dev, uint8_t *log_dev
 cudaError_t launch_forward_step(const StepParams &p, int64_t n_off, const int64_t *n_base, cudaStream_t st);
 // *n_base = v (set) or *n_base += v.
 cudaError_t launch_step_counter(int64_t *n_base, int64_t v, bool set, cudaStream_t st);
+// Draw the delays of step n into keff + (n & 1) * nb (and log row n): the set-up before a first step.
+cudaError_t launch_draw_delays(const StepParams &p, int64_t n, cudaStream_t st);
 cudaError_t launch_wave_field(const WaveParams &w, double t, double *tables, double *out, cudaStream_t st);
 cudaError_t launch_error_stats(const WaveParams &w, const StepParams &p, const double *u, double t,
                                double *tables, double *partials, double *result, cudaStream_t st);

@@ -1,5 +1,17 @@
-// stencil.cuh -- device building blocks of the fused AT step, shared by the per-step kernels (fwd.cu) and
-// the persistent ensemble kernel (ensemble.cu).  See fwd.cu for the method and its citations.
+// stencil.cuh -- device building blocks of the fused AT step, shared by the per-step kernels (fwd.cu) and the
+// persistent ensemble kernel (ensemble.cu).
+//
+// A thread updates a group of four consecutive x points (x0 a multiple of 4) of one (y, z) row.  It loads
+// the level-n values its merged stencil needs -- the x window x0-2 .. x0+5 and, in 3D, the four values of
+// rows y +- j and z +- j -- and replaces every value that lies outside the group's PE (a buffer point,
+// Sec. 2) by the halo value its PE side sees:
+//     u~ = sum_{m<T} w_m(k) U^{n-k-m}     (k: that side's effective delay for step n; k = 0 keeps U^n)
+// Groups never straddle a PE (PE widths are multiples of 4 on these paths), so each loaded value is either
+// inside the PE or a buffer point of exactly one side.  The update is then the same chain of FMAs for every
+// group:  r = fma(s0, u_i, +0), the taps of axis x in offset order, then axis y, then axis z.
+//
+// Delays are drawn once per PE side and step (Philox, Sec. 5.1) by a draw pass into a small array of
+// effective delays (uint8, clamped so that no level before 0 is read); the raw draw goes to the delay log.
 #pragma once
 #include "internal.h"
 #include "philox.cuh"
@@ -18,30 +30,123 @@ struct LdCoherent {
   static __device__ __forceinline__ double2 ld2(const double *p) { return *reinterpret_cast<const double2 *>(p); }
 };
 
-
 __device__ __forceinline__ int wrap_coord(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-// Halo value of `cell` seen across a PE side with effective delay k (T successive levels).
+// Draw the delays of step n for sides b = first, first+stride, ...: effective delay to keff[b], raw draw to
+// the log row n (when the log holds that row).
+__device__ __forceinline__ void draw_sides(const StepParams &p, int64_t n, int64_t first, int64_t stride,
+                                           uint8_t *keff) {
+  for (int64_t b = first; b < p.nb; b += stride) {
+    int raw = 0;
+    if (p.scheme != 0) raw = delay_draw(p.seed, (uint32_t)n, (uint32_t)b, p.L, p.use_thr ? p.thr : nullptr);
+    keff[b] = (uint8_t)delay_clamp(raw, n, p.T);
+    if (p.log != nullptr && n < p.log_steps) p.log[n * p.nb + b] = (uint8_t)raw;
+  }
+}
+
+// Halo value of `cell` seen across a PE side with effective delay k >= 1 (T successive levels).
 template <class LD>
 __device__ __forceinline__ double halo_value(const StepParams &p, int64_t cell, int64_t n, int k) {
-  if (k == 0) return LD::ld(p.ring + (n % p.R) * p.ntot + cell);
-  double acc = 0.0;
+  double acc = fma(p.w[k][0], LD::ld(p.ring + ((n - k) % p.R) * p.ntot + cell), p.zero);
 #pragma unroll
-  for (int m = 0; m < AT_MAX_T; ++m) {
+  for (int m = 1; m < AT_MAX_T; ++m) {
     if (m >= p.T) break;
-    const int64_t lev = n - k - m;
-    acc = fma(p.w[k][m], LD::ld(p.ring + (lev % p.R) * p.ntot + cell), acc);
+    acc = fma(p.w[k][m], LD::ld(p.ring + ((n - k - m) % p.R) * p.ntot + cell), acc);
   }
   return acc;
 }
 
-// Updated value of point i (linear index) with coordinates c: the general path, used for points within h
-// of a PE edge, points whose stencil wraps around the periodic domain, and ragged groups.
+// Side index of face (axis a, lo/hi) of the PE with index (px, py, pz).
+template <int DIM>
+__device__ __forceinline__ int64_t side_of(const StepParams &p, const int pidx[3], int a, int hi) {
+  int64_t pe = pidx[0];
+  if (DIM == 3) pe = ((int64_t)pidx[2] * p.pe[1] + pidx[1]) * p.pe[0] + pidx[0];
+  return 2 * (int64_t)DIM * pe + 2 * a + hi;
+}
+
+// Update the four points x0..x0+3 of row (y, z); requires n[0] % 4 == 0 (1D: the group count covers N) and a
+// 16-byte aligned slot.  keff: effective delays of step n.
 template <int DIM, int H, class LD>
-__device__ __noinline__ double point_update(const StepParams &p, const double *__restrict__ un, int64_t n, int64_t i,
-                                            const int c[3]) {
+__device__ __forceinline__ void group_update(const StepParams &p, const uint8_t *__restrict__ keff,
+                                             const double *__restrict__ un, double *__restrict__ out, int64_t n,
+                                             int x0, int y, int z) {
+  const int nx = p.n[0];
+  const int64_t row = DIM == 3 ? ((int64_t)z * p.n[1] + y) * nx : 0;
+  const int64_t i0 = row + x0;
+  int pidx[3] = {x0 / p.S[0], 0, 0}, pos[3] = {0, 0, 0};
+  pos[0] = x0 - pidx[0] * p.S[0];
+  if (DIM == 3) {
+    pidx[1] = y / p.S[1]; pos[1] = y - pidx[1] * p.S[1];
+    pidx[2] = z / p.S[2]; pos[2] = z - pidx[2] * p.S[2];
+  }
+  // x window: cells x0-2 .. x0+5 of the row
+  double v[8];
+  if (x0 >= 2 && x0 + 6 <= nx) {
+    const double2 a = LD::ld2(un + i0 - 2), b = LD::ld2(un + i0), c = LD::ld2(un + i0 + 2), d = LD::ld2(un + i0 + 4);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y; v[6] = d.x; v[7] = d.y;
+  } else {
+#pragma unroll
+    for (int t = 0; t < 8; ++t) v[t] = LD::ld(un + row + wrap_coord(x0 - 2 + t, nx));
+  }
+  if (p.use_pe[0] && (pos[0] < H || pos[0] + 3 >= p.S[0] - H)) {
+    const int kl = keff[side_of<DIM>(p, pidx, 0, 0)], kr = keff[side_of<DIM>(p, pidx, 0, 1)];
+#pragma unroll
+    for (int t = 2 - H; t <= 5 + H; ++t) {
+      const int rel = pos[0] - 2 + t;
+      const int k = rel < 0 ? kl : (rel >= p.S[0] ? kr : 0);
+      if (k > 0) v[t] = halo_value<LD>(p, row + wrap_coord(x0 - 2 + t, nx), n, k);
+    }
+  }
+  double r[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    double acc = fma(p.s0, v[q + 2], p.zero);
+#pragma unroll
+    for (int j = -H; j <= H; ++j)
+      if (j != 0) acc = fma(p.s[0][j + H], v[q + 2 + j], acc);
+    r[q] = acc;
+  }
+  if (DIM == 3) {
+#pragma unroll
+    for (int a = 1; a < 3; ++a) {
+      const int c = a == 1 ? y : z, na = p.n[a];
+      const int64_t st = a == 1 ? (int64_t)nx : (int64_t)nx * p.n[1];
+      const bool edge = p.use_pe[a] && (pos[a] < H || pos[a] >= p.S[a] - H);
+      int kl = 0, kr = 0;
+      if (edge) {
+        kl = keff[side_of<DIM>(p, pidx, a, 0)];
+        kr = keff[side_of<DIM>(p, pidx, a, 1)];
+      }
+#pragma unroll
+      for (int j = -H; j <= H; ++j) {
+        if (j == 0) continue;
+        const int cj = wrap_coord(c + j, na);
+        const int64_t base = i0 + (int64_t)(cj - c) * st;
+        const int k = !edge ? 0 : (pos[a] + j < 0 ? kl : (pos[a] + j >= p.S[a] ? kr : 0));
+        double w[4];
+        if (k > 0) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) w[q] = halo_value<LD>(p, base + q, n, k);
+        } else {
+          const double2 e = LD::ld2(un + base), f = LD::ld2(un + base + 2);
+          w[0] = e.x; w[1] = e.y; w[2] = f.x; w[3] = f.y;
+        }
+        const double s = p.s[a][j + H];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) r[q] = fma(s, w[q], r[q]);
+      }
+    }
+  }
+  reinterpret_cast<double2 *>(out + i0)[0] = make_double2(r[0], r[1]);
+  reinterpret_cast<double2 *>(out + i0)[1] = make_double2(r[2], r[3]);
+}
+
+// One point of any shape (the fallback for point counts that are not a multiple of 4), same arithmetic.
+template <int DIM, int H, class LD>
+__device__ double point_update(const StepParams &p, const uint8_t *__restrict__ keff, const double *__restrict__ un,
+                               int64_t n, int64_t i, const int c[3]) {
   const int64_t stride[3] = {1, (int64_t)p.n[0], (int64_t)p.n[0] * p.n[1]};
-  int pos[3], pidx[3];
+  int pos[3] = {0, 0, 0}, pidx[3] = {0, 0, 0};
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
     pidx[a] = c[a] / p.S[a];
@@ -50,73 +155,20 @@ __device__ __noinline__ double point_update(const StepParams &p, const double *_
   double acc = fma(p.s0, LD::ld(un + i), p.zero);
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
-    const int S = p.S[a];
-    const bool lo = pos[a] < H, hi = pos[a] >= S - H;
-    const bool edge = p.use_pe[a] && (lo || hi);
-    int k = 0;
-    if (lo || hi) {
-      int pe_id = pidx[0];
-      if (DIM == 3) pe_id = (pidx[2] * p.pe[1] + pidx[1]) * p.pe[0] + pidx[0];
-      const int64_t side = 2 * (int64_t)DIM * pe_id + 2 * a + (lo ? 0 : 1);
-      int raw = 0;
-      if (p.scheme != 0) raw = atfd::delay_draw(p.seed, (uint32_t)n, (uint32_t)side, p.L, p.use_thr ? p.thr : nullptr);
-      k = atfd::delay_clamp(raw, n, p.T);
-      // the log writer of this side: the edge point of the side with the other coordinates at the PE origin
-      bool writer = lo ? (pos[a] == 0) : (pos[a] == S - 1);
-#pragma unroll
-      for (int b = 0; b < DIM; ++b)
-        if (b != a && pos[b] != 0) writer = false;
-      if (writer && p.log != nullptr) p.log[n * p.nb + side] = (uint8_t)raw;
-    }
+    const bool edge = p.use_pe[a] && (pos[a] < H || pos[a] >= p.S[a] - H);
 #pragma unroll
     for (int j = -H; j <= H; ++j) {
       if (j == 0) continue;
       const int cj = wrap_coord(c[a] + j, p.n[a]);
       const int64_t cell = i + (int64_t)(cj - c[a]) * stride[a];
-      double v;
-      if (edge && (pos[a] + j < 0 || pos[a] + j >= S))
-        v = halo_value<LD>(p, cell, n, k);
-      else
-        v = LD::ld(un + cell);
+      int k = 0;
+      if (edge && pos[a] + j < 0) k = keff[side_of<DIM>(p, pidx, a, 0)];
+      if (edge && pos[a] + j >= p.S[a]) k = keff[side_of<DIM>(p, pidx, a, 1)];
+      const double v = k > 0 ? halo_value<LD>(p, cell, n, k) : LD::ld(un + cell);
       acc = fma(p.s[a][j + H], v, acc);
     }
   }
   return acc;
-}
-
-
-// Merged stencil of one point from the values of its line along one axis (v[H + j] = u_{i+j}).
-template <int H>
-__device__ __forceinline__ double axis_taps(const double (&s)[2 * AT_MAX_H + 1], const double *v, double acc) {
-#pragma unroll
-  for (int j = -H; j <= H; ++j)
-    if (j != 0) acc = fma(s[j + H], v[H + j], acc);
-  return acc;
-}
-
-// One group of four consecutive 1D points starting at i0 (a multiple of 4): the straight FMA path with four
-// independent chains when the group lies inside one PE, at least h from its edges and from the ends of the
-// domain; otherwise the general path point by point.  Requires N even and a 16-byte aligned slot.
-template <int H, class LD>
-__device__ __forceinline__ void group_1d(const StepParams &p, const double *__restrict__ un, double *__restrict__ out,
-                                         int64_t n, int i0) {
-  const int N = p.n[0], S = p.S[0];
-  const int pos0 = i0 % S;
-  const bool inside = (i0 >= 2) && (i0 + 6 <= N) && (!p.use_pe[0] || (pos0 >= H && pos0 + 3 < S - H));
-  if (inside) {
-    const double2 a = LD::ld2(un + i0 - 2), b = LD::ld2(un + i0), c = LD::ld2(un + i0 + 2), d = LD::ld2(un + i0 + 4);
-    const double v[8] = {a.x, a.y, b.x, b.y, c.x, c.y, d.x, d.y};  // u[i0-2 .. i0+5]
-    double r[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) r[q] = axis_taps<H>(p.s[0], v + q + 2 - H, fma(p.s0, v[q + 2], p.zero));
-    reinterpret_cast<double2 *>(out + i0)[0] = make_double2(r[0], r[1]);
-    reinterpret_cast<double2 *>(out + i0)[1] = make_double2(r[2], r[3]);
-  } else {
-    for (int q = 0; q < 4 && i0 + q < N; ++q) {
-      const int c[3] = {i0 + q, 0, 0};
-      out[i0 + q] = point_update<1, H, LD>(p, un, n, i0 + q, c);
-    }
-  }
 }
 
 }  // namespace atfd
