@@ -157,7 +157,11 @@ def run_ensemble(args, rank: int, world: int, local: int):
         s["seed"] = int(s["seed"]) + 100000 * rank
     updates = sum(s["n"][0] for s in specs) * T
     stream = torch.cuda.current_stream()
-    ens = Ensemble(specs, T, threads=args.threads, ctas_per_sm=args.ctas_per_sm, device=f"cuda:{local}", stream=stream)
+    threads, ctas = args.threads, args.ctas_per_sm
+    if threads == 0:
+        from paper_1702_00496_gb300 import autotune
+        threads, ctas = autotune.tune_ensemble(specs, T, device=f"cuda:{local}", use_cache=not args.retune)
+    ens = Ensemble(specs, T, threads=threads, ctas_per_sm=ctas, device=f"cuda:{local}", stream=stream)
     for _ in range(args.warmup):
         ens.run()
     torch.cuda.synchronize()
@@ -201,7 +205,8 @@ def run_ensemble(args, rank: int, world: int, local: int):
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": "ensemble", "members": len(specs), "time_steps": T,
-                           "total_points": sum(s["n"][0] for s in specs)},
+                           "total_points": sum(s["n"][0] for s in specs),
+                           "launch": {"threads": threads, "ctas_per_sm": ctas}},
                 "one_at_a_time_ms": one, "speedup_vs_one_at_a_time": (one / ms) if one else None,
                 "groups": groups, "clocks": clocks, "gpu_launches": args.steps * 3}
         print(json.dumps(line), flush=True)
@@ -221,6 +226,7 @@ def main():
     ap.add_argument("--threads", type=int, default=0, help="ensemble: threads per CTA (0: library default)")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="ensemble: CTAs per SM (0: occupancy limit)")
     ap.add_argument("--skip-one-at-a-time", action="store_true")
+    ap.add_argument("--retune", action="store_true", help="ignore the autotuner cache")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -249,6 +255,8 @@ def main():
         ntot *= x
     stream = torch.cuda.current_stream()
     solver = Solver(spec, log_steps=0, device=f"cuda:{local}", stream=stream)
+    from paper_1702_00496_gb300 import autotune
+    launch = autotune.tune_forward(solver, spec, use_cache=not args.retune)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device=f"cuda:{local}")  # 512 MiB > L2
     kern_ev = []
 
@@ -351,7 +359,7 @@ def main():
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": args.workload, "points": ntot, "pes": spec["pe"][0], "order": spec["order"],
                            "L": spec["L"], "time_steps_per_step": T, "l2": "flushed (512 MiB write) each step",
-                           "replicas": world},
+                           "replicas": world, "launch": {"threads": launch[0], "blocks_per_sm": launch[1]}},
                 "e2e": {"value": e2e_value, "unit": "updates/s", "h2d_bytes_per_step": 8 * ntot,
                         "d2h_bytes_per_step": 8 * ntot + 8 * 9},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,

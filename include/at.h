@@ -139,6 +139,11 @@ int at_step(at_handle_t *hd, int64_t nsteps);
  * replays from step 0.  Enqueued on the handle's stream.  Errors: AT_ERR_ARG, AT_ERR_CUDA. */
 int at_reset(at_handle_t *hd, const double *u0_dev);
 
+/* Launch shape of the per-step kernel for the following at_step calls: threads per block (128, 256 or 512)
+ * and a cap of blocks_per_sm (1..64) blocks per SM on its grid-stride loop.  Defaults 256 and 32.  Waits
+ * for the stream and drops the captured step graph.  Used by the autotuner.  Errors: AT_ERR_ARG. */
+int at_set_launch(at_handle_t *hd, int32_t threads, int32_t blocks_per_sm);
+
 /* Wait for the handle's stream and return its sticky device status (AT_OK, AT_ERR_BOUNDS, ...). Blocks. */
 int at_sync(at_handle_t *hd);
 
@@ -169,8 +174,8 @@ int at_destroy(at_handle_t *hd);
  * at_ensemble_sizes: doubles of ring and bytes of delay log the members need (members stored one after
  * another, member r's ring holding its own R_r slots).
  * at_ensemble_create: members are copied; ring_dev (ring_len doubles) and the optional log_dev (log_len bytes,
- * NULL for no log) are borrowed.  threads per CTA is 64, 128 or 256 (0: 256); ctas_per_sm <= 0 takes the
- * occupancy limit.  Errors: AT_ERR_ARG (non-1D member, n[0] % 4 != 0, sizes), AT_ERR_CUDA.
+ * NULL for no log) are borrowed.  threads per CTA is 128, 256, 512 or 1024 (0: 1024); ctas_per_sm <= 0
+ * takes the occupancy limit.  Errors: AT_ERR_ARG (non-1D member, n[0] % 4 != 0, sizes), AT_ERR_CUDA.
  * at_ensemble_run: one graph launch on the ensemble's stream (asynchronous).
  * at_ensemble_stats: blocks; per_member[r] (up to cap entries) receives member r's error statistics at its
  * final step (the at_error_stats fields); for each distinct grid size g < *ngroups (ascending, up to cap):

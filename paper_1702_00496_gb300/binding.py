@@ -21,7 +21,7 @@ AT_SYNC, AT_ASYNC_STD, AT_AT = 0, 1, 2
 # every entry point include/at.h declares (checked by the CPU test of the boundary)
 EXPORTS = (
     "at_coeffs", "at_stencil_taps", "at_solve_stencil", "at_delay", "at_ring_slots", "at_num_sides",
-    "at_init", "at_step", "at_reset", "at_sync", "at_state", "at_error_stats", "at_destroy", "at_last_error",
+    "at_init", "at_step", "at_reset", "at_set_launch", "at_sync", "at_state", "at_error_stats", "at_destroy", "at_last_error",
     "at_ensemble_sizes", "at_ensemble_create", "at_ensemble_run", "at_ensemble_stats", "at_ensemble_destroy",
 )
 
@@ -85,6 +85,7 @@ def load(build_if_missing: bool = True):
     L.at_step.argtypes = [vp, i64]
     L.at_sync.argtypes = [vp]
     L.at_reset.argtypes = [vp, vp]
+    L.at_set_launch.argtypes = [vp, i32, i32]
     L.at_state.argtypes = [vp, C.POINTER(i64), C.POINTER(vp)]
     L.at_error_stats.argtypes = [vp, C.POINTER(at_stats_t)]
     L.at_destroy.argtypes = [vp]
@@ -210,6 +211,10 @@ def at_step(h, nsteps: int) -> None:
 def at_reset(h, u0=None) -> None:
     """u0: CUDA float64 tensor with the initial field, or None for Eq. "IC"."""
     _check(load().at_reset(h, C.c_void_p(u0.data_ptr()) if u0 is not None else None), "at_reset")
+
+
+def at_set_launch(h, threads: int, blocks_per_sm: int) -> None:
+    _check(load().at_set_launch(h, int(threads), int(blocks_per_sm)), "at_set_launch")
 
 
 def at_sync(h) -> None:

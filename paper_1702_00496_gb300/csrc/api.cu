@@ -270,6 +270,20 @@ extern "C" int at_reset(at_handle_t *hd, const double *u0_dev) {
   return AT_OK;
 }
 
+extern "C" int at_set_launch(at_handle_t *hd, int32_t threads, int32_t blocks_per_sm) {
+  if (!hd || (threads != 128 && threads != 256 && threads != 512) || blocks_per_sm < 1 || blocks_per_sm > 64)
+    return fail(AT_ERR_ARG, "at_set_launch: threads must be 128, 256 or 512 and blocks_per_sm in 1..64");
+  cudaError_t e = cudaStreamSynchronize(hd->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "at_set_launch");
+  if (hd->exec) cudaGraphExecDestroy(hd->exec);
+  if (hd->graph) cudaGraphDestroy(hd->graph);
+  hd->exec = nullptr;
+  hd->graph = nullptr;
+  hd->sp.threads = threads;
+  hd->sp.blocks_per_sm = blocks_per_sm;
+  return AT_OK;
+}
+
 extern "C" int at_sync(at_handle_t *hd) {
   if (!hd) return fail(AT_ERR_ARG, "at_sync: NULL handle");
   cudaError_t e = cudaStreamSynchronize(hd->stream);

@@ -64,12 +64,12 @@ __device__ void run_member(const StepParams &p, uint8_t *keff_sh, int64_t nsteps
   }
 }
 
-__global__ void __launch_bounds__(256, 4) ensemble_kernel(const MemberParams *__restrict__ members,
+__global__ void __launch_bounds__(1024, 1) ensemble_kernel(const MemberParams *__restrict__ members,
                                                        const int32_t *__restrict__ order, int32_t count, int64_t nsteps,
                                                        int32_t *counter, double *__restrict__ member_stats) {
   __shared__ MemberParams m;
   __shared__ int32_t item;
-  __shared__ double red[kStatFields][256];
+  __shared__ double red[kStatFields][32];  // one partial per warp
   extern __shared__ uint8_t keff_sh[];  // two buffers of the largest member's side count
   for (;;) {
     if (threadIdx.x == 0) item = atomicAdd(counter, 1);
@@ -106,19 +106,30 @@ __global__ void __launch_bounds__(256, 4) ensemble_kernel(const MemberParams *__
       acc[6] += ua * ua;
       if (e != e) acc[1] = e;
     }
+    // warp partials by shuffles, then warp 0 combines them in warp order (deterministic)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
 #pragma unroll
-    for (int f = 0; f < kStatFields; ++f) red[f][threadIdx.x] = acc[f];
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-      if ((int)threadIdx.x < s) {
-#pragma unroll
-        for (int f = 0; f < kStatFields; ++f) {
-          const double o = red[f][threadIdx.x + s];
-          red[f][threadIdx.x] = (f == 1) ? ((o != o) ? o : fmax(red[f][threadIdx.x], o)) : red[f][threadIdx.x] + o;
-        }
+    for (int f = 0; f < kStatFields; ++f) {
+      double v = acc[f];
+      for (int o = 16; o > 0; o >>= 1) {
+        const double w = __shfl_down_sync(0xffffffffu, v, o);
+        v = (f == 1) ? ((w != w) ? w : fmax(v, w)) : v + w;
       }
-      __syncthreads();
+      if (lane == 0) red[f][warp] = v;
     }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+      for (int f = 0; f < kStatFields; ++f) {
+        double v = lane < nwarps ? red[f][lane] : (f == 1 ? 0.0 : 0.0);
+        for (int o = 16; o > 0; o >>= 1) {
+          const double w = __shfl_down_sync(0xffffffffu, v, o);
+          v = (f == 1) ? ((w != w) ? w : fmax(v, w)) : v + w;
+        }
+        if (lane == 0) red[f][0] = v;
+      }
+    }
+    __syncthreads();
     if (threadIdx.x < kStatFields) member_stats[(int64_t)r * kStatFields + threadIdx.x] = red[threadIdx.x][0];
     __syncthreads();
   }
@@ -212,8 +223,9 @@ extern "C" int at_ensemble_create(const at_config_t *members, int32_t count, int
   if (!out || !ring_dev || ring_len < need_ring) return fail(AT_ERR_ARG, "at_ensemble_create: ring too small");
   if (log_dev && log_len < need_log) return fail(AT_ERR_ARG, "at_ensemble_create: log too small");
   if (nsteps > 0xFFFFFFFFll) return fail(AT_ERR_ARG, "at_ensemble_create: step counter exceeds 32 bits");
-  if (threads == 0) threads = 256;
-  if (threads != 64 && threads != 128 && threads != 256) return fail(AT_ERR_ARG, "threads must be 64, 128 or 256");
+  if (threads == 0) threads = 1024;
+  if (threads != 128 && threads != 256 && threads != 512 && threads != 1024)
+    return fail(AT_ERR_ARG, "threads must be 128, 256, 512 or 1024");
 
   std::vector<MemberParams> host(count);
   std::map<int64_t, int> groups;

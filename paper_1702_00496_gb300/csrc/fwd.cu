@@ -29,7 +29,7 @@ using namespace atfd;
 // also draws the delays of one slice of the PE sides for step n+1 into the other half of the double-buffered
 // delay array, so the next launch finds them ready.
 template <int DIM, int H>
-__global__ void __launch_bounds__(256) forward_group_kernel(const StepParams p, const int64_t n_off,
+__global__ void __launch_bounds__(512) forward_group_kernel(const StepParams p, const int64_t n_off,
                                                             const int64_t *n_base) {
   const int64_t n = n_off + (n_base ? *n_base : 0);
   const double *__restrict__ un = p.ring + (n % p.R) * p.ntot;
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(256) forward_group_kernel(const StepParams p, 
 
 // Fallback for shapes the grouped kernel does not take (n[0] not a multiple of 4, odd slots).
 template <int DIM, int H>
-__global__ void __launch_bounds__(256) forward_point_kernel(const StepParams p, const int64_t n_off,
+__global__ void __launch_bounds__(512) forward_point_kernel(const StepParams p, const int64_t n_off,
                                                             const int64_t *n_base) {
   const int64_t n = n_off + (n_base ? *n_base : 0);
   const double *__restrict__ un = p.ring + (n % p.R) * p.ntot;
@@ -97,8 +97,13 @@ cudaError_t launch_draw_delays(const StepParams &p, int64_t n, cudaStream_t st) 
 }
 
 cudaError_t launch_forward_step(const StepParams &p, int64_t n, const int64_t *n_base, cudaStream_t st) {
-  const int threads = 256;
-  const int max_blocks = 152 * 8 * 4;
+  const int threads = p.threads > 0 ? p.threads : 256;
+  int sms = 152;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const int max_blocks = sms * (p.blocks_per_sm > 0 ? p.blocks_per_sm : 32);
   auto grid = [&](int64_t work) { int64_t b = (work + threads - 1) / threads; return (int)(b < max_blocks ? b : max_blocks); };
   // groups of four x points must not straddle a PE and must start on 16 bytes
   const bool grouped = p.n[0] % 4 == 0 && (!p.use_pe[0] || p.S[0] % 4 == 0) &&

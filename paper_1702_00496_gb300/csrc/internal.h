@@ -32,6 +32,8 @@ struct StepParams {
   int32_t use_thr;        // thresholds given (else uniform bins)
   uint64_t seed;
   uint64_t thr[AT_MAX_L]; // L-1 bin edges on the 32-bit word
+  int32_t threads;        // launch shape of the per-step kernel: threads per block
+  int32_t blocks_per_sm;  // and a cap on blocks per SM for its grid-stride loop
   double zero;            // +0.0, kept opaque so the compiler issues an FMA rather than a multiply
   double s0;              // merged centre coefficient: 1 + dt sum_a (-c_a cd1_0/dx_a + alpha cd2_0/dx_a^2)
   double s[3][2 * AT_MAX_H + 1];  // merged off-centre coefficients per axis (index j+h)

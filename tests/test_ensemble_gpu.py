@@ -41,7 +41,7 @@ def _check_members(ens, specs, nsteps, idx):
     return per, groups
 
 
-@pytest.mark.parametrize("threads,ctas", [(256, 0), (128, 2), (64, 1)])
+@pytest.mark.parametrize("threads,ctas", [(1024, 0), (512, 2), (256, 0), (128, 1)])
 def test_mixed_ensemble_matches_oracle(threads, ctas):
     from paper_1702_00496_gb300 import Ensemble
     specs = _members(14, [128, 256, 512, 1024], [2, 3, 4], [2, 4])

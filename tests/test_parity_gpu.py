@@ -162,3 +162,21 @@ def test_full_size_3d_512_prefix(order):
     ref, _, _ = oracle.run(cfg, 6, want_log=False, threads=THREADS)
     assert np.linalg.norm(u - ref) / np.linalg.norm(ref) <= TOL
     assert np.isfinite(st["rms"]) and st["rms"] < 1e-2 * st["ua_rms"]
+
+
+def test_launch_shapes_do_not_change_results():
+    """Every launch shape the autotuner may pick gives the same bits (the arithmetic per point is fixed)."""
+    from paper_1702_00496_gb300 import Solver, at_set_launch
+    for spec in (W.wl_1d(4096, 16, 4, 4, 0, 12, range(1, 6))[0], W.wl_3d([32, 24, 16], [4, 3, 2], 4, 3, 0, 13,
+                                                                         c=(0.3, 0.2, 0.1))[0]):
+        ref = None
+        for threads, bps in ((256, 32), (128, 4), (512, 16), (256, 1)):
+            s = Solver(spec)
+            at_set_launch(s.h, threads, bps)
+            s.step(120)
+            s.sync()
+            u = s.field().clone()
+            s.close()
+            if ref is None:
+                ref = u
+            assert torch.equal(u, ref), (threads, bps)
