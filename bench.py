@@ -212,6 +212,51 @@ def run_ensemble(args, rank: int, world: int, local: int):
         print(json.dumps(line), flush=True)
 
 
+def run_adjoint(args, rank: int, world: int, local: int):
+    """Gradient of 1/2 ||U^T - u_target||^2 (256^3, order 4, 2000 steps) by the hand-written adjoint with
+    sqrt(T) checkpointing, against the forward run alone: reports the adjoint/forward time ratio."""
+    import torch
+    from paper_1702_00496_gb300 import Solver
+
+    spec, T = W.workload("adjoint_256")
+    if args.time_steps is not None:
+        T = args.time_steps
+    spec["seed"] = int(spec["seed"]) + rank
+    ntot = spec["n"][0] * spec["n"][1] * spec["n"][2]
+    stream = torch.cuda.current_stream()
+    s = Solver(spec, device=f"cuda:{local}", stream=stream)
+    target = torch.zeros(ntot, dtype=torch.float64, device=f"cuda:{local}")
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    fwd, adj = [], []
+    for it in range(args.warmup + args.steps):
+        s.reset()
+        a, b = ev(), ev()
+        a.record(stream)
+        s.step(T)
+        b.record(stream)
+        s.reset()
+        c, d = ev(), ev()
+        c.record(stream)
+        s.adjoint_forward(T)
+        lam = s.field().reshape(-1) - target
+        g, ga = s.adjoint_backward(lam)
+        d.record(stream)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            fwd.append(a.elapsed_time(b))
+            adj.append(c.elapsed_time(d))
+    s.close()
+    f_ms, a_ms = statistics.median(fwd), statistics.median(adj)
+    if rank == 0:
+        line = {"metric": METRIC + " -- adjoint", "value": world * ntot * T / (a_ms / 1e3), "unit": "updates/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": a_ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "adjoint_256", "points": ntot, "time_steps": T},
+                "forward_ms": f_ms, "adjoint_ms": a_ms, "adjoint_forward_ratio": a_ms / f_ms,
+                "grad_alpha": ga}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -243,6 +288,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     if args.workload == "ensemble":
         return run_ensemble(args, rank, world, local)
+    if args.workload == "adjoint_256":
+        return run_adjoint(args, rank, world, local)
 
     from paper_1702_00496_gb300 import Solver
 

@@ -164,6 +164,29 @@ int at_error_stats(at_handle_t *hd, at_stats_t *out);
 /* Release the handle's scratch.  The caller's ring and log are untouched. */
 int at_destroy(at_handle_t *hd);
 
+/* ------------------------------------------------------------------ adjoint */
+/* Gradient of a misfit J(U^nsteps) with respect to the initial field U^0 and the diffusivity alpha, through the
+ * same delays as the forward run.  The forward step is linear in the stored levels; its transpose sends
+ * lambda^{n+1} back through the merged taps to lambda^n and, for buffer points, through the extrapolation
+ * weights w_m(k) of the replayed delay k to lambda^{n-k-m}.  dJ/dalpha = sum_n <lambda^{n+1}, dt D2_AT U^n>.
+ * The paper has no adjoint; this is the exact discrete adjoint of the forward step of Sec. 4.1 / Tables
+ * "atschemes-left/right".
+ *
+ * at_adjoint_workspace: doubles of device workspace for a run of nsteps with a checkpoint every ckpt_every
+ *   steps (0: ceil(sqrt(nsteps))): checkpoints of the R-1 live levels, one segment of recomputed levels, the
+ *   R-slot adjoint ring and small accumulators.
+ * at_adjoint_forward: from step 0 (after at_init or at_reset), run nsteps forward steps exactly as at_step and
+ *   keep the checkpoints in work_dev (caller-owned, 16-byte aligned).  Errors: AT_ERR_ARG, AT_ERR_STATE (not at
+ *   step 0), AT_ERR_CUDA.
+ * at_adjoint_backward: given lambda_dev = dJ/dU^nsteps (device, ntot doubles), write dJ/dU^0 to grad_u0_dev
+ *   (device, ntot doubles) and dJ/dalpha to *grad_alpha_host.  Replays one checkpoint segment at a time:
+ *   restores it, recomputes its levels with the forward kernel, runs its adjoint steps in reverse.  Blocks.
+ *   Requires at_adjoint_forward to have been the last stepping call.  Errors: AT_ERR_ARG, AT_ERR_STATE,
+ *   AT_ERR_CUDA, AT_ERR_NONFINITE. */
+int at_adjoint_workspace(at_handle_t *hd, int64_t nsteps, int64_t ckpt_every, int64_t *work_len);
+int at_adjoint_forward(at_handle_t *hd, int64_t nsteps, int64_t ckpt_every, double *work_dev, int64_t work_len);
+int at_adjoint_backward(at_handle_t *hd, const double *lambda_dev, double *grad_u0_dev, double *grad_alpha_host);
+
 /* ------------------------------------------------------------------ batched ensemble */
 /* The error of an AT scheme is a statistical quantity (Sec. 4: ensemble average over delay realizations,
  * Eq. "aveE_split"; Sec. 5.1: averages over runs with random phases).  An ensemble runs `count` independent

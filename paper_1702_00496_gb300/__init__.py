@@ -8,3 +8,4 @@ from .binding import (AT_AT, AT_ASYNC_STD, AT_SYNC, ATError, Config, at_coeffs, 
                       at_error_stats, at_init, at_last_error, at_num_sides, at_ring_slots, at_solve_stencil,
                       at_reset, at_set_launch, at_state, at_stencil_taps, at_step, at_sync, load)
 from .solver import Ensemble, Solver  # noqa: F401
+from .autograd import ATForward, at_forward  # noqa: F401

@@ -22,6 +22,7 @@ AT_SYNC, AT_ASYNC_STD, AT_AT = 0, 1, 2
 EXPORTS = (
     "at_coeffs", "at_stencil_taps", "at_solve_stencil", "at_delay", "at_ring_slots", "at_num_sides",
     "at_init", "at_step", "at_reset", "at_set_launch", "at_sync", "at_state", "at_error_stats", "at_destroy", "at_last_error",
+    "at_adjoint_workspace", "at_adjoint_forward", "at_adjoint_backward",
     "at_ensemble_sizes", "at_ensemble_create", "at_ensemble_run", "at_ensemble_stats", "at_ensemble_destroy",
 )
 
@@ -90,6 +91,9 @@ def load(build_if_missing: bool = True):
     L.at_error_stats.argtypes = [vp, C.POINTER(at_stats_t)]
     L.at_destroy.argtypes = [vp]
     L.at_last_error.restype = C.c_char_p
+    L.at_adjoint_workspace.argtypes = [vp, i64, i64, C.POINTER(i64)]
+    L.at_adjoint_forward.argtypes = [vp, i64, i64, vp, i64]
+    L.at_adjoint_backward.argtypes = [vp, vp, vp, C.POINTER(C.c_double)]
     L.at_ensemble_sizes.argtypes = [C.POINTER(at_config_t), i32, i64, C.POINTER(i64), C.POINTER(i64)]
     L.at_ensemble_create.argtypes = [C.POINTER(at_config_t), i32, i64, vp, i64, vp, i64, i32, i32, vp, C.POINTER(vp)]
     L.at_ensemble_run.argtypes = [vp]
@@ -283,3 +287,22 @@ def at_ensemble_stats(h, count: int):
 
 def at_ensemble_destroy(h) -> None:
     _check(load().at_ensemble_destroy(h), "at_ensemble_destroy")
+
+
+def at_adjoint_workspace(h, nsteps: int, ckpt_every: int = 0) -> int:
+    n = C.c_int64()
+    _check(load().at_adjoint_workspace(h, int(nsteps), int(ckpt_every), C.byref(n)), "at_adjoint_workspace")
+    return n.value
+
+
+def at_adjoint_forward(h, nsteps: int, ckpt_every: int, work) -> None:
+    _check(load().at_adjoint_forward(h, int(nsteps), int(ckpt_every), C.c_void_p(work.data_ptr()), work.numel()),
+           "at_adjoint_forward")
+
+
+def at_adjoint_backward(h, lam, grad_u0) -> float:
+    """lam = dJ/dU^nsteps, grad_u0 receives dJ/dU^0 (CUDA float64 tensors); returns dJ/dalpha."""
+    ga = C.c_double()
+    _check(load().at_adjoint_backward(h, C.c_void_p(lam.data_ptr()), C.c_void_p(grad_u0.data_ptr()), C.byref(ga)),
+           "at_adjoint_backward")
+    return ga.value

@@ -1,0 +1,406 @@
+// adjoint.cu -- hand-written adjoint of the AT forward step (gradient of a final-time misfit with respect to
+// the initial field and the diffusivity alpha), replaying the recorded delays backward.
+//
+// Forward step n (fwd.cu) is linear in the stored levels:
+//     U^{n+1}_i = s0 U^n_i + sum_a sum_{j != 0} s_{a,j} v_{a,j}(i),
+//     v = U^n_{i+j}                                  when i+j lies in i's PE (or the side's delay is 0),
+//     v = sum_{m<T} w_m(k) U^{n-k-m}_{i+j}          when i+j is a buffer point of the side with delay k.
+// Its transpose sends lambda^{n+1}_i to lambda^n_{i+j} with weight s_{a,j}, or to the older levels
+// lambda^{n-k-m}_{i+j} with weight s_{a,j} w_m(k).  The kernel below evaluates that transpose as a GATHER over
+// output cells c: each thread owns cells c at every level, so no atomics are needed.  A level l steps back
+// receives contributions from backward steps n = l .. l + R - 2, so lambda lives in an R-slot ring (level m in
+// slot m mod R): step n reads slot n+1, adds into levels n .. n-R+3, and initialises level n-R+2 (whose slot
+// held the consumed lambda^{n+2}).
+//
+// d/d alpha: s_{a,j} = dt (-c_a cd1_j/dx_a + alpha cd2_j/dx_a^2), so dU^{n+1}_i/d alpha = sum q_{a,j} v_{a,j}(i)
+// with q_{a,j} = dt cd2_j / dx_a^2 (the AT second derivative times dt); the kernel accumulates
+// <lambda^{n+1}, dt D2_AT U> per block, in a fixed block-to-cell assignment, so the sum is deterministic.
+//
+// Forward levels for the alpha term come from a segment buffer: the forward pass keeps a checkpoint of the
+// R-1 live levels every s steps (s ~ sqrt(steps)); the backward sweep restores one segment at a time, recomputes
+// its levels with the forward kernels, and runs the adjoint steps of that segment in reverse.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/at.h"
+#include "stencil.cuh"
+
+namespace {
+
+using namespace atfd;
+
+#define AT_MAX_LAG (AT_MAX_L + AT_MAX_T)
+
+struct AdjParams {
+  StepParams f;        // forward parameters whose ring is the segment buffer (R = segment depth)
+  double *lam;         // adjoint ring, Rl slots of f.ntot
+  int32_t Rl;          // = L + T of the problem
+  uint8_t *akeff;      // effective delays of the forward steps the backward sweep replays (two buffers)
+  double *g_blk;       // per-block accumulators of d J / d alpha
+};
+
+// Block sum of v into g_blk[blockIdx.x] (warp shuffles, then warp 0 in warp order).
+__device__ __forceinline__ void block_accumulate(double v, double *g_blk) {
+  __shared__ double part[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) part[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    double s = lane < (int)(blockDim.x >> 5) ? part[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) g_blk[blockIdx.x] += s;
+  }
+}
+
+// General path for one output cell c (any position): transpose contributions per lag and the alpha term.
+template <int DIM, int H>
+__device__ void adjoint_cell(const AdjParams &a, const uint8_t *__restrict__ keff, int64_t n, int64_t ci,
+                             const int c[3], double &galpha) {
+  const StepParams &f = a.f;
+  const int64_t N = f.ntot;
+  const double *ln = a.lam + ((n + 1) % a.Rl) * N;
+  const double *un = f.ring + (n % f.R) * N;
+  const int64_t stride[3] = {1, (int64_t)f.n[0], (int64_t)f.n[0] * f.n[1]};
+  int pidx[3] = {0, 0, 0}, pos[3] = {0, 0, 0};
+#pragma unroll
+  for (int ax = 0; ax < DIM; ++ax) {
+    pidx[ax] = c[ax] / f.S[ax];
+    pos[ax] = c[ax] - pidx[ax] * f.S[ax];
+  }
+  double acc[AT_MAX_LAG];
+#pragma unroll
+  for (int l = 0; l < AT_MAX_LAG; ++l) acc[l] = 0.0;
+  const double lc = ln[ci];
+  acc[0] = fma(f.s0, lc, f.zero);
+  double d2 = fma(f.q0, __ldg(un + ci), f.zero);
+#pragma unroll
+  for (int ax = 0; ax < DIM; ++ax) {
+    const bool edge = f.use_pe[ax] && (pos[ax] < H || pos[ax] >= f.S[ax] - H);
+#pragma unroll
+    for (int j = -H; j <= H; ++j) {
+      if (j == 0) continue;
+      // transpose: point i = c - j reads c through its tap j
+      const int ia = wrap_coord(c[ax] - j, f.n[ax]);
+      const int64_t i = ci + (int64_t)(ia - c[ax]) * stride[ax];
+      const double s = f.s[ax][j + H], li = ln[i];
+      int k = 0;
+      if (edge) {
+        const int pi = ia / f.S[ax];
+        if (pi != pidx[ax]) {  // c is a buffer point of i, on the side of i's PE that faces c
+          int pid[3] = {pidx[0], pidx[1], pidx[2]};
+          pid[ax] = pi;
+          k = keff[side_of<DIM>(f, pid, ax, j > 0 ? 1 : 0)];
+        }
+      }
+      if (k == 0) {
+        acc[0] = fma(s, li, acc[0]);
+      } else {
+        for (int m = 0; m < f.T; ++m) acc[k + m] = fma(s * f.w[k][m], li, acc[k + m]);
+      }
+      // alpha term: c's own tap j, with c's own side delays
+      const int cj = wrap_coord(c[ax] + j, f.n[ax]);
+      const int64_t cell = ci + (int64_t)(cj - c[ax]) * stride[ax];
+      int kc = 0;
+      if (edge && pos[ax] + j < 0) kc = keff[side_of<DIM>(f, pidx, ax, 0)];
+      if (edge && pos[ax] + j >= f.S[ax]) kc = keff[side_of<DIM>(f, pidx, ax, 1)];
+      const double v = kc > 0 ? halo_value<LdgNC>(f, cell, n, kc) : __ldg(un + cell);
+      d2 = fma(f.q[ax][j + H], v, d2);
+    }
+  }
+  galpha = fma(lc, d2, galpha);
+  const int maxlag = a.Rl - 2;
+  for (int l = 0; l <= maxlag; ++l) {
+    const int64_t level = n - l;
+    if (level < 0) break;
+    double *slot = a.lam + (level % a.Rl) * N + ci;
+    if (l == maxlag) *slot = acc[l];
+    else if (l == 0 || acc[l] != 0.0) *slot = *slot + acc[l];
+  }
+}
+
+// Backward step n.  G: cells come in groups of four x points (n[0] % 4 == 0, 16-byte aligned slots); a group
+// whose cells and neighbours all lie inside one PE and away from the domain ends takes the straight path.
+template <int DIM, int H, bool G>
+__global__ void __launch_bounds__(256) adjoint_step_kernel(const AdjParams a, const int64_t n) {
+  const StepParams &f = a.f;
+  const int64_t N = f.ntot;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nthreads = (int64_t)gridDim.x * blockDim.x;
+  if (n >= 1) draw_sides(f, n - 1, tid, nthreads, a.akeff + ((n - 1) & 1) * f.nb);
+  const uint8_t *keff = a.akeff + (n & 1) * f.nb;
+  double galpha = 0.0;
+  if (!G) {
+    const int nx = f.n[0], ny = DIM == 3 ? f.n[1] : 1;
+    for (int64_t i = tid; i < N; i += nthreads) {
+      int c[3] = {(int)i, 0, 0};
+      if (DIM == 3) {
+        const int64_t yz = i / nx;
+        c[0] = (int)(i - yz * nx); c[2] = (int)(yz / ny); c[1] = (int)(yz - (int64_t)c[2] * ny);
+      }
+      adjoint_cell<DIM, H>(a, keff, n, i, c, galpha);
+    }
+  } else {
+    const double *ln = a.lam + ((n + 1) % a.Rl) * N;
+    const double *un = f.ring + (n % f.R) * N;
+    const int nx = f.n[0], ny = f.n[1], nz = f.n[2];
+    const int gx = nx >> 2;
+    const int64_t groups = N >> 2;
+    for (int64_t g = tid; g < groups; g += nthreads) {
+      const int64_t r = g / gx;
+      const int x0 = (int)(g - r * gx) << 2;
+      const int z = DIM == 3 ? (int)(r / ny) : 0, y = DIM == 3 ? (int)(r - (int64_t)z * ny) : 0;
+      const int64_t i0 = r * nx + x0;
+      const int px = x0 % f.S[0];
+      bool inside = (x0 >= 2) && (x0 + 6 <= nx) && (!f.use_pe[0] || (px >= H && px + 3 < f.S[0] - H));
+      if (DIM == 3) {
+        const int py = y % f.S[1], pz = z % f.S[2];
+        inside = inside && (y >= H) && (y + H < ny) && (!f.use_pe[1] || (py >= H && py < f.S[1] - H)) &&
+                 (z >= H) && (z + H < nz) && (!f.use_pe[2] || (pz >= H && pz < f.S[2] - H));
+      }
+      if (!inside) {
+        for (int q = 0; q < 4; ++q) {
+          const int c[3] = {x0 + q, y, z};
+          adjoint_cell<DIM, H>(a, keff, n, i0 + q, c, galpha);
+        }
+        continue;
+      }
+      double lv[8], uv[8];
+      {
+        const double2 l0 = LdgNC::ld2(ln + i0 - 2), l1 = LdgNC::ld2(ln + i0), l2 = LdgNC::ld2(ln + i0 + 2),
+                      l3 = LdgNC::ld2(ln + i0 + 4);
+        lv[0] = l0.x; lv[1] = l0.y; lv[2] = l1.x; lv[3] = l1.y; lv[4] = l2.x; lv[5] = l2.y; lv[6] = l3.x; lv[7] = l3.y;
+        const double2 u0 = LdgNC::ld2(un + i0 - 2), u1 = LdgNC::ld2(un + i0), u2 = LdgNC::ld2(un + i0 + 2),
+                      u3 = LdgNC::ld2(un + i0 + 4);
+        uv[0] = u0.x; uv[1] = u0.y; uv[2] = u1.x; uv[3] = u1.y; uv[4] = u2.x; uv[5] = u2.y; uv[6] = u3.x; uv[7] = u3.y;
+      }
+      double A[4], D[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        double acc = fma(f.s0, lv[q + 2], f.zero), d = fma(f.q0, uv[q + 2], f.zero);
+#pragma unroll
+        for (int j = -H; j <= H; ++j) {
+          if (j == 0) continue;
+          acc = fma(f.s[0][j + H], lv[q + 2 - j], acc);
+          d = fma(f.q[0][j + H], uv[q + 2 + j], d);
+        }
+        A[q] = acc;
+        D[q] = d;
+      }
+      if (DIM == 3) {
+#pragma unroll
+        for (int ax = 1; ax < 3; ++ax) {
+          const int64_t st = ax == 1 ? (int64_t)nx : (int64_t)nx * ny;
+#pragma unroll
+          for (int j = -H; j <= H; ++j) {
+            if (j == 0) continue;
+            const double2 la = LdgNC::ld2(ln + i0 - j * st), lb = LdgNC::ld2(ln + i0 - j * st + 2);
+            const double2 ua = LdgNC::ld2(un + i0 + j * st), ub = LdgNC::ld2(un + i0 + j * st + 2);
+            const double s = f.s[ax][j + H], qq = f.q[ax][j + H];
+            A[0] = fma(s, la.x, A[0]); A[1] = fma(s, la.y, A[1]); A[2] = fma(s, lb.x, A[2]); A[3] = fma(s, lb.y, A[3]);
+            D[0] = fma(qq, ua.x, D[0]); D[1] = fma(qq, ua.y, D[1]); D[2] = fma(qq, ub.x, D[2]); D[3] = fma(qq, ub.y, D[3]);
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) galpha = fma(lv[q + 2], D[q], galpha);
+      double2 *cur = reinterpret_cast<double2 *>(a.lam + (n % a.Rl) * N + i0);
+      if (a.Rl == 2) {
+        cur[0] = make_double2(A[0], A[1]);
+        cur[1] = make_double2(A[2], A[3]);
+      } else {
+        const double2 p0 = cur[0], p1 = cur[1];
+        cur[0] = make_double2(p0.x + A[0], p0.y + A[1]);
+        cur[1] = make_double2(p1.x + A[2], p1.y + A[3]);
+        const int64_t fresh = n - a.Rl + 2;
+        if (fresh >= 0) {
+          double2 *fr = reinterpret_cast<double2 *>(a.lam + (fresh % a.Rl) * N + i0);
+          fr[0] = make_double2(0.0, 0.0);
+          fr[1] = make_double2(0.0, 0.0);
+        }
+      }
+    }
+  }
+  block_accumulate(galpha, a.g_blk);
+}
+
+__global__ void sum_blocks_kernel(const double *g_blk, int nblk, double *out) {
+  __shared__ double part[32];
+  double v = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) v += g_blk[b];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) part[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    double s = lane < (int)(blockDim.x >> 5) ? part[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) *out = s;
+  }
+}
+
+const int kAdjThreads = 256;
+
+int adj_blocks() {
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms * 8;
+}
+
+cudaError_t launch_adjoint_step(const AdjParams &a, int64_t n, int nblk, cudaStream_t st) {
+  const bool grouped = a.f.n[0] % 4 == 0 && (!a.f.use_pe[0] || a.f.S[0] % 4 == 0) &&
+                       (reinterpret_cast<uintptr_t>(a.lam) % 16) == 0 && (reinterpret_cast<uintptr_t>(a.f.ring) % 16) == 0;
+  if (a.f.dim == 1) {
+    if (a.f.h == 1) grouped ? adjoint_step_kernel<1, 1, true><<<nblk, kAdjThreads, 0, st>>>(a, n)
+                            : adjoint_step_kernel<1, 1, false><<<nblk, kAdjThreads, 0, st>>>(a, n);
+    else grouped ? adjoint_step_kernel<1, 2, true><<<nblk, kAdjThreads, 0, st>>>(a, n)
+                 : adjoint_step_kernel<1, 2, false><<<nblk, kAdjThreads, 0, st>>>(a, n);
+  } else {
+    if (a.f.h == 1) grouped ? adjoint_step_kernel<3, 1, true><<<nblk, kAdjThreads, 0, st>>>(a, n)
+                            : adjoint_step_kernel<3, 1, false><<<nblk, kAdjThreads, 0, st>>>(a, n);
+    else grouped ? adjoint_step_kernel<3, 2, true><<<nblk, kAdjThreads, 0, st>>>(a, n)
+                 : adjoint_step_kernel<3, 2, false><<<nblk, kAdjThreads, 0, st>>>(a, n);
+  }
+  return cudaGetLastError();
+}
+
+int fail(int code, const char *msg) {
+  at_internal_set_error(msg);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where) {
+  char buf[200];
+  std::snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+  at_internal_set_error(buf);
+  return AT_ERR_CUDA;
+}
+
+}  // namespace
+
+namespace {
+
+// Workspace layout (doubles, each part rounded up to 32 doubles):
+//   checkpoints  nck x (R-1) x ntot     levels n0-R+2 .. n0 of every checkpoint n0 = 0, s, 2s, ...
+//   segment      (s + R - 1) x ntot     levels of the segment being replayed (level m in slot m mod depth)
+//   lambda       R x ntot               adjoint ring
+//   g_blk        nblk                   per-block d J / d alpha accumulators, then the sum
+//   delays       2 x 2 x nb bytes       effective delays of the recompute and of the backward sweep
+struct AdjLayout {
+  int64_t s, nck, seg_depth, ck, seg, lam, gblk, keff, total;
+};
+
+int64_t up32(int64_t v) { return (v + 31) / 32 * 32; }
+
+AdjLayout layout(const at_handle *hd, int64_t nsteps, int64_t every) {
+  AdjLayout L;
+  const int64_t N = hd->sp.ntot, R = hd->sp.R;
+  L.s = every > 0 ? every : (int64_t)std::ceil(std::sqrt((double)(nsteps > 0 ? nsteps : 1)));
+  if (L.s < 1) L.s = 1;
+  L.nck = nsteps > 0 ? (nsteps + L.s - 1) / L.s : 0;
+  L.seg_depth = L.s + R - 1;
+  L.ck = 0;
+  L.seg = L.ck + up32(L.nck * (R - 1) * N);
+  L.lam = L.seg + up32(L.seg_depth * N);
+  L.gblk = L.lam + up32(R * N);
+  L.keff = L.gblk + up32(adj_blocks() + 1);
+  L.total = L.keff + up32((4 * hd->sp.nb + 7) / 8);
+  return L;
+}
+
+cudaError_t copy_field(double *dst, const double *src, int64_t n, cudaStream_t st) {
+  return cudaMemcpyAsync(dst, src, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+}
+
+}  // namespace
+
+extern "C" int at_adjoint_workspace(at_handle_t *hd, int64_t nsteps, int64_t ckpt_every, int64_t *work_len) {
+  if (!hd || nsteps < 0 || ckpt_every < 0 || !work_len) return fail(AT_ERR_ARG, "at_adjoint_workspace: bad argument");
+  *work_len = layout(hd, nsteps, ckpt_every).total;
+  return AT_OK;
+}
+
+extern "C" int at_adjoint_forward(at_handle_t *hd, int64_t nsteps, int64_t ckpt_every, double *work_dev,
+                                  int64_t work_len) {
+  if (!hd || nsteps < 0 || ckpt_every < 0 || !work_dev) return fail(AT_ERR_ARG, "at_adjoint_forward: bad argument");
+  if (hd->step != 0) return fail(AT_ERR_STATE, "at_adjoint_forward: the handle must be at step 0 (at_reset)");
+  const AdjLayout L = layout(hd, nsteps, ckpt_every);
+  if (work_len < L.total) return fail(AT_ERR_ARG, "at_adjoint_forward: workspace too small");
+  if (reinterpret_cast<uintptr_t>(work_dev) % 16) return fail(AT_ERR_ARG, "at_adjoint_forward: workspace not 16-byte aligned");
+  const int64_t N = hd->sp.ntot, R = hd->sp.R;
+  hd->adj_nsteps = -1;
+  for (int64_t c = 0; c < L.nck; ++c) {
+    const int64_t n0 = c * L.s;
+    for (int64_t lev = n0 - R + 2; lev <= n0; ++lev) {
+      if (lev < 0) continue;
+      cudaError_t e = copy_field(work_dev + L.ck + (c * (R - 1) + (lev - (n0 - R + 2))) * N,
+                                 hd->sp.ring + (lev % R) * N, N, hd->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "at_adjoint_forward: checkpoint");
+    }
+    const int64_t todo = (n0 + L.s <= nsteps) ? L.s : nsteps - n0;
+    int rc = at_step(hd, todo);
+    if (rc) return rc;
+  }
+  hd->adj_nsteps = nsteps;
+  hd->adj_every = L.s;
+  hd->adj_work = work_dev;
+  hd->adj_work_len = work_len;
+  return AT_OK;
+}
+
+extern "C" int at_adjoint_backward(at_handle_t *hd, const double *lambda_dev, double *grad_u0_dev,
+                                   double *grad_alpha_host) {
+  if (!hd || !lambda_dev || !grad_u0_dev || !grad_alpha_host) return fail(AT_ERR_ARG, "at_adjoint_backward: bad argument");
+  if (hd->adj_nsteps < 0 || hd->step != hd->adj_nsteps)
+    return fail(AT_ERR_STATE, "at_adjoint_backward: needs the at_adjoint_forward pass right before");
+  const int64_t Ns = hd->adj_nsteps, N = hd->sp.ntot, R = hd->sp.R;
+  const AdjLayout L = layout(hd, Ns, hd->adj_every);
+  double *w = hd->adj_work;
+  cudaStream_t st = hd->stream;
+  cudaError_t e = cudaSuccess;
+  const int nblk = adj_blocks();
+  // segment parameters: forward levels in the segment buffer, no log, own delay buffers
+  StepParams seg = hd->sp;
+  seg.ring = w + L.seg;
+  seg.R = (int32_t)L.seg_depth;
+  seg.log = nullptr;
+  seg.log_steps = 0;
+  seg.keff = reinterpret_cast<uint8_t *>(w + L.keff);
+  AdjParams a;
+  a.f = seg;
+  a.lam = w + L.lam;
+  a.Rl = (int32_t)R;
+  a.akeff = reinterpret_cast<uint8_t *>(w + L.keff) + 2 * hd->sp.nb;
+  a.g_blk = w + L.gblk;
+  // lambda^Ns = the caller's seed; the R-2 older levels start at zero; alpha accumulators at zero
+  e = copy_field(a.lam + (Ns % R) * N, lambda_dev, N, st);
+  for (int64_t m = 1; m <= R - 2 && e == cudaSuccess; ++m)
+    if (Ns - m >= 0) e = cudaMemsetAsync(a.lam + ((Ns - m) % R) * N, 0, sizeof(double) * (size_t)N, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.g_blk, 0, sizeof(double) * (size_t)(nblk + 1), st);
+  if (e == cudaSuccess && Ns > 0) {
+    StepParams first = seg;
+    first.keff = a.akeff;
+    e = launch_draw_delays(first, Ns - 1, st);
+  }
+  for (int64_t c = L.nck - 1; c >= 0 && e == cudaSuccess; --c) {
+    const int64_t n0 = c * L.s, n1 = (n0 + L.s < Ns) ? n0 + L.s : Ns;
+    for (int64_t lev = n0 - R + 2; lev <= n0 && e == cudaSuccess; ++lev) {
+      if (lev < 0) continue;
+      e = copy_field(seg.ring + (lev % seg.R) * N, w + L.ck + (c * (R - 1) + (lev - (n0 - R + 2))) * N, N, st);
+    }
+    if (e == cudaSuccess) e = launch_draw_delays(seg, n0, st);
+    for (int64_t n = n0; n + 1 < n1 && e == cudaSuccess; ++n) e = launch_forward_step(seg, n, nullptr, st);
+    for (int64_t n = n1 - 1; n >= n0 && e == cudaSuccess; --n) e = launch_adjoint_step(a, n, nblk, st);
+  }
+  if (e == cudaSuccess) e = copy_field(grad_u0_dev, a.lam, N, st);  // level 0 lives in slot 0
+  if (e == cudaSuccess) {
+    sum_blocks_kernel<<<1, 256, 0, st>>>(a.g_blk, nblk, a.g_blk + nblk);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(grad_alpha_host, a.g_blk + nblk, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "at_adjoint_backward");
+  if (!std::isfinite(*grad_alpha_host)) return fail(AT_ERR_NONFINITE, "at_adjoint_backward: non-finite gradient");
+  return AT_OK;
+}

@@ -10,27 +10,7 @@
 #include "internal.h"
 #include "philox.cuh"
 
-struct at_handle {
-  at_config_t cfg;
-  std::vector<uint64_t> thr;
-  StepParams sp;
-  WaveParams wp;
-  int64_t log_steps = 0;
-  int64_t step = 0;
-  cudaStream_t stream = nullptr;
-  // scratch owned by the handle: status word, reduction partials and result, 3D axis tables
-  void *scratch = nullptr;
-  int32_t *d_status = nullptr;
-  double *d_partials = nullptr;
-  double *d_result = nullptr;
-  double *d_tables = nullptr;
-  int64_t *d_step = nullptr;  // step base read by the captured graph
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-};
 
-// Steps per captured graph: long runs replay one graph of kGraphSteps kernel nodes plus a counter update.
-static const int64_t kGraphSteps = 50;
 
 namespace {
 
@@ -124,7 +104,7 @@ int at_prepare_params(const at_config_t *cfg, double *ring_dev, uint8_t *log_dev
   p.use_thr = cfg->thresholds != nullptr;
   if (cfg->thresholds)
     for (int m = 0; m + 1 < cfg->L; ++m) p.thr[m] = cfg->thresholds[m];
-  double s0 = 1.0;
+  double s0 = 1.0, q0 = 0.0;
   for (int a = 0; a < 3; ++a) {
     p.n[a] = (int32_t)cfg->n[a];
     p.pe[a] = cfg->pe[a];
@@ -134,10 +114,12 @@ int at_prepare_params(const at_config_t *cfg, double *ring_dev, uint8_t *log_dev
     const double dx = kTwoPi / (double)cfg->n[a];
     for (int j = -h; j <= h; ++j) {
       const double v = cfg->dt * (-cfg->c[a] * c1.cd[j + h] / dx + cfg->alpha * c2.cd[j + h] / (dx * dx));
-      if (j == 0) s0 += v; else p.s[a][j + h] = v;
+      const double dv = cfg->dt * c2.cd[j + h] / (dx * dx);
+      if (j == 0) { s0 += v; q0 += dv; } else { p.s[a][j + h] = v; p.q[a][j + h] = dv; }
     }
   }
   p.s0 = s0;
+  p.q0 = q0;
   for (int k = 0; k < cfg->L; ++k)
     for (int m = 0; m < T; ++m)
       p.w[k][m] = cfg->scheme == AT_AT ? c2.w[k][m] : (m == 0 ? 1.0 : 0.0);

@@ -1,6 +1,7 @@
 // internal.h -- declarations shared by the translation units of libatfd (not part of the C ABI).
 #pragma once
 #include <cstdint>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -37,6 +38,8 @@ struct StepParams {
   double zero;            // +0.0, kept opaque so the compiler issues an FMA rather than a multiply
   double s0;              // merged centre coefficient: 1 + dt sum_a (-c_a cd1_0/dx_a + alpha cd2_0/dx_a^2)
   double s[3][2 * AT_MAX_H + 1];  // merged off-centre coefficients per axis (index j+h)
+  double q0;                      // d s0 / d alpha = dt sum_a cd2_0 / dx_a^2
+  double q[3][2 * AT_MAX_H + 1];  // d s_{a,j} / d alpha = dt cd2_j / dx_a^2
   double w[AT_MAX_L][AT_MAX_T];   // halo extrapolation weights w[k][m] of level n-k-m
 };
 
@@ -67,3 +70,31 @@ cudaError_t launch_draw_delays(const StepParams &p, int64_t n, cudaStream_t st);
 cudaError_t launch_wave_field(const WaveParams &w, double t, double *tables, double *out, cudaStream_t st);
 cudaError_t launch_error_stats(const WaveParams &w, const StepParams &p, const double *u, double t,
                                double *tables, double *partials, double *result, cudaStream_t st);
+
+// The solver handle behind at_handle_t (shared by api.cu and adjoint.cu).
+struct at_handle {
+  at_config_t cfg;
+  std::vector<uint64_t> thr;
+  StepParams sp;
+  WaveParams wp;
+  int64_t log_steps = 0;
+  int64_t step = 0;
+  cudaStream_t stream = nullptr;
+  // scratch owned by the handle: status word, reduction partials and result, 3D axis tables
+  void *scratch = nullptr;
+  int32_t *d_status = nullptr;
+  double *d_partials = nullptr;
+  double *d_result = nullptr;
+  double *d_tables = nullptr;
+  int64_t *d_step = nullptr;  // step base read by the captured graph
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  // adjoint state: the forward pass with checkpoints records its schedule here
+  int64_t adj_nsteps = -1;       // steps of the checkpointed forward pass (-1: none)
+  int64_t adj_every = 0;         // checkpoint interval
+  double *adj_work = nullptr;    // caller's workspace
+  int64_t adj_work_len = 0;
+};
+
+// Steps per captured graph: long runs replay one graph of kGraphSteps kernel nodes plus a counter update.
+static const int64_t kGraphSteps = 50;

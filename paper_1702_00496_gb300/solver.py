@@ -58,6 +58,21 @@ class Solver:
     def error_stats(self) -> dict:
         return B.at_error_stats(self.h)
 
+    def adjoint_forward(self, nsteps: int, ckpt_every: int = 0) -> None:
+        """Run nsteps from step 0 keeping checkpoints every ckpt_every steps (0: ceil(sqrt(nsteps)))."""
+        n = B.at_adjoint_workspace(self.h, nsteps, ckpt_every)
+        if getattr(self, "work", None) is None or self.work.numel() < n:
+            self.work = None
+            self.work = torch.empty(n, dtype=torch.float64, device=self.device)
+        B.at_adjoint_forward(self.h, nsteps, ckpt_every, self.work)
+
+    def adjoint_backward(self, lam: torch.Tensor):
+        """dJ/dU^0 (shaped like the field) and dJ/dalpha for lam = dJ/dU^nsteps."""
+        lam = lam.reshape(-1).to(device=self.device, dtype=torch.float64).contiguous()
+        g = torch.empty(self.cfg.ntot, dtype=torch.float64, device=self.device)
+        ga = B.at_adjoint_backward(self.h, lam, g)
+        return g.view(self.cfg.shape), ga
+
     def close(self) -> None:
         if self.h is not None:
             B.at_destroy(self.h)

@@ -1,0 +1,128 @@
+"""GPU adjoint: the hand-written transposed AT step against the CPU adjoint (oracle) and against central finite
+differences of the GPU forward run; checkpoint intervals and the autograd wrapper."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+
+def _gpu_grad(spec, nsteps, target, every=0, u0=None):
+    from paper_1702_00496_gb300 import Solver
+    s = Solver(spec)
+    if u0 is not None:
+        s.reset(torch.as_tensor(u0, device="cuda"))
+    s.adjoint_forward(nsteps, every)
+    u = s.field().clone()
+    tgt = torch.as_tensor(target, device="cuda").reshape(u.shape)
+    lam = u - tgt
+    J = 0.5 * float((lam * lam).sum())
+    g, ga = s.adjoint_backward(lam)
+    out = (J, g.cpu().numpy(), ga, u.cpu().numpy())
+    s.close()
+    return out
+
+
+CASES = [
+    ("1d_o4_L3", lambda: W.wl_1d(256, 8, 4, 3, 0, 61, (1, 2, 3))[0], 80),
+    ("1d_o2_L4", lambda: W.wl_1d(192, 6, 2, 4, 0, 62, (1, 4))[0], 90),
+    ("1d_o4_std", lambda: W.wl_1d(256, 8, 4, 3, 0, 63, (1, 2), scheme=W.ASYNC_STD)[0], 60),
+    ("1d_o4_sync", lambda: W.wl_1d(256, 8, 4, 3, 0, 64, (1, 2), scheme=W.SYNC)[0], 60),
+    ("1d_point_path", lambda: W.wl_1d(250, 5, 4, 3, 0, 65, (1, 2))[0], 50),
+    ("3d_o4", lambda: W.wl_3d([16, 12, 8], [2, 2, 2], 4, 3, 0, 66, c=(0.3, 0.2, 0.1))[0], 20),
+    ("3d_o2_unsplit", lambda: W.wl_3d([12, 16, 8], [3, 1, 2], 2, 4, 0, 67, c=(0.2, 0.2, 0.2))[0], 25),
+]
+
+
+@pytest.mark.parametrize("name,make,nsteps", CASES, ids=[c[0] for c in CASES])
+def test_adjoint_matches_cpu_adjoint(name, make, nsteps):
+    spec = make()
+    cfg = oracle.Config(spec)
+    rng = np.random.default_rng(3)
+    target = 0.5 * oracle.initial(cfg) + 0.1 * rng.standard_normal(cfg.shape)
+    J, g, ga, _ = _gpu_grad(spec, nsteps, target)
+    Jo, go, gao = oracle.adjoint(cfg, nsteps, target)
+    assert J == pytest.approx(Jo, rel=1e-11)
+    assert np.linalg.norm(g - go) / np.linalg.norm(go) <= 1e-12
+    assert ga == pytest.approx(gao, rel=1e-10)
+
+
+def test_checkpoint_interval_does_not_change_the_gradient():
+    spec, _ = W.wl_1d(512, 8, 4, 4, 0, 71, (1, 2, 3))
+    target = np.zeros(512)
+    ref = None
+    for every in (0, 1, 5, 13, 97):
+        J, g, ga, _ = _gpu_grad(spec, 97, target, every)
+        if ref is None:
+            ref = (J, g, ga)
+        assert J == ref[0] and ga == ref[2] and np.array_equal(g, ref[1]), every
+
+
+def test_zero_steps_gradient_is_the_seed():
+    spec, _ = W.wl_1d(128, 4, 4, 3, 0, 72, (1, 2))
+    target = np.ones(128)
+    J, g, ga, u = _gpu_grad(spec, 0, target)
+    assert np.array_equal(g, u - target) and ga == 0.0
+
+
+def test_autograd_function():
+    from paper_1702_00496_gb300 import at_forward
+    spec, _ = W.wl_3d([16, 12, 8], [2, 2, 2], 4, 3, 0, 73, c=(0.3, 0.2, 0.1))
+    cfg = oracle.Config(spec)
+    u0 = torch.as_tensor(oracle.initial(cfg), device="cuda").requires_grad_(True)
+    alpha = torch.tensor(spec["alpha"], dtype=torch.float64, device="cuda", requires_grad=True)
+    target = torch.zeros_like(u0)
+    u = at_forward(u0, alpha, spec, 15)
+    loss = 0.5 * ((u - target) ** 2).sum()
+    loss.backward()
+    Jo, go, gao = oracle.adjoint(cfg, 15, np.zeros(cfg.shape))
+    assert float(loss) == pytest.approx(Jo, rel=1e-11)
+    assert np.linalg.norm(u0.grad.cpu().numpy() - go) / np.linalg.norm(go) <= 1e-12
+    assert float(alpha.grad) == pytest.approx(gao, rel=1e-10)
+
+
+def test_full_size_adjoint_against_finite_differences():
+    """256^3, 4^3 PEs, order 4, L = 3, 2000 steps; u_target from a forward run at alpha = 0.06 with the same
+    delays; the gradient in u0 against central differences on 16 random directions (exact for the quadratic
+    misfit up to rounding) and the alpha derivative against Richardson-extrapolated differences."""
+    from paper_1702_00496_gb300 import Solver
+    spec, nsteps = W.workload("adjoint_256")
+    t_spec = dict(spec)
+    t_spec["alpha"] = 0.06
+    s = Solver(t_spec)
+    s.step(nsteps)
+    target = s.field().clone()
+    s.close()
+    s = Solver(spec)
+    u0 = s.field().clone()
+    s.adjoint_forward(nsteps)
+    lam = s.field() - target
+    g, ga = s.adjoint_backward(lam.clone())
+    s.close()
+
+    def J(u_init, alpha=spec["alpha"]):
+        sp = dict(spec)
+        sp["alpha"] = alpha
+        sv = Solver(sp)
+        sv.reset(u_init)
+        sv.step(nsteps)
+        r = sv.field() - target
+        val = 0.5 * float(torch.dot(r.reshape(-1), r.reshape(-1)))
+        sv.close()
+        return val
+
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    for _ in range(16):
+        v = torch.randn(u0.shape, dtype=torch.float64, device="cuda", generator=gen)
+        eps = 1e-2
+        fd = (J(u0 + eps * v) - J(u0 - eps * v)) / (2 * eps)
+        assert float(torch.dot(g.reshape(-1), v.reshape(-1))) == pytest.approx(fd, rel=1e-6)
+    a0 = spec["alpha"]
+    h = 1e-3 * a0
+    d1 = (J(u0, a0 + h) - J(u0, a0 - h)) / (2 * h)
+    d2 = (J(u0, a0 + h / 2) - J(u0, a0 - h / 2)) / h
+    assert ga == pytest.approx((4 * d2 - d1) / 3, rel=1e-6)
