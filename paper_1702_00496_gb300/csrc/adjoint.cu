@@ -121,6 +121,128 @@ __device__ void adjoint_cell(const AdjParams &a, const uint8_t *__restrict__ kef
   }
 }
 
+// Edge group: the four cells x0..x0+3 of row (y, z) when some of them lie within h of a PE edge (or the stencil
+// wraps around the domain).  Neighbour points i = c - j in another PE read c as a buffer point; their
+// contributions are summed per PE side (one side per axis, two along x) and sent to the levels n-k-m of that
+// side's delay k with weights w_m(k).  The fresh level n-R+2 is zeroed before any contribution lands in it.
+template <int DIM, int H>
+__device__ __forceinline__ void adjoint_group(const AdjParams &a, const uint8_t *__restrict__ keff, int64_t n, int x0,
+                                              int y, int z, double &galpha) {
+  const StepParams &f = a.f;
+  const int64_t N = f.ntot;
+  const int nx = f.n[0];
+  const int64_t row = DIM == 3 ? ((int64_t)z * f.n[1] + y) * nx : 0;
+  const int64_t i0 = row + x0;
+  const double *ln = a.lam + ((n + 1) % a.Rl) * N;
+  double d[4];
+  group_eval<DIM, H, LdgNC, true>(f, keff, f.ring + (n % f.R) * N, n, x0, y, z, d);
+  int pidx[3] = {x0 / f.S[0], 0, 0}, pos[3] = {0, 0, 0};
+  pos[0] = x0 - pidx[0] * f.S[0];
+  if (DIM == 3) {
+    pidx[1] = y / f.S[1]; pos[1] = y - pidx[1] * f.S[1];
+    pidx[2] = z / f.S[2]; pos[2] = z - pidx[2] * f.S[2];
+  }
+  double lv[8];
+  if (x0 >= 2 && x0 + 6 <= nx) {
+    const double2 l0 = LdgNC::ld2(ln + i0 - 2), l1 = LdgNC::ld2(ln + i0), l2 = LdgNC::ld2(ln + i0 + 2),
+                  l3 = LdgNC::ld2(ln + i0 + 4);
+    lv[0] = l0.x; lv[1] = l0.y; lv[2] = l1.x; lv[3] = l1.y; lv[4] = l2.x; lv[5] = l2.y; lv[6] = l3.x; lv[7] = l3.y;
+  } else {
+#pragma unroll
+    for (int t = 0; t < 8; ++t) lv[t] = LdgNC::ld(ln + row + wrap_coord(x0 - 2 + t, nx));
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) galpha = fma(lv[q + 2], d[q], galpha);
+  // x: window element t is point i = x0-2+t; rel < 0 lies in the lower PE (reads c on its high side),
+  // rel >= S in the upper PE (reads c on its low side)
+  int kxl = 0, kxr = 0;
+  if (f.use_pe[0]) {
+    int pl[3] = {(pidx[0] + f.pe[0] - 1) % f.pe[0], pidx[1], pidx[2]};
+    int pr[3] = {(pidx[0] + 1) % f.pe[0], pidx[1], pidx[2]};
+    kxl = keff[side_of<DIM>(f, pl, 0, 1)];
+    kxr = keff[side_of<DIM>(f, pr, 0, 0)];
+  }
+  double A[4], X[4][4];  // X[0]: lower x PE, X[1]: upper x PE, X[2]: y neighbour PE, X[3]: z neighbour PE
+  int kX[4] = {kxl, kxr, 0, 0};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    A[q] = fma(f.s0, lv[q + 2], f.zero);
+    X[0][q] = X[1][q] = X[2][q] = X[3][q] = 0.0;
+#pragma unroll
+    for (int j = -H; j <= H; ++j) {
+      if (j == 0) continue;
+      const int t = q + 2 - j;
+      const int rel = pos[0] - 2 + t;
+      const double s = f.s[0][j + H];
+      if (rel < 0 && kxl > 0) X[0][q] = fma(s, lv[t], X[0][q]);
+      else if (rel >= f.S[0] && kxr > 0) X[1][q] = fma(s, lv[t], X[1][q]);
+      else A[q] = fma(s, lv[t], A[q]);
+    }
+  }
+  if (DIM == 3) {
+#pragma unroll
+    for (int ax = 1; ax < 3; ++ax) {
+      const int c = ax == 1 ? y : z, na = f.n[ax];
+      const int64_t st = ax == 1 ? (int64_t)nx : (int64_t)nx * f.n[1];
+#pragma unroll
+      for (int j = -H; j <= H; ++j) {
+        if (j == 0) continue;
+        const int ia = wrap_coord(c - j, na);
+        const int64_t base = i0 + (int64_t)(ia - c) * st;
+        int k = 0;
+        if (f.use_pe[ax]) {
+          const int pi = ia / f.S[ax];
+          if (pi != pidx[ax]) {
+            int pid[3] = {pidx[0], pidx[1], pidx[2]};
+            pid[ax] = pi;
+            k = keff[side_of<DIM>(f, pid, ax, j > 0 ? 1 : 0)];
+          }
+        }
+        const double2 e = LdgNC::ld2(ln + base), g = LdgNC::ld2(ln + base + 2);
+        const double lr[4] = {e.x, e.y, g.x, g.y};
+        const double s = f.s[ax][j + H];
+        if (k > 0) {
+          kX[ax + 1] = k;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) X[ax + 1][q] = fma(s, lr[q], X[ax + 1][q]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) A[q] = fma(s, lr[q], A[q]);
+        }
+      }
+    }
+  }
+  const int64_t fresh = n - a.Rl + 2;
+  double2 *cur = reinterpret_cast<double2 *>(a.lam + (n % a.Rl) * N + i0);
+  if (a.Rl == 2) {
+    cur[0] = make_double2(A[0], A[1]);
+    cur[1] = make_double2(A[2], A[3]);
+    return;
+  }
+  if (fresh >= 0) {
+    double2 *fr = reinterpret_cast<double2 *>(a.lam + (fresh % a.Rl) * N + i0);
+    fr[0] = make_double2(0.0, 0.0);
+    fr[1] = make_double2(0.0, 0.0);
+  }
+  {
+    const double2 p0 = cur[0], p1 = cur[1];
+    cur[0] = make_double2(p0.x + A[0], p0.y + A[1]);
+    cur[1] = make_double2(p1.x + A[2], p1.y + A[3]);
+  }
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const int k = kX[b];
+    if (k == 0) continue;
+    for (int m = 0; m < f.T; ++m) {
+      const double wk = f.w[k][m];
+      double2 *o = reinterpret_cast<double2 *>(a.lam + ((n - k - m) % a.Rl) * N + i0);
+      const double2 p0 = o[0], p1 = o[1];
+      o[0] = make_double2(fma(wk, X[b][0], p0.x), fma(wk, X[b][1], p0.y));
+      o[1] = make_double2(fma(wk, X[b][2], p1.x), fma(wk, X[b][3], p1.y));
+    }
+  }
+}
+
 // Backward step n.  G: cells come in groups of four x points (n[0] % 4 == 0, 16-byte aligned slots); a group
 // whose cells and neighbours all lie inside one PE and away from the domain ends takes the straight path.
 template <int DIM, int H, bool G>
@@ -160,10 +282,7 @@ __global__ void __launch_bounds__(256) adjoint_step_kernel(const AdjParams a, co
                  (z >= H) && (z + H < nz) && (!f.use_pe[2] || (pz >= H && pz < f.S[2] - H));
       }
       if (!inside) {
-        for (int q = 0; q < 4; ++q) {
-          const int c[3] = {x0 + q, y, z};
-          adjoint_cell<DIM, H>(a, keff, n, i0 + q, c, galpha);
-        }
+        adjoint_group<DIM, H>(a, keff, n, x0, y, z, galpha);
         continue;
       }
       double lv[8], uv[8];

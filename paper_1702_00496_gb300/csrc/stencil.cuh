@@ -64,12 +64,13 @@ __device__ __forceinline__ int64_t side_of(const StepParams &p, const int pidx[3
   return 2 * (int64_t)DIM * pe + 2 * a + hi;
 }
 
-// Update the four points x0..x0+3 of row (y, z); requires n[0] % 4 == 0 (1D: the group count covers N) and a
-// 16-byte aligned slot.  keff: effective delays of step n.
-template <int DIM, int H, class LD>
-__device__ __forceinline__ void group_update(const StepParams &p, const uint8_t *__restrict__ keff,
-                                             const double *__restrict__ un, double *__restrict__ out, int64_t n,
-                                             int x0, int y, int z) {
+// The merged stencil of the four points x0..x0+3 of row (y, z) into r[4]; requires n[0] % 4 == 0 and a
+// 16-byte aligned slot.  keff: effective delays of step n.  ALPHA = true evaluates the alpha derivative of the
+// step instead (coefficients q0, q: dt times the AT second derivative).
+template <int DIM, int H, class LD, bool ALPHA>
+__device__ __forceinline__ void group_eval(const StepParams &p, const uint8_t *__restrict__ keff,
+                                           const double *__restrict__ un, int64_t n, int x0, int y, int z,
+                                           double r[4]) {
   const int nx = p.n[0];
   const int64_t row = DIM == 3 ? ((int64_t)z * p.n[1] + y) * nx : 0;
   const int64_t i0 = row + x0;
@@ -97,13 +98,13 @@ __device__ __forceinline__ void group_update(const StepParams &p, const uint8_t 
       if (k > 0) v[t] = halo_value<LD>(p, row + wrap_coord(x0 - 2 + t, nx), n, k);
     }
   }
-  double r[4];
+  const double c0 = ALPHA ? p.q0 : p.s0;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    double acc = fma(p.s0, v[q + 2], p.zero);
+    double acc = fma(c0, v[q + 2], p.zero);
 #pragma unroll
     for (int j = -H; j <= H; ++j)
-      if (j != 0) acc = fma(p.s[0][j + H], v[q + 2 + j], acc);
+      if (j != 0) acc = fma(ALPHA ? p.q[0][j + H] : p.s[0][j + H], v[q + 2 + j], acc);
     r[q] = acc;
   }
   if (DIM == 3) {
@@ -131,12 +132,22 @@ __device__ __forceinline__ void group_update(const StepParams &p, const uint8_t 
           const double2 e = LD::ld2(un + base), f = LD::ld2(un + base + 2);
           w[0] = e.x; w[1] = e.y; w[2] = f.x; w[3] = f.y;
         }
-        const double s = p.s[a][j + H];
+        const double s = ALPHA ? p.q[a][j + H] : p.s[a][j + H];
 #pragma unroll
         for (int q = 0; q < 4; ++q) r[q] = fma(s, w[q], r[q]);
       }
     }
   }
+}
+
+// Update the four points x0..x0+3 of row (y, z) (the forward step).
+template <int DIM, int H, class LD>
+__device__ __forceinline__ void group_update(const StepParams &p, const uint8_t *__restrict__ keff,
+                                             const double *__restrict__ un, double *__restrict__ out, int64_t n,
+                                             int x0, int y, int z) {
+  double r[4];
+  group_eval<DIM, H, LD, false>(p, keff, un, n, x0, y, z, r);
+  const int64_t i0 = (DIM == 3 ? ((int64_t)z * p.n[1] + y) * p.n[0] : 0) + x0;
   reinterpret_cast<double2 *>(out + i0)[0] = make_double2(r[0], r[1]);
   reinterpret_cast<double2 *>(out + i0)[1] = make_double2(r[2], r[3]);
 }
