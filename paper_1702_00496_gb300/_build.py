@@ -45,7 +45,7 @@ def _compile(src: str, verbose_ptxas: bool) -> str:
     cmd = [nvcc(), "-c", src, "-o", obj, "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
            "-I", os.path.join(ROOT, "include"), "--expt-relaxed-constexpr"]
     if src.endswith(".cu"):
-        cmd += ARCH + ["-lineinfo"]
+        cmd += ARCH + ["-lineinfo"] + os.environ.get("ATFD_NVCC_FLAGS", "").split()
         if verbose_ptxas:
             cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -245,12 +245,24 @@ __device__ __forceinline__ void adjoint_group(const AdjParams &a, const uint8_t 
 
 // Backward step n.  G: cells come in groups of four x points (n[0] % 4 == 0, 16-byte aligned slots); a group
 // whose cells and neighbours all lie inside one PE and away from the domain ends takes the straight path.
-template <int DIM, int H, bool G>
-__global__ void __launch_bounds__(256) adjoint_step_kernel(const AdjParams a, const int64_t n) {
+// MODE 0: every cell by the general path (shapes without groups of four).  MODE 1: interior groups only.
+// MODE 2: edge groups only, plus the draw of the delays of step n-1.  The two grouped launches of a step touch
+// disjoint cells and add their alpha partials into the same per-block slots in launch order.
+#ifndef AT_ADJ_MIN_BLOCKS
+#define AT_ADJ_MIN_BLOCKS 3
+#endif
+template <int MODE>
+struct AdjBounds {
+  static constexpr int min_blocks = MODE == 1 ? AT_ADJ_MIN_BLOCKS : 2;
+};
+template <int DIM, int H, int MODE>
+__global__ void __launch_bounds__(256, AdjBounds<MODE>::min_blocks) adjoint_step_kernel(const AdjParams a,
+                                                                                      const int64_t n) {
+  constexpr bool G = MODE != 0;
   const StepParams &f = a.f;
   const int64_t N = f.ntot;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nthreads = (int64_t)gridDim.x * blockDim.x;
-  if (n >= 1) draw_sides(f, n - 1, tid, nthreads, a.akeff + ((n - 1) & 1) * f.nb);
+  if (n >= 1 && MODE != 1) draw_sides(f, n - 1, tid, nthreads, a.akeff + ((n - 1) & 1) * f.nb);
   const uint8_t *keff = a.akeff + (n & 1) * f.nb;
   double galpha = 0.0;
   if (!G) {
@@ -282,9 +294,10 @@ __global__ void __launch_bounds__(256) adjoint_step_kernel(const AdjParams a, co
                  (z >= H) && (z + H < nz) && (!f.use_pe[2] || (pz >= H && pz < f.S[2] - H));
       }
       if (!inside) {
-        adjoint_group<DIM, H>(a, keff, n, x0, y, z, galpha);
+        if (MODE == 2) adjoint_group<DIM, H>(a, keff, n, x0, y, z, galpha);
         continue;
       }
+      if (MODE == 2) continue;
       double lv[8], uv[8];
       {
         const double2 l0 = LdgNC::ld2(ln + i0 - 2), l1 = LdgNC::ld2(ln + i0), l2 = LdgNC::ld2(ln + i0 + 2),
@@ -367,19 +380,25 @@ int adj_blocks() {
   return sms * 8;
 }
 
+template <int DIM, int H>
+void launch_modes(const AdjParams &a, int64_t n, int nblk, bool grouped, cudaStream_t st) {
+  if (grouped) {
+    adjoint_step_kernel<DIM, H, 2><<<nblk, kAdjThreads, 0, st>>>(a, n);
+    adjoint_step_kernel<DIM, H, 1><<<nblk, kAdjThreads, 0, st>>>(a, n);
+  } else {
+    adjoint_step_kernel<DIM, H, 0><<<nblk, kAdjThreads, 0, st>>>(a, n);
+  }
+}
+
 cudaError_t launch_adjoint_step(const AdjParams &a, int64_t n, int nblk, cudaStream_t st) {
   const bool grouped = a.f.n[0] % 4 == 0 && (!a.f.use_pe[0] || a.f.S[0] % 4 == 0) &&
                        (reinterpret_cast<uintptr_t>(a.lam) % 16) == 0 && (reinterpret_cast<uintptr_t>(a.f.ring) % 16) == 0;
   if (a.f.dim == 1) {
-    if (a.f.h == 1) grouped ? adjoint_step_kernel<1, 1, true><<<nblk, kAdjThreads, 0, st>>>(a, n)
-                            : adjoint_step_kernel<1, 1, false><<<nblk, kAdjThreads, 0, st>>>(a, n);
-    else grouped ? adjoint_step_kernel<1, 2, true><<<nblk, kAdjThreads, 0, st>>>(a, n)
-                 : adjoint_step_kernel<1, 2, false><<<nblk, kAdjThreads, 0, st>>>(a, n);
+    if (a.f.h == 1) launch_modes<1, 1>(a, n, nblk, grouped, st);
+    else launch_modes<1, 2>(a, n, nblk, grouped, st);
   } else {
-    if (a.f.h == 1) grouped ? adjoint_step_kernel<3, 1, true><<<nblk, kAdjThreads, 0, st>>>(a, n)
-                            : adjoint_step_kernel<3, 1, false><<<nblk, kAdjThreads, 0, st>>>(a, n);
-    else grouped ? adjoint_step_kernel<3, 2, true><<<nblk, kAdjThreads, 0, st>>>(a, n)
-                 : adjoint_step_kernel<3, 2, false><<<nblk, kAdjThreads, 0, st>>>(a, n);
+    if (a.f.h == 1) launch_modes<3, 1>(a, n, nblk, grouped, st);
+    else launch_modes<3, 2>(a, n, nblk, grouped, st);
   }
   return cudaGetLastError();
 }
