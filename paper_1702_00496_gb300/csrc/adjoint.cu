@@ -106,7 +106,7 @@ __device__ void adjoint_cell(const AdjParams &a, const uint8_t *__restrict__ kef
       int kc = 0;
       if (edge && pos[ax] + j < 0) kc = keff[side_of<DIM>(f, pidx, ax, 0)];
       if (edge && pos[ax] + j >= f.S[ax]) kc = keff[side_of<DIM>(f, pidx, ax, 1)];
-      const double v = kc > 0 ? halo_value<LdgNC>(f, cell, n, kc) : __ldg(un + cell);
+      const double v = kc > 0 ? halo_value<LdgNC>(f, cell, (int)(n % f.R), kc) : __ldg(un + cell);
       d2 = fma(f.q[ax][j + H], v, d2);
     }
   }
@@ -213,14 +213,15 @@ __device__ __forceinline__ void adjoint_group(const AdjParams &a, const uint8_t 
     }
   }
   const int64_t fresh = n - a.Rl + 2;
-  double2 *cur = reinterpret_cast<double2 *>(a.lam + (n % a.Rl) * N + i0);
+  const int snl = (int)(n % a.Rl);
+  double2 *cur = reinterpret_cast<double2 *>(a.lam + snl * N + i0);
   if (a.Rl == 2) {
     cur[0] = make_double2(A[0], A[1]);
     cur[1] = make_double2(A[2], A[3]);
     return;
   }
   if (fresh >= 0) {
-    double2 *fr = reinterpret_cast<double2 *>(a.lam + (fresh % a.Rl) * N + i0);
+    double2 *fr = reinterpret_cast<double2 *>(a.lam + slot_back(snl, a.Rl - 2, a.Rl) * N + i0);
     fr[0] = make_double2(0.0, 0.0);
     fr[1] = make_double2(0.0, 0.0);
   }
@@ -235,7 +236,7 @@ __device__ __forceinline__ void adjoint_group(const AdjParams &a, const uint8_t 
     if (k == 0) continue;
     for (int m = 0; m < f.T; ++m) {
       const double wk = f.w[k][m];
-      double2 *o = reinterpret_cast<double2 *>(a.lam + ((n - k - m) % a.Rl) * N + i0);
+      double2 *o = reinterpret_cast<double2 *>(a.lam + slot_back(snl, k + m, a.Rl) * N + i0);
       const double2 p0 = o[0], p1 = o[1];
       o[0] = make_double2(fma(wk, X[b][0], p0.x), fma(wk, X[b][1], p0.y));
       o[1] = make_double2(fma(wk, X[b][2], p1.x), fma(wk, X[b][3], p1.y));

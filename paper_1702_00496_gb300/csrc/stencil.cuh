@@ -44,14 +44,21 @@ __device__ __forceinline__ void draw_sides(const StepParams &p, int64_t n, int64
   }
 }
 
-// Halo value of `cell` seen across a PE side with effective delay k >= 1 (T successive levels).
+// Slot of the level `back` levels below the level in slot sn (0 <= back < R): no 64-bit modulo per load.
+__device__ __forceinline__ int64_t slot_back(int sn, int back, int R) {
+  const int s = sn - back;
+  return s < 0 ? s + R : s;
+}
+
+// Halo value of `cell` seen across a PE side with effective delay k >= 1 (T successive levels); sn is the
+// slot of level n.
 template <class LD>
-__device__ __forceinline__ double halo_value(const StepParams &p, int64_t cell, int64_t n, int k) {
-  double acc = fma(p.w[k][0], LD::ld(p.ring + ((n - k) % p.R) * p.ntot + cell), p.zero);
+__device__ __forceinline__ double halo_value(const StepParams &p, int64_t cell, int sn, int k) {
+  double acc = fma(p.w[k][0], LD::ld(p.ring + slot_back(sn, k, p.R) * p.ntot + cell), p.zero);
 #pragma unroll
   for (int m = 1; m < AT_MAX_T; ++m) {
     if (m >= p.T) break;
-    acc = fma(p.w[k][m], LD::ld(p.ring + ((n - k - m) % p.R) * p.ntot + cell), acc);
+    acc = fma(p.w[k][m], LD::ld(p.ring + slot_back(sn, k + m, p.R) * p.ntot + cell), acc);
   }
   return acc;
 }
@@ -72,6 +79,7 @@ __device__ __forceinline__ void group_eval(const StepParams &p, const uint8_t *_
                                            const double *__restrict__ un, int64_t n, int x0, int y, int z,
                                            double r[4]) {
   const int nx = p.n[0];
+  const int sn = (int)(n % p.R);
   const int64_t row = DIM == 3 ? ((int64_t)z * p.n[1] + y) * nx : 0;
   const int64_t i0 = row + x0;
   int pidx[3] = {x0 / p.S[0], 0, 0}, pos[3] = {0, 0, 0};
@@ -95,7 +103,7 @@ __device__ __forceinline__ void group_eval(const StepParams &p, const uint8_t *_
     for (int t = 2 - H; t <= 5 + H; ++t) {
       const int rel = pos[0] - 2 + t;
       const int k = rel < 0 ? kl : (rel >= p.S[0] ? kr : 0);
-      if (k > 0) v[t] = halo_value<LD>(p, row + wrap_coord(x0 - 2 + t, nx), n, k);
+      if (k > 0) v[t] = halo_value<LD>(p, row + wrap_coord(x0 - 2 + t, nx), sn, k);
     }
   }
   const double c0 = ALPHA ? p.q0 : p.s0;
@@ -127,7 +135,7 @@ __device__ __forceinline__ void group_eval(const StepParams &p, const uint8_t *_
         double w[4];
         if (k > 0) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) w[q] = halo_value<LD>(p, base + q, n, k);
+          for (int q = 0; q < 4; ++q) w[q] = halo_value<LD>(p, base + q, sn, k);
         } else {
           const double2 e = LD::ld2(un + base), f = LD::ld2(un + base + 2);
           w[0] = e.x; w[1] = e.y; w[2] = f.x; w[3] = f.y;
@@ -175,7 +183,7 @@ __device__ double point_update(const StepParams &p, const uint8_t *__restrict__ 
       int k = 0;
       if (edge && pos[a] + j < 0) k = keff[side_of<DIM>(p, pidx, a, 0)];
       if (edge && pos[a] + j >= p.S[a]) k = keff[side_of<DIM>(p, pidx, a, 1)];
-      const double v = k > 0 ? halo_value<LD>(p, cell, n, k) : LD::ld(un + cell);
+      const double v = k > 0 ? halo_value<LD>(p, cell, (int)(n % p.R), k) : LD::ld(un + cell);
       acc = fma(p.s[a][j + H], v, acc);
     }
   }
