@@ -39,6 +39,9 @@ struct AdjParams {
   int32_t Rl;          // = L + T of the problem
   uint8_t *akeff;      // effective delays of the forward steps the backward sweep replays (two buffers)
   double *g_blk;       // per-block accumulators of d J / d alpha
+  const int32_t *list; // group indices of this launch (interior groups for MODE 1, edge groups for MODE 2)
+  int64_t list_len;
+  int64_t edge_len;    // on the host: the edge groups come first in the list
 };
 
 // Block sum of v into g_blk[blockIdx.x] (warp shuffles, then warp 0 in warp order).
@@ -279,26 +282,19 @@ __global__ void __launch_bounds__(256, AdjBounds<MODE>::min_blocks) adjoint_step
   } else {
     const double *ln = a.lam + ((n + 1) % a.Rl) * N;
     const double *un = f.ring + (n % f.R) * N;
-    const int nx = f.n[0], ny = f.n[1], nz = f.n[2];
+    const int nx = f.n[0], ny = f.n[1];
     const int gx = nx >> 2;
-    const int64_t groups = N >> 2;
-    for (int64_t g = tid; g < groups; g += nthreads) {
+    // the host partitions the groups into interior and edge lists, so a warp's lanes take the same path
+    for (int64_t e = tid; e < a.list_len; e += nthreads) {
+      const int64_t g = a.list[e];
       const int64_t r = g / gx;
       const int x0 = (int)(g - r * gx) << 2;
       const int z = DIM == 3 ? (int)(r / ny) : 0, y = DIM == 3 ? (int)(r - (int64_t)z * ny) : 0;
       const int64_t i0 = r * nx + x0;
-      const int px = x0 % f.S[0];
-      bool inside = (x0 >= 2) && (x0 + 6 <= nx) && (!f.use_pe[0] || (px >= H && px + 3 < f.S[0] - H));
-      if (DIM == 3) {
-        const int py = y % f.S[1], pz = z % f.S[2];
-        inside = inside && (y >= H) && (y + H < ny) && (!f.use_pe[1] || (py >= H && py < f.S[1] - H)) &&
-                 (z >= H) && (z + H < nz) && (!f.use_pe[2] || (pz >= H && pz < f.S[2] - H));
-      }
-      if (!inside) {
-        if (MODE == 2) adjoint_group<DIM, H>(a, keff, n, x0, y, z, galpha);
+      if (MODE == 2) {
+        adjoint_group<DIM, H>(a, keff, n, x0, y, z, galpha);
         continue;
       }
-      if (MODE == 2) continue;
       double lv[8], uv[8];
       {
         const double2 l0 = LdgNC::ld2(ln + i0 - 2), l1 = LdgNC::ld2(ln + i0), l2 = LdgNC::ld2(ln + i0 + 2),
@@ -384,16 +380,42 @@ int adj_blocks() {
 template <int DIM, int H>
 void launch_modes(const AdjParams &a, int64_t n, int nblk, bool grouped, cudaStream_t st) {
   if (grouped) {
-    adjoint_step_kernel<DIM, H, 2><<<nblk, kAdjThreads, 0, st>>>(a, n);
-    adjoint_step_kernel<DIM, H, 1><<<nblk, kAdjThreads, 0, st>>>(a, n);
+    AdjParams e = a, i = a;
+    e.list = a.list;
+    e.list_len = a.edge_len;
+    i.list = a.list + a.edge_len;
+    i.list_len = a.list_len - a.edge_len;
+    adjoint_step_kernel<DIM, H, 2><<<nblk, kAdjThreads, 0, st>>>(e, n);
+    adjoint_step_kernel<DIM, H, 1><<<nblk, kAdjThreads, 0, st>>>(i, n);
   } else {
     adjoint_step_kernel<DIM, H, 0><<<nblk, kAdjThreads, 0, st>>>(a, n);
   }
 }
 
+bool adjoint_grouped(const AdjParams &a) {
+  return a.f.n[0] % 4 == 0 && (!a.f.use_pe[0] || a.f.S[0] % 4 == 0) &&
+         (reinterpret_cast<uintptr_t>(a.lam) % 16) == 0 && (reinterpret_cast<uintptr_t>(a.f.ring) % 16) == 0;
+}
+
+// Group g (x0 = 4 (g mod nx/4), row g div nx/4) is interior when its cells and all their stencil neighbours lie in
+// its PE and away from the domain ends: the straight path of the interior launch applies.
+bool group_interior(const StepParams &f, int64_t g) {
+  const int h = f.h, nx = (int)f.n[0], gx = nx / 4;
+  const int64_t r = g / gx;
+  const int x0 = (int)(g - r * gx) * 4;
+  const int px = x0 % f.S[0];
+  bool in = x0 >= 2 && x0 + 6 <= nx && (!f.use_pe[0] || (px >= h && px + 3 < f.S[0] - h));
+  if (f.dim == 3) {
+    const int z = (int)(r / f.n[1]), y = (int)(r - (int64_t)z * f.n[1]);
+    const int py = y % f.S[1], pz = z % f.S[2];
+    in = in && y >= h && y + h < f.n[1] && (!f.use_pe[1] || (py >= h && py < f.S[1] - h)) && z >= h &&
+         z + h < f.n[2] && (!f.use_pe[2] || (pz >= h && pz < f.S[2] - h));
+  }
+  return in;
+}
+
 cudaError_t launch_adjoint_step(const AdjParams &a, int64_t n, int nblk, cudaStream_t st) {
-  const bool grouped = a.f.n[0] % 4 == 0 && (!a.f.use_pe[0] || a.f.S[0] % 4 == 0) &&
-                       (reinterpret_cast<uintptr_t>(a.lam) % 16) == 0 && (reinterpret_cast<uintptr_t>(a.f.ring) % 16) == 0;
+  const bool grouped = adjoint_grouped(a);
   if (a.f.dim == 1) {
     if (a.f.h == 1) launch_modes<1, 1>(a, n, nblk, grouped, st);
     else launch_modes<1, 2>(a, n, nblk, grouped, st);
@@ -427,7 +449,7 @@ namespace {
 //   g_blk        nblk                   per-block d J / d alpha accumulators, then the sum
 //   delays       2 x 2 x nb bytes       effective delays of the recompute and of the backward sweep
 struct AdjLayout {
-  int64_t s, nck, seg_depth, ck, seg, lam, gblk, keff, total;
+  int64_t s, nck, seg_depth, ck, seg, lam, gblk, keff, list, total;
 };
 
 int64_t up32(int64_t v) { return (v + 31) / 32 * 32; }
@@ -444,7 +466,8 @@ AdjLayout layout(const at_handle *hd, int64_t nsteps, int64_t every) {
   L.lam = L.seg + up32(L.seg_depth * N);
   L.gblk = L.lam + up32(R * N);
   L.keff = L.gblk + up32(adj_blocks() + 1);
-  L.total = L.keff + up32((4 * hd->sp.nb + 7) / 8);
+  L.list = L.keff + up32((4 * hd->sp.nb + 7) / 8);
+  L.total = L.list + up32((hd->sp.ntot / 4 + 1) / 2);
   return L;
 }
 
@@ -512,6 +535,23 @@ extern "C" int at_adjoint_backward(at_handle_t *hd, const double *lambda_dev, do
   a.Rl = (int32_t)R;
   a.akeff = reinterpret_cast<uint8_t *>(w + L.keff) + 2 * hd->sp.nb;
   a.g_blk = w + L.gblk;
+  a.list = reinterpret_cast<int32_t *>(w + L.list);
+  a.list_len = 0;
+  a.edge_len = 0;
+  if (adjoint_grouped(a)) {  // edge groups first, then interior groups
+    const int64_t groups = N / 4;
+    std::vector<int32_t> list;
+    list.reserve((size_t)groups);
+    for (int64_t g = 0; g < groups; ++g)
+      if (!group_interior(seg, g)) list.push_back((int32_t)g);
+    a.edge_len = (int64_t)list.size();
+    for (int64_t g = 0; g < groups; ++g)
+      if (group_interior(seg, g)) list.push_back((int32_t)g);
+    a.list_len = (int64_t)list.size();
+    e = cudaMemcpyAsync(w + L.list, list.data(), sizeof(int32_t) * list.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "at_adjoint_backward: group lists");
+  }
   // lambda^Ns = the caller's seed; the R-2 older levels start at zero; alpha accumulators at zero
   e = copy_field(a.lam + (Ns % R) * N, lambda_dev, N, st);
   for (int64_t m = 1; m <= R - 2 && e == cudaSuccess; ++m)
