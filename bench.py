@@ -227,7 +227,7 @@ def run_adjoint(args, rank: int, world: int, local: int):
     s = Solver(spec, device=f"cuda:{local}", stream=stream)
     target = torch.zeros(ntot, dtype=torch.float64, device=f"cuda:{local}")
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
-    fwd, adj = [], []
+    fwd, adj, adj_u0 = [], [], []
     for it in range(args.warmup + args.steps):
         s.reset()
         a, b = ev(), ev()
@@ -241,10 +241,17 @@ def run_adjoint(args, rank: int, world: int, local: int):
         lam = s.field().reshape(-1) - target
         g, ga = s.adjoint_backward(lam)
         d.record(stream)
+        s.reset()
+        e, f = ev(), ev()
+        e.record(stream)
+        s.adjoint_forward(T)
+        g0, _ = s.adjoint_backward(s.field().reshape(-1) - target, want_alpha=False)
+        f.record(stream)
         torch.cuda.synchronize()
         if it >= args.warmup:
             fwd.append(a.elapsed_time(b))
             adj.append(c.elapsed_time(d))
+            adj_u0.append(e.elapsed_time(f))
     s.close()
     f_ms, a_ms = statistics.median(fwd), statistics.median(adj)
     if rank == 0:
@@ -253,6 +260,10 @@ def run_adjoint(args, rank: int, world: int, local: int):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": "adjoint_256", "points": ntot, "time_steps": T},
                 "forward_ms": f_ms, "adjoint_ms": a_ms, "adjoint_forward_ratio": a_ms / f_ms,
+                "adjoint_u0_only_ms": statistics.median(adj_u0),
+                "adjoint_u0_only_forward_ratio": statistics.median(adj_u0) / f_ms,
+                "note": "adjoint_ms = checkpointed forward pass + backward sweep (restore, recompute, transposed steps) "
+                        "for dJ/du0 and dJ/dalpha; the u0-only sweep needs no recompute",
                 "grad_alpha": ga}
         print(json.dumps(line), flush=True)
 

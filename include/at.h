@@ -180,7 +180,9 @@ int at_destroy(at_handle_t *hd);
  *   step 0), AT_ERR_CUDA.
  * at_adjoint_backward: given lambda_dev = dJ/dU^nsteps (device, ntot doubles), write dJ/dU^0 to grad_u0_dev
  *   (device, ntot doubles) and dJ/dalpha to *grad_alpha_host.  Replays one checkpoint segment at a time:
- *   restores it, recomputes its levels with the forward kernel, runs its adjoint steps in reverse.  Blocks.
+ *   restores it, recomputes its levels with the forward kernel, runs its adjoint steps in reverse.  With
+ *   grad_alpha_host NULL only dJ/dU^0 is formed; the transposed steps need no forward level then, so the sweep
+ *   skips the restore and the recompute.  Blocks.
  *   Requires at_adjoint_forward to have been the last stepping call.  Errors: AT_ERR_ARG, AT_ERR_STATE,
  *   AT_ERR_CUDA, AT_ERR_NONFINITE. */
 int at_adjoint_workspace(at_handle_t *hd, int64_t nsteps, int64_t ckpt_every, int64_t *work_len);

@@ -27,11 +27,13 @@ class ATForward(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_out: torch.Tensor):
         solver = ctx.solver
-        g0, ga = solver.adjoint_backward(grad_out.detach())
+        want_alpha = ctx.needs_input_grad[1]
+        g0, ga = solver.adjoint_backward(grad_out.detach(), want_alpha)
         solver.close()
         ctx.solver = None
         dtype, device, shape = ctx.alpha_meta
-        return g0.view_as(grad_out), torch.full(shape, ga, dtype=dtype, device=device), None, None, None
+        galpha = torch.full(shape, ga, dtype=dtype, device=device) if want_alpha else None
+        return g0.view_as(grad_out), galpha, None, None, None
 
 
 def at_forward(u0: torch.Tensor, alpha: torch.Tensor, spec: dict, nsteps: int, ckpt_every: int = 0) -> torch.Tensor:

@@ -300,9 +300,10 @@ def at_adjoint_forward(h, nsteps: int, ckpt_every: int, work) -> None:
            "at_adjoint_forward")
 
 
-def at_adjoint_backward(h, lam, grad_u0) -> float:
-    """lam = dJ/dU^nsteps, grad_u0 receives dJ/dU^0 (CUDA float64 tensors); returns dJ/dalpha."""
+def at_adjoint_backward(h, lam, grad_u0, want_alpha: bool = True):
+    """lam = dJ/dU^nsteps, grad_u0 receives dJ/dU^0 (CUDA float64 tensors); returns dJ/dalpha (None when not
+    requested: the sweep then skips the recompute of the forward levels)."""
     ga = C.c_double()
-    _check(load().at_adjoint_backward(h, C.c_void_p(lam.data_ptr()), C.c_void_p(grad_u0.data_ptr()), C.byref(ga)),
-           "at_adjoint_backward")
-    return ga.value
+    _check(load().at_adjoint_backward(h, C.c_void_p(lam.data_ptr()), C.c_void_p(grad_u0.data_ptr()),
+                                      C.byref(ga) if want_alpha else None), "at_adjoint_backward")
+    return ga.value if want_alpha else None

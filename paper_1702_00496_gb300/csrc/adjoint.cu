@@ -42,6 +42,7 @@ struct AdjParams {
   const int32_t *list; // group indices of this launch (interior groups for MODE 1, edge groups for MODE 2)
   int64_t list_len;
   int64_t edge_len;    // on the host: the edge groups come first in the list
+  int32_t alpha;       // accumulate dJ/dalpha (needs the forward levels); 0: lambda only
 };
 
 // Block sum of v into g_blk[blockIdx.x] (warp shuffles, then warp 0 in warp order).
@@ -78,7 +79,7 @@ __device__ void adjoint_cell(const AdjParams &a, const uint8_t *__restrict__ kef
   for (int l = 0; l < AT_MAX_LAG; ++l) acc[l] = 0.0;
   const double lc = ln[ci];
   acc[0] = fma(f.s0, lc, f.zero);
-  double d2 = fma(f.q0, __ldg(un + ci), f.zero);
+  double d2 = a.alpha ? fma(f.q0, __ldg(un + ci), f.zero) : 0.0;
 #pragma unroll
   for (int ax = 0; ax < DIM; ++ax) {
     const bool edge = f.use_pe[ax] && (pos[ax] < H || pos[ax] >= f.S[ax] - H);
@@ -103,6 +104,7 @@ __device__ void adjoint_cell(const AdjParams &a, const uint8_t *__restrict__ kef
       } else {
         for (int m = 0; m < f.T; ++m) acc[k + m] = fma(s * f.w[k][m], li, acc[k + m]);
       }
+      if (!a.alpha) continue;
       // alpha term: c's own tap j, with c's own side delays
       const int cj = wrap_coord(c[ax] + j, f.n[ax]);
       const int64_t cell = ci + (int64_t)(cj - c[ax]) * stride[ax];
@@ -137,8 +139,8 @@ __device__ __forceinline__ void adjoint_group(const AdjParams &a, const uint8_t 
   const int64_t row = DIM == 3 ? ((int64_t)z * f.n[1] + y) * nx : 0;
   const int64_t i0 = row + x0;
   const double *ln = a.lam + ((n + 1) % a.Rl) * N;
-  double d[4];
-  group_eval<DIM, H, LdgNC, true>(f, keff, f.ring + (n % f.R) * N, n, x0, y, z, d);
+  double d[4] = {0.0, 0.0, 0.0, 0.0};
+  if (a.alpha) group_eval<DIM, H, LdgNC, true>(f, keff, f.ring + (n % f.R) * N, n, x0, y, z, d);
   int pidx[3] = {x0 / f.S[0], 0, 0}, pos[3] = {0, 0, 0};
   pos[0] = x0 - pidx[0] * f.S[0];
   if (DIM == 3) {
@@ -259,7 +261,7 @@ template <int MODE>
 struct AdjBounds {
   static constexpr int min_blocks = MODE == 1 ? AT_ADJ_MIN_BLOCKS : 2;
 };
-template <int DIM, int H, int MODE>
+template <int DIM, int H, int MODE, bool AL>
 __global__ void __launch_bounds__(256, AdjBounds<MODE>::min_blocks) adjoint_step_kernel(const AdjParams a,
                                                                                       const int64_t n) {
   constexpr bool G = MODE != 0;
@@ -300,19 +302,21 @@ __global__ void __launch_bounds__(256, AdjBounds<MODE>::min_blocks) adjoint_step
         const double2 l0 = LdgNC::ld2(ln + i0 - 2), l1 = LdgNC::ld2(ln + i0), l2 = LdgNC::ld2(ln + i0 + 2),
                       l3 = LdgNC::ld2(ln + i0 + 4);
         lv[0] = l0.x; lv[1] = l0.y; lv[2] = l1.x; lv[3] = l1.y; lv[4] = l2.x; lv[5] = l2.y; lv[6] = l3.x; lv[7] = l3.y;
-        const double2 u0 = LdgNC::ld2(un + i0 - 2), u1 = LdgNC::ld2(un + i0), u2 = LdgNC::ld2(un + i0 + 2),
-                      u3 = LdgNC::ld2(un + i0 + 4);
-        uv[0] = u0.x; uv[1] = u0.y; uv[2] = u1.x; uv[3] = u1.y; uv[4] = u2.x; uv[5] = u2.y; uv[6] = u3.x; uv[7] = u3.y;
+        if (AL) {
+          const double2 u0 = LdgNC::ld2(un + i0 - 2), u1 = LdgNC::ld2(un + i0), u2 = LdgNC::ld2(un + i0 + 2),
+                        u3 = LdgNC::ld2(un + i0 + 4);
+          uv[0] = u0.x; uv[1] = u0.y; uv[2] = u1.x; uv[3] = u1.y; uv[4] = u2.x; uv[5] = u2.y; uv[6] = u3.x; uv[7] = u3.y;
+        }
       }
       double A[4], D[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        double acc = fma(f.s0, lv[q + 2], f.zero), d = fma(f.q0, uv[q + 2], f.zero);
+        double acc = fma(f.s0, lv[q + 2], f.zero), d = AL ? fma(f.q0, uv[q + 2], f.zero) : 0.0;
 #pragma unroll
         for (int j = -H; j <= H; ++j) {
           if (j == 0) continue;
           acc = fma(f.s[0][j + H], lv[q + 2 - j], acc);
-          d = fma(f.q[0][j + H], uv[q + 2 + j], d);
+          if (AL) d = fma(f.q[0][j + H], uv[q + 2 + j], d);
         }
         A[q] = acc;
         D[q] = d;
@@ -325,15 +329,16 @@ __global__ void __launch_bounds__(256, AdjBounds<MODE>::min_blocks) adjoint_step
           for (int j = -H; j <= H; ++j) {
             if (j == 0) continue;
             const double2 la = LdgNC::ld2(ln + i0 - j * st), lb = LdgNC::ld2(ln + i0 - j * st + 2);
-            const double2 ua = LdgNC::ld2(un + i0 + j * st), ub = LdgNC::ld2(un + i0 + j * st + 2);
+            double2 ua = make_double2(0.0, 0.0), ub = ua;
+            if (AL) { ua = LdgNC::ld2(un + i0 + j * st); ub = LdgNC::ld2(un + i0 + j * st + 2); }
             const double s = f.s[ax][j + H], qq = f.q[ax][j + H];
             A[0] = fma(s, la.x, A[0]); A[1] = fma(s, la.y, A[1]); A[2] = fma(s, lb.x, A[2]); A[3] = fma(s, lb.y, A[3]);
-            D[0] = fma(qq, ua.x, D[0]); D[1] = fma(qq, ua.y, D[1]); D[2] = fma(qq, ub.x, D[2]); D[3] = fma(qq, ub.y, D[3]);
+            if (AL) { D[0] = fma(qq, ua.x, D[0]); D[1] = fma(qq, ua.y, D[1]); D[2] = fma(qq, ub.x, D[2]); D[3] = fma(qq, ub.y, D[3]); }
           }
         }
       }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) galpha = fma(lv[q + 2], D[q], galpha);
+      for (int q = 0; q < 4; ++q) if (AL) galpha = fma(lv[q + 2], D[q], galpha);
       double2 *cur = reinterpret_cast<double2 *>(a.lam + (n % a.Rl) * N + i0);
       if (a.Rl == 2) {
         cur[0] = make_double2(A[0], A[1]);
@@ -351,7 +356,7 @@ __global__ void __launch_bounds__(256, AdjBounds<MODE>::min_blocks) adjoint_step
       }
     }
   }
-  block_accumulate(galpha, a.g_blk);
+  if (AL) block_accumulate(galpha, a.g_blk);
 }
 
 __global__ void sum_blocks_kernel(const double *g_blk, int nblk, double *out) {
@@ -377,7 +382,7 @@ int adj_blocks() {
   return sms * 8;
 }
 
-template <int DIM, int H>
+template <int DIM, int H, bool AL>
 void launch_modes(const AdjParams &a, int64_t n, int nblk, bool grouped, cudaStream_t st) {
   if (grouped) {
     AdjParams e = a, i = a;
@@ -385,11 +390,17 @@ void launch_modes(const AdjParams &a, int64_t n, int nblk, bool grouped, cudaStr
     e.list_len = a.edge_len;
     i.list = a.list + a.edge_len;
     i.list_len = a.list_len - a.edge_len;
-    adjoint_step_kernel<DIM, H, 2><<<nblk, kAdjThreads, 0, st>>>(e, n);
-    adjoint_step_kernel<DIM, H, 1><<<nblk, kAdjThreads, 0, st>>>(i, n);
+    adjoint_step_kernel<DIM, H, 2, AL><<<nblk, kAdjThreads, 0, st>>>(e, n);
+    adjoint_step_kernel<DIM, H, 1, AL><<<nblk, kAdjThreads, 0, st>>>(i, n);
   } else {
-    adjoint_step_kernel<DIM, H, 0><<<nblk, kAdjThreads, 0, st>>>(a, n);
+    adjoint_step_kernel<DIM, H, 0, AL><<<nblk, kAdjThreads, 0, st>>>(a, n);
   }
+}
+
+template <int DIM, int H>
+void launch_alpha(const AdjParams &a, int64_t n, int nblk, bool grouped, cudaStream_t st) {
+  if (a.alpha) launch_modes<DIM, H, true>(a, n, nblk, grouped, st);
+  else launch_modes<DIM, H, false>(a, n, nblk, grouped, st);
 }
 
 bool adjoint_grouped(const AdjParams &a) {
@@ -417,11 +428,11 @@ bool group_interior(const StepParams &f, int64_t g) {
 cudaError_t launch_adjoint_step(const AdjParams &a, int64_t n, int nblk, cudaStream_t st) {
   const bool grouped = adjoint_grouped(a);
   if (a.f.dim == 1) {
-    if (a.f.h == 1) launch_modes<1, 1>(a, n, nblk, grouped, st);
-    else launch_modes<1, 2>(a, n, nblk, grouped, st);
+    if (a.f.h == 1) launch_alpha<1, 1>(a, n, nblk, grouped, st);
+    else launch_alpha<1, 2>(a, n, nblk, grouped, st);
   } else {
-    if (a.f.h == 1) launch_modes<3, 1>(a, n, nblk, grouped, st);
-    else launch_modes<3, 2>(a, n, nblk, grouped, st);
+    if (a.f.h == 1) launch_alpha<3, 1>(a, n, nblk, grouped, st);
+    else launch_alpha<3, 2>(a, n, nblk, grouped, st);
   }
   return cudaGetLastError();
 }
@@ -513,7 +524,8 @@ extern "C" int at_adjoint_forward(at_handle_t *hd, int64_t nsteps, int64_t ckpt_
 
 extern "C" int at_adjoint_backward(at_handle_t *hd, const double *lambda_dev, double *grad_u0_dev,
                                    double *grad_alpha_host) {
-  if (!hd || !lambda_dev || !grad_u0_dev || !grad_alpha_host) return fail(AT_ERR_ARG, "at_adjoint_backward: bad argument");
+  if (!hd || !lambda_dev || !grad_u0_dev) return fail(AT_ERR_ARG, "at_adjoint_backward: bad argument");
+  const bool want_alpha = grad_alpha_host != nullptr;
   if (hd->adj_nsteps < 0 || hd->step != hd->adj_nsteps)
     return fail(AT_ERR_STATE, "at_adjoint_backward: needs the at_adjoint_forward pass right before");
   const int64_t Ns = hd->adj_nsteps, N = hd->sp.ntot, R = hd->sp.R;
@@ -535,6 +547,7 @@ extern "C" int at_adjoint_backward(at_handle_t *hd, const double *lambda_dev, do
   a.Rl = (int32_t)R;
   a.akeff = reinterpret_cast<uint8_t *>(w + L.keff) + 2 * hd->sp.nb;
   a.g_blk = w + L.gblk;
+  a.alpha = want_alpha ? 1 : 0;
   a.list = reinterpret_cast<int32_t *>(w + L.list);
   a.list_len = 0;
   a.edge_len = 0;
@@ -564,22 +577,23 @@ extern "C" int at_adjoint_backward(at_handle_t *hd, const double *lambda_dev, do
   }
   for (int64_t c = L.nck - 1; c >= 0 && e == cudaSuccess; --c) {
     const int64_t n0 = c * L.s, n1 = (n0 + L.s < Ns) ? n0 + L.s : Ns;
-    for (int64_t lev = n0 - R + 2; lev <= n0 && e == cudaSuccess; ++lev) {
+    for (int64_t lev = n0 - R + 2; want_alpha && lev <= n0 && e == cudaSuccess; ++lev) {
       if (lev < 0) continue;
       e = copy_field(seg.ring + (lev % seg.R) * N, w + L.ck + (c * (R - 1) + (lev - (n0 - R + 2))) * N, N, st);
     }
-    if (e == cudaSuccess) e = launch_draw_delays(seg, n0, st);
-    for (int64_t n = n0; n + 1 < n1 && e == cudaSuccess; ++n) e = launch_forward_step(seg, n, nullptr, st);
+    // the forward levels only serve the alpha term: without it the sweep needs no recompute
+    if (want_alpha && e == cudaSuccess) e = launch_draw_delays(seg, n0, st);
+    for (int64_t n = n0; want_alpha && n + 1 < n1 && e == cudaSuccess; ++n) e = launch_forward_step(seg, n, nullptr, st);
     for (int64_t n = n1 - 1; n >= n0 && e == cudaSuccess; --n) e = launch_adjoint_step(a, n, nblk, st);
   }
   if (e == cudaSuccess) e = copy_field(grad_u0_dev, a.lam, N, st);  // level 0 lives in slot 0
-  if (e == cudaSuccess) {
+  if (want_alpha && e == cudaSuccess) {
     sum_blocks_kernel<<<1, 256, 0, st>>>(a.g_blk, nblk, a.g_blk + nblk);
     e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(grad_alpha_host, a.g_blk + nblk, sizeof(double), cudaMemcpyDeviceToHost, st);
   }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(grad_alpha_host, a.g_blk + nblk, sizeof(double), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "at_adjoint_backward");
-  if (!std::isfinite(*grad_alpha_host)) return fail(AT_ERR_NONFINITE, "at_adjoint_backward: non-finite gradient");
+  if (want_alpha && !std::isfinite(*grad_alpha_host)) return fail(AT_ERR_NONFINITE, "at_adjoint_backward: non-finite gradient");
   return AT_OK;
 }

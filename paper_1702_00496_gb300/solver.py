@@ -66,11 +66,11 @@ class Solver:
             self.work = torch.empty(n, dtype=torch.float64, device=self.device)
         B.at_adjoint_forward(self.h, nsteps, ckpt_every, self.work)
 
-    def adjoint_backward(self, lam: torch.Tensor):
-        """dJ/dU^0 (shaped like the field) and dJ/dalpha for lam = dJ/dU^nsteps."""
+    def adjoint_backward(self, lam: torch.Tensor, want_alpha: bool = True):
+        """dJ/dU^0 (shaped like the field) and dJ/dalpha (None if not wanted) for lam = dJ/dU^nsteps."""
         lam = lam.reshape(-1).to(device=self.device, dtype=torch.float64).contiguous()
         g = torch.empty(self.cfg.ntot, dtype=torch.float64, device=self.device)
-        ga = B.at_adjoint_backward(self.h, lam, g)
+        ga = B.at_adjoint_backward(self.h, lam, g, want_alpha)
         return g.view(self.cfg.shape), ga
 
     def close(self) -> None:

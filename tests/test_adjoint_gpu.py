@@ -126,3 +126,17 @@ def test_full_size_adjoint_against_finite_differences():
     d1 = (J(u0, a0 + h) - J(u0, a0 - h)) / (2 * h)
     d2 = (J(u0, a0 + h / 2) - J(u0, a0 - h / 2)) / h
     assert ga == pytest.approx((4 * d2 - d1) / 3, rel=1e-6)
+
+
+def test_u0_only_sweep_gives_the_same_u0_gradient():
+    from paper_1702_00496_gb300 import Solver
+    spec, _ = W.wl_3d([16, 12, 8], [2, 2, 2], 4, 3, 0, 74, c=(0.3, 0.2, 0.1))
+    grads = []
+    for want_alpha in (True, False):
+        s = Solver(spec)
+        s.adjoint_forward(30, 7)
+        g, ga = s.adjoint_backward(s.field().clone(), want_alpha)
+        grads.append(g.clone())
+        assert (ga is None) == (not want_alpha)
+        s.close()
+    assert torch.equal(grads[0], grads[1])
