@@ -394,11 +394,11 @@ def main():
     peaks = measured_peaks()
     flops_launch = flops_per_update(spec) * ntot
     achieved = flops_launch / (kern_ms / 1e3)
-    bytes_launch = 16 * ntot  # read U^n, write U^{n+1}; halo reads of old levels add < 0.2 % at S = 4096
+    bytes_launch = 16 * ntot  # read U^n, write U^{n+1} (halo reads of delayed levels not counted)
     hbm = peaks.get("hbm_gbs")
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": PEAK_FP64_FLOPS / 1e12, "unit": "TFLOP/s",
                 "frac": achieved / PEAK_FP64_FLOPS, "traffic": None,
-                "kernel": "forward_step_kernel<1,2>", "launch_ms": kern_ms,
+                "kernel": f"forward_group_kernel<{spec['dim']},{spec['order'] // 2}>", "launch_ms": kern_ms,
                 "peak_source": "152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
                 "hbm_gbs": bytes_launch / (kern_ms / 1e3) / 1e9,
                 "hbm_frac_of_measured": (bytes_launch / (kern_ms / 1e3) / 1e9 / hbm) if hbm else None}
@@ -415,7 +415,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": args.workload, "points": ntot, "pes": spec["pe"][0], "order": spec["order"],
+                "config": {"workload": args.workload, "points": ntot, "pes": spec["pe"], "order": spec["order"],
                            "L": spec["L"], "time_steps_per_step": T, "l2": "flushed (512 MiB write) each step",
                            "replicas": world, "launch": {"threads": launch[0], "blocks_per_sm": launch[1]}},
                 "e2e": {"value": e2e_value, "unit": "updates/s", "h2d_bytes_per_step": 8 * ntot,

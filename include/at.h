@@ -192,7 +192,7 @@ int at_adjoint_backward(at_handle_t *hd, const double *lambda_dev, double *grad_
 /* ------------------------------------------------------------------ batched ensemble */
 /* The error of an AT scheme is a statistical quantity (Sec. 4: ensemble average over delay realizations,
  * Eq. "aveE_split"; Sec. 5.1: averages over runs with random phases).  An ensemble runs `count` independent
- * 1D problems -- each with its own n[0] (a multiple of 4), PEs, L, seed, initial condition and dt -- for
+ * 1D problems -- each with its own n[0] and PE width (multiples of 4), L, seed, initial condition and dt -- for
  * `nsteps` steps each, inside one persistent kernel captured in a CUDA graph: CTAs take realizations from a
  * work counter in longest-first order, so uneven grid sizes balance over the SMs.
  *

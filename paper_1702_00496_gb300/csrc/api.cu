@@ -169,14 +169,46 @@ extern "C" int at_init(const at_config_t *cfg, double *ring_dev, int64_t ring_le
 
   const size_t n_tables = (size_t)(cfg->n[0] + cfg->n[1] + cfg->n[2]);
   const size_t keff_bytes = (size_t)(2 * p.nb + 255) / 256 * 256;
-  const size_t bytes = 512 + keff_bytes + sizeof(double) * ((size_t)AT_STAT_BLOCKS * AT_STAT_FIELDS + 16 + n_tables);
+  // 3D grouped shapes: visit interior groups first, then edge groups, so a warp's lanes share one path
+  std::vector<int32_t> order;
+  if (cfg->dim == 3 && cfg->n[0] % 4 == 0 && (p.use_pe[0] == 0 || p.S[0] % 4 == 0)) {
+    const int64_t gx = cfg->n[0] / 4, groups = ntot / 4;
+    const int h = cfg->order / 2;
+    auto interior = [&](int64_t g) {  // every cell and stencil neighbour inside the group's PE and the domain
+      const int64_t r = g / gx;
+      const int x0 = (int)(g - r * gx) * 4, z = (int)(r / cfg->n[1]), y = (int)(r - (int64_t)z * cfg->n[1]);
+      const int c[3] = {x0, y, z}, span[3] = {3, 0, 0};
+      for (int a = 0; a < 3; ++a) {
+        if (c[a] - h < 0 || c[a] + span[a] + h >= cfg->n[a]) return false;
+        const int pos = c[a] % p.S[a];
+        if (p.use_pe[a] && (pos < h || pos + span[a] >= p.S[a] - h)) return false;
+      }
+      return true;
+    };
+    order.reserve((size_t)groups);
+    for (int64_t g = 0; g < groups; ++g)
+      if (interior(g)) order.push_back((int32_t)g);
+    for (int64_t g = 0; g < groups; ++g)
+      if (!interior(g)) order.push_back((int32_t)g);
+  }
+  const size_t order_bytes = (order.size() * sizeof(int32_t) + 255) / 256 * 256;
+  const size_t bytes = 512 + keff_bytes + order_bytes +
+                       sizeof(double) * ((size_t)AT_STAT_BLOCKS * AT_STAT_FIELDS + 16 + n_tables);
   cudaError_t e = cudaMalloc(&hd->scratch, bytes);
   if (e != cudaSuccess) { delete hd; return cuda_fail(e, "at_init: cudaMalloc"); }
   char *base = (char *)hd->scratch;
   hd->d_status = (int32_t *)base;
   hd->d_step = (int64_t *)(base + 256);
   p.keff = (uint8_t *)(base + 512);
-  hd->d_partials = (double *)(base + 512 + keff_bytes);
+  p.order = order.empty() ? nullptr : (const int32_t *)(base + 512 + keff_bytes);
+  hd->d_partials = (double *)(base + 512 + keff_bytes + order_bytes);
+  if (!order.empty() &&
+      (e = cudaMemcpy((void *)p.order, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice)) !=
+          cudaSuccess) {
+    cudaFree(hd->scratch);
+    delete hd;
+    return cuda_fail(e, "at_init: group order");
+  }
   hd->d_result = hd->d_partials + (size_t)AT_STAT_BLOCKS * AT_STAT_FIELDS;
   hd->d_tables = hd->d_result + 16;
   p.status = hd->d_status;

@@ -58,8 +58,8 @@ __device__ void run_member(const StepParams &p, uint8_t *keff_sh, int64_t nsteps
     double *out = p.ring + ((n + 1) % p.R) * p.ntot;
     if (n + 1 < nsteps) atfd::draw_sides(p, n + 1, threadIdx.x, blockDim.x, keff_sh + ((n + 1) & 1) * p.nb);
     const uint8_t *keff = keff_sh + (n & 1) * p.nb;
-    for (int g = threadIdx.x; g < groups; g += blockDim.x)
-      atfd::group_update<1, H, atfd::LdCoherent>(p, keff, un, out, n, g << 2, 0, 0);
+    for (int k = threadIdx.x; k < groups; k += blockDim.x)
+      atfd::group_update<1, H, atfd::LdCoherent>(p, keff, un, out, n, (int)(atfd::group_1d_order(p, k) << 2), 0, 0);
     __syncthreads();
   }
 }
@@ -205,7 +205,8 @@ extern "C" int at_ensemble_sizes(const at_config_t *members, int32_t count, int6
     int rc = at_ring_slots(members + r, &R);
     if (rc) return rc;
     if ((rc = at_num_sides(members + r, &nb))) return rc;
-    if (members[r].dim != 1 || members[r].n[0] % 4) return fail(AT_ERR_ARG, "ensemble members must be 1D with N % 4 == 0");
+    if (members[r].dim != 1 || members[r].n[0] % 4 || (members[r].pe[0] > 1 && (members[r].n[0] / members[r].pe[0]) % 4))
+      return fail(AT_ERR_ARG, "ensemble members must be 1D with N and the PE width multiples of 4");
     ring += (int64_t)R * members[r].n[0];
     log += nsteps * nb;
   }

@@ -39,10 +39,12 @@ __global__ void __launch_bounds__(512) forward_group_kernel(const StepParams p, 
   draw_sides(p, n + 1, tid, nthreads, p.keff + ((n + 1) & 1) * p.nb);
   const int gx = p.n[0] >> 2;
   const int64_t groups = (int64_t)gx * p.n[1] * p.n[2];
-  for (int64_t g = tid; g < groups; g += nthreads) {
+  for (int64_t k = tid; k < groups; k += nthreads) {
     if (DIM == 1) {
+      const int64_t g = group_1d_order(p, k);
       group_update<1, H, LdgNC>(p, keff, un, out, n, (int)(g << 2), 0, 0);
     } else {
+      const int64_t g = p.order ? (int64_t)p.order[k] : k;
       const int64_t r = g / gx;
       const int x0 = (int)(g - r * gx) << 2;
       const int z = (int)(r / p.n[1]), y = (int)(r - (int64_t)z * p.n[1]);

@@ -22,6 +22,7 @@ struct StepParams {
   uint8_t *log;           // raw delays, step-major [log_steps][nb], or nullptr
   uint8_t *keff;          // effective delays, two buffers of nb: step n uses keff + (n & 1) * nb
   int64_t log_steps;      // rows of the log
+  const int32_t *order;   // 3D: group visiting order (interior groups first, then edge groups), or nullptr
   int32_t *status;        // sticky device status word
   int64_t ntot;           // points
   int64_t nb;             // PE sides, 2 * dim * prod(pe)

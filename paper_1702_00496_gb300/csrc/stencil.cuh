@@ -63,6 +63,22 @@ __device__ __forceinline__ double halo_value(const StepParams &p, int64_t cell, 
   return acc;
 }
 
+// Order of the 1D groups that keeps the lanes of a warp on one path: the interior groups of every PE (local
+// index 1 .. gS-2 of the gS = S/4 groups of a PE) first, then the two edge groups of every PE.  Any order is
+// correct; this one avoids warps in which a few lanes take the halo path.  k < number of groups.
+__device__ __forceinline__ int64_t group_1d_order(const StepParams &p, int64_t k) {
+  const uint32_t gS = (uint32_t)(p.use_pe[0] ? p.S[0] >> 2 : p.n[0] >> 2);
+  if (gS < 3) return k;
+  const uint32_t inner = gS - 2, npe = (uint32_t)(p.n[0] >> 2) / gS, uk = (uint32_t)k;
+  const uint32_t n_int = npe * inner;
+  if (uk < n_int) {
+    const uint32_t pe = uk / inner;
+    return (int64_t)pe * gS + 1 + (uk - pe * inner);
+  }
+  const uint32_t kk = uk - n_int;
+  return (int64_t)(kk >> 1) * gS + ((kk & 1) ? gS - 1 : 0);
+}
+
 // Side index of face (axis a, lo/hi) of the PE with index (px, py, pz).
 template <int DIM>
 __device__ __forceinline__ int64_t side_of(const StepParams &p, const int pidx[3], int a, int hi) {
