@@ -161,6 +161,20 @@ typedef struct {
 } at_stats_t;
 int at_error_stats(at_handle_t *hd, at_stats_t *out);
 
+/* The statistics of at_error_stats for a field the caller holds (u_dev: device, n0*n1*n2 doubles of the problem
+ * cfg at step `step`, t = step * dt), computed without allocating anything.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory -- a process under a memory pool that refuses
+ * new allocations after start-up, an embedding that gives the library only buffers it owns, or a job close to
+ * its memory limit -- and so cannot create a handle (at_init allocates scratch).
+ * Scratch: one static device array of this library (33,808 doubles, about 270 KB), held by every GPU that loads
+ * the library until the process exits.  3D problems need n[0] + n[1] + n[2] <= 24576; larger ones are rejected
+ * with AT_ERR_ARG.  Each call overwrites the scratch it reads, so nothing must be cleared between calls, but every
+ * call shares the one array: calls that overlap on the GPU (different streams or host threads) race.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress) with that device current; make
+ * that first call before any stream capture.  No cudaMalloc, cudaFree or other allocating call is made.  Blocks
+ * on `stream` (a cudaStream_t, NULL = default stream).  Errors: AT_ERR_ARG, AT_ERR_CUDA, AT_ERR_NONFINITE. */
+int at_error_stats_noalloc(const at_config_t *cfg, const double *u_dev, int64_t step, void *stream, at_stats_t *out);
+
 /* Release the handle's scratch.  The caller's ring and log are untouched. */
 int at_destroy(at_handle_t *hd);
 

@@ -22,6 +22,7 @@ AT_SYNC, AT_ASYNC_STD, AT_AT = 0, 1, 2
 EXPORTS = (
     "at_coeffs", "at_stencil_taps", "at_solve_stencil", "at_delay", "at_ring_slots", "at_num_sides",
     "at_init", "at_step", "at_reset", "at_set_launch", "at_sync", "at_state", "at_error_stats", "at_destroy", "at_last_error",
+    "at_error_stats_noalloc",
     "at_adjoint_workspace", "at_adjoint_forward", "at_adjoint_backward",
     "at_ensemble_sizes", "at_ensemble_create", "at_ensemble_run", "at_ensemble_stats", "at_ensemble_destroy",
 )
@@ -91,6 +92,7 @@ def load(build_if_missing: bool = True):
     L.at_error_stats.argtypes = [vp, C.POINTER(at_stats_t)]
     L.at_destroy.argtypes = [vp]
     L.at_last_error.restype = C.c_char_p
+    L.at_error_stats_noalloc.argtypes = [C.POINTER(at_config_t), vp, i64, vp, C.POINTER(at_stats_t)]
     L.at_adjoint_workspace.argtypes = [vp, i64, i64, C.POINTER(i64)]
     L.at_adjoint_forward.argtypes = [vp, i64, i64, vp, i64]
     L.at_adjoint_backward.argtypes = [vp, vp, vp, C.POINTER(C.c_double)]
@@ -307,3 +309,12 @@ def at_adjoint_backward(h, lam, grad_u0, want_alpha: bool = True):
     _check(load().at_adjoint_backward(h, C.c_void_p(lam.data_ptr()), C.c_void_p(grad_u0.data_ptr()),
                                       C.byref(ga) if want_alpha else None), "at_adjoint_backward")
     return ga.value if want_alpha else None
+
+
+def at_error_stats_noalloc(cfg: Config, u, step: int, stream=None) -> dict:
+    """Statistics of a device field u (CUDA float64 tensor of the problem cfg at `step`) without any allocation
+    inside the library (static device scratch)."""
+    st = at_stats_t()
+    _check(load().at_error_stats_noalloc(C.byref(cfg.s), C.c_void_p(u.data_ptr()), int(step), _stream_ptr(stream),
+                                         C.byref(st)), "at_error_stats_noalloc")
+    return st.as_dict()
