@@ -80,6 +80,8 @@ def workload(name: str, scheme: int = AT):
         return wl_3d(512, 8, 2, 3, 500, 3, scheme)
     if name == "3d_512_o4":
         return wl_3d(512, 8, 4, 3, 500, 3, scheme)
+    if name == "3d_256_o4":
+        return wl_3d(256, 4, 4, 3, 500, 3, scheme)
     if name == "adjoint_256":
         return adjoint_spec(256, 4, 2000)
     raise KeyError(name)
