@@ -31,6 +31,9 @@ import workloads as W  # noqa: E402
 
 METRIC = "grid-point updates/s (FP64)"
 PEAK_FP64_FLOPS = 152 * 2 * 2 * 2.07e9  # 152 SMs x 2 FP64 FMA lanes/clk x 2 flop x 2.07 GHz max clock
+# DRAM bytes (read + write) per launch of the step kernel from one ncu capture of the current kernel source
+# (profiles/forward_group_kernel_1d_n16m.md); None where no capture of the current source exists.
+MEASURED_TRAFFIC = {("1d_n16m", "forward_group_kernel<1,2>"): 134.798080e6 + 83.307264e6}
 
 
 def measured_peaks():
@@ -396,9 +399,12 @@ def main():
     achieved = flops_launch / (kern_ms / 1e3)
     bytes_launch = 16 * ntot  # read U^n, write U^{n+1} (halo reads of delayed levels not counted)
     hbm = peaks.get("hbm_gbs")
+    kname = f"forward_group_kernel<{spec['dim']},{spec['order'] // 2}>"
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": PEAK_FP64_FLOPS / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / PEAK_FP64_FLOPS, "traffic": None,
-                "kernel": f"forward_group_kernel<{spec['dim']},{spec['order'] // 2}>", "launch_ms": kern_ms,
+                "frac": achieved / PEAK_FP64_FLOPS, "traffic": MEASURED_TRAFFIC.get((args.workload, kname)),
+                "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
+                "algorithmic_bytes_per_launch": bytes_launch,
+                "kernel": kname, "launch_ms": kern_ms,
                 "peak_source": "152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
                 "hbm_gbs": bytes_launch / (kern_ms / 1e3) / 1e9,
                 "hbm_frac_of_measured": (bytes_launch / (kern_ms / 1e3) / 1e9 / hbm) if hbm else None}
