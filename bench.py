@@ -102,6 +102,27 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+def replica_seed(seed: int, rank: int, stride: int = 1) -> int:
+    """Seed of this rank's independent replica (ranks share no data; each runs its own delay realization)."""
+    return int(seed) + stride * int(rank)
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The job's time is the slowest rank's: all-reduce MAX (NCCL on GPUs, gloo on CPU in the tests)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time (weak scaling)."""
+    return world * units_per_rank / seconds
+
+
 def flops_per_update(spec) -> int:
     """FP64 flops of the merged stencil per interior point: 1 multiply + 2*h*dim FMAs (2 flops each)."""
     h = spec["order"] // 2
@@ -157,7 +178,7 @@ def run_ensemble(args, rank: int, world: int, local: int):
     if args.time_steps is not None:
         T = args.time_steps
     for s in specs:
-        s["seed"] = int(s["seed"]) + 100000 * rank
+        s["seed"] = replica_seed(s["seed"], rank, 100000)
     updates = sum(s["n"][0] for s in specs) * T
     stream = torch.cuda.current_stream()
     threads, ctas = args.threads, args.ctas_per_sm
@@ -181,10 +202,7 @@ def run_ensemble(args, rank: int, world: int, local: int):
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1) / args.steps
     per, groups = ens.stats()
-    if world > 1:
-        tt = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{local}")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, world, f"cuda:{local}")
     # the same realizations one problem at a time: reset, T steps, statistics, in sequence
     one = None
     if not args.skip_one_at_a_time:
@@ -224,7 +242,7 @@ def run_adjoint(args, rank: int, world: int, local: int):
     spec, T = W.workload("adjoint_256")
     if args.time_steps is not None:
         T = args.time_steps
-    spec["seed"] = int(spec["seed"]) + rank
+    spec["seed"] = replica_seed(spec["seed"], rank)
     ntot = spec["n"][0] * spec["n"][1] * spec["n"][2]
     stream = torch.cuda.current_stream()
     s = Solver(spec, device=f"cuda:{local}", stream=stream)
@@ -310,7 +328,7 @@ def main():
     spec, T = W.workload(args.workload)
     if args.time_steps is not None:
         T = args.time_steps
-    spec["seed"] = int(spec["seed"]) + rank  # independent replica per rank
+    spec["seed"] = replica_seed(spec["seed"], rank)  # independent replica per rank
     ntot = 1
     for x in spec["n"]:
         ntot *= x
@@ -356,11 +374,8 @@ def main():
     clocks = sampler.stop()
     ms = t_start.elapsed_time(t_end) / args.steps
     kern_ms = sum(a.elapsed_time(b) for a, b in kern_ev) / (args.steps * T)
-    if world > 1:
-        tt = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{local}")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * ntot * T / (ms / 1e3)
+    ms = max_over_ranks(ms, world, f"cuda:{local}")
+    value = aggregate_rate(ntot * T, world, ms / 1e3)
 
     # end to end through the public API: pinned host field in, final field and statistics out
     solver.reset()
@@ -388,11 +403,8 @@ def main():
         e2e_step()
     barrier()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        tt = torch.tensor([e2e_s], dtype=torch.float64, device=f"cuda:{local}")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e_value = world * ntot * T / e2e_s
+    e2e_s = max_over_ranks(e2e_s, world, f"cuda:{local}")
+    e2e_value = aggregate_rate(ntot * T, world, e2e_s)
 
     peaks = measured_peaks()
     flops_launch = flops_per_update(spec) * ntot

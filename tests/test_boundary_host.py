@@ -164,3 +164,16 @@ def test_descending_thresholds_are_rejected():
     spec["thresholds"] = np.array([3 << 30, 1 << 30], dtype=np.uint64)
     with pytest.raises(B.ATError):
         P.at_num_sides(B.Config(spec))
+
+
+def test_ensemble_members_must_be_1d_with_aligned_sizes():
+    from paper_1702_00496_gb300.binding import at_ensemble_sizes
+    ok, _ = W.wl_1d(1024, 16, 4, 3, 0, 1, (1, 2))
+    bad_dim, _ = W.wl_3d([16, 16, 16], [2, 2, 2], 2, 3, 0, 2)
+    bad_n, _ = W.wl_1d(1022, 2, 4, 3, 0, 3, (1, 2))
+    bad_s, _ = W.wl_1d(1020, 170, 4, 3, 0, 4, (1, 2))  # PE width 6
+    assert at_ensemble_sizes([B.Config(ok)], 10)[0] == (3 + 3) * 1024  # R = L + T
+    for spec in (bad_dim, bad_n, bad_s):
+        with pytest.raises(B.ATError) as e:
+            at_ensemble_sizes([B.Config(ok), B.Config(spec)], 10)
+        assert e.value.code == B.AT_ERR_ARG
