@@ -34,7 +34,7 @@ class OrcCfg(C.Structure):
         ("n", C.c_int64 * 3), ("pe", C.c_int32 * 3), ("nmodes", C.c_int32),
         ("c", C.c_double * 3), ("alpha", C.c_double), ("dt", C.c_double), ("seed", C.c_uint64),
         ("thresholds", C.POINTER(C.c_uint64)), ("amp", C.POINTER(C.c_double)),
-        ("phase", C.POINTER(C.c_double)), ("kappa", C.POINTER(C.c_int32)),
+        ("phase", C.POINTER(C.c_double)), ("kappa", C.POINTER(C.c_int32)), ("tsteps", C.c_int32),
     ]
 
 
@@ -116,6 +116,7 @@ class Config:
         s.amp = self.amp.ctypes.data_as(C.POINTER(C.c_double))
         s.phase = self.phase.ctypes.data_as(C.POINTER(C.c_double))
         s.kappa = self.kappa.ctypes.data_as(C.POINTER(C.c_int32))
+        s.tsteps = int(spec.get("tsteps", 1))
         self.s = s
         self.shape = (int(n[2]), int(n[1]), int(n[0])) if dim == 3 else (int(n[0]),)
         self.ntot = int(n[0] * n[1] * n[2])
@@ -151,7 +152,7 @@ def time_width(order, scheme):
 
 def taps(order, scheme, deriv, pos, S, use_pe, kL, kR, dx):
     """List of (j, l, c) taps of one derivative at one point (see orc_taps)."""
-    buf = (OrcTap * 16)()
+    buf = (OrcTap * 32)()
     nt = lib().orc_taps(int(order), int(scheme), int(deriv), int(pos), int(S), int(use_pe), int(kL), int(kR),
                         float(dx), buf)
     return [(buf[t].j, buf[t].l, buf[t].c) for t in range(nt)]

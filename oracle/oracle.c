@@ -18,7 +18,8 @@
  *     tables "atschemes-left" / "atschemes-right" ((1,2,2)b, (2,2,2)b, (1,4,2), (2,4,2)), written
  *     out as the explicit sum over (point, time level) pairs of Eq. "general_deriv_at2".
  *     ASYNC_STD is the standard scheme read at delayed levels, Eq. "general_deriv_async".
- *   - time integration: forward Euler, the T=1 case of Eq. "time_disc".
+ *   - time integration: forward Euler (one level of Eq. "time_disc"), or Adams-Bashforth with two (Eq.
+ *     "time_ab2") or three levels, started with Euler and then AB2.
  *   - error: E = U - u_a (Sec. 5.1, Eq. "ana_sol", with the travelling phase read as
  *     sin(kappa (x - c t) + phi)); averages over I, I_I and I_B (Sec. 4).
  *   - adjoint: the literal transpose of the forward step over the stored history.
@@ -61,6 +62,7 @@ typedef struct {
   const double *amp;          /* [dim][nmodes] */
   const double *phase;        /* [dim][nmodes] */
   const int32_t *kappa;       /* [dim][nmodes] */
+  int32_t tsteps;             /* time integration: 0 or 1 forward Euler, 2 AB2, 3 AB3 (Eq. "time_disc") */
 } orc_cfg;
 
 typedef struct {
@@ -129,19 +131,27 @@ int orc_delay_effective(int k, int64_t n, int T) {
  *   CD2, d=1: (U_{i+1} - U_{i-1}) / (2 dx)
  *   CD2, d=2: (U_{i+1} - 2 U_i + U_{i-1}) / dx^2
  *   CD4, d=1: (-U_{i+2} + 8 U_{i+1} - 8 U_{i-1} + U_{i-2}) / (12 dx)
- *   CD4, d=2: (-U_{i+2} + 16 U_{i+1} - 30 U_i + 16 U_{i-1} - U_{i-2}) / (12 dx^2)        */
+ *   CD4, d=2: (-U_{i+2} + 16 U_{i+1} - 30 U_i + 16 U_{i-1} - U_{i-2}) / (12 dx^2)
+ *   CD6, d=2: (2 U_{i+3} - 27 U_{i+2} + 270 U_{i+1} - 490 U_i + 270 U_{i-1} - 27 U_{i-2} + 2 U_{i-3}) / (180 dx^2)
+ *   CD6, d=1: (U_{i+3} - 9 U_{i+2} + 45 U_{i+1} - 45 U_{i-1} + 9 U_{i-2} - U_{i-3}) / (60 dx), the textbook sixth-
+ *             order first derivative (the paper's sixth-order case is pure diffusion and prints none)      */
 static const double CD2_D1[3] = {-1.0, 0.0, 1.0};
 static const double CD2_D2[3] = {1.0, -2.0, 1.0};
 static const double CD4_D1[5] = {1.0, -8.0, 0.0, 8.0, -1.0};
 static const double CD4_D2[5] = {-1.0, 16.0, -30.0, 16.0, -1.0};
+static const double CD6_D1[7] = {-1.0, 9.0, -45.0, 0.0, 45.0, -9.0, 1.0};
+static const double CD6_D2[7] = {2.0, -27.0, 270.0, -490.0, 270.0, -27.0, 2.0};
 
 static void cd_table(int order, int deriv, const double **num, double *den) {
   if (order == 2) {
     *num = deriv == 1 ? CD2_D1 : CD2_D2;
     *den = deriv == 1 ? 2.0 : 1.0;
-  } else {
+  } else if (order == 4) {
     *num = deriv == 1 ? CD4_D1 : CD4_D2;
     *den = 12.0;
+  } else {
+    *num = deriv == 1 ? CD6_D1 : CD6_D2;
+    *den = deriv == 1 ? 60.0 : 180.0;
   }
 }
 
@@ -154,11 +164,22 @@ static void w_order4(int k, double w[3]) {
   w[2] = 0.5 * (kk * kk + kk);
 }
 
+/* Weights of the delayed copies in the (2,6,2) rows (read with U_{i-3} where the left rows print U_{i+3}):
+ *   (1/6)(k^3+6k^2+11k+6), -(1/2)(k^3+5k^2+6k), (1/2)(k^3+4k^2+3k), -(1/6)(k^3+3k^2+2k)
+ * at levels n-k, n-k-1, n-k-2, n-k-3. */
+static void w_order6(int k, double w[4]) {
+  double kk = (double)k, k2 = kk * kk, k3 = k2 * kk;
+  w[0] = (k3 + 6.0 * k2 + 11.0 * kk + 6.0) / 6.0;
+  w[1] = -(k3 + 5.0 * k2 + 6.0 * kk) / 2.0;
+  w[2] = (k3 + 4.0 * k2 + 3.0 * kk) / 2.0;
+  w[3] = -(k3 + 3.0 * k2 + 2.0 * kk) / 6.0;
+}
+
 static double dxpow(double dx, int d) { return d == 1 ? dx : dx * dx; }
 
 /* Taps of one derivative (deriv = 1 or 2) at a point at position pos (0..S-1) of its PE along
  * one axis.  use_pe = 0 means the axis has no PE boundary.  kL / kR are the effective delays of the
- * PE's left / right buffer points.  Returns the number of taps written to out (at most 16). */
+ * PE's left / right buffer points.  Returns the number of taps written to out (at most 32). */
 int orc_taps(int order, int scheme, int deriv, int64_t pos, int64_t S, int use_pe, int kL, int kR,
              double dx, orc_tap *out) {
   const int h = order / 2;
@@ -218,11 +239,13 @@ int orc_taps(int order, int scheme, int deriv, int64_t pos, int64_t S, int use_p
     out[3].j = -1; out[3].l = 0;     out[3].c = 1.0 / scale;
     return 4;
   }
-  /* (1,4,2) / (2,4,2): sum over m of w_m(k) times the CD4 stencil whose buffer points are read at
-   * level n-k-m; points inside the PE stay at level n. */
-  double w[3];
-  w_order4(k, w);
-  for (int m = 0; m < 3; ++m) {
+  /* (1,4,2) / (2,4,2) and (2,6,2): sum over m of w_m(k) times the central stencil whose buffer points are
+   * read at level n-k-m; points inside the PE stay at level n. */
+  double w[4];
+  int T = 3;
+  if (order == 4) w_order4(k, w);
+  else { w_order6(k, w); T = 4; }
+  for (int m = 0; m < T; ++m) {
     for (int j = -h; j <= h; ++j) {
       if (num[j + h] == 0.0) continue;
       int buf = (pos + j < 0) || (pos + j >= S);
@@ -239,7 +262,8 @@ int64_t orc_num_sides(const orc_cfg *g) { return 2 * (int64_t)g->dim * ptot(g); 
 
 int orc_check(const orc_cfg *g) {
   if (g->dim != 1 && g->dim != 3) return -1;
-  if (g->order != 2 && g->order != 4) return -1;
+  if (g->order != 2 && g->order != 4 && g->order != 6) return -1;
+  if (g->tsteps < 0 || g->tsteps > 3) return -1;
   if (g->scheme < 0 || g->scheme > 2) return -1;
   if (g->L < 1 || g->L > 8) return -1;
   if (g->nmodes < 1) return -1;
@@ -328,29 +352,49 @@ static double eval_taps(const orc_cfg *g, const double *const *lev, int64_t x, i
   return s;
 }
 
-/* One forward-Euler step, Eq. "time_disc" with T=1:
- *   U^{n+1} = U^n + dt * sum_axes ( -c_a D1_a U + alpha D2_a U ),
- * lev[m] = U^{n-m} (m = 0.. as deep as the delays need), keff = effective delay of every PE side. */
-int orc_step(const orc_cfg *g, const double *const *lev, const int32_t *keff, double *out) {
+/* Right-hand side f^n = sum_axes ( -c_a D1_a U + alpha D2_a U ) at every point, with the AT stencils at PE
+ * edges; lev[m] = U^{n-m} (m = 0.. as deep as the delays need), keff = effective delay of every PE side. */
+int orc_rhs(const orc_cfg *g, const double *const *lev, const int32_t *keff, double *f_out) {
   if (orc_check(g)) return -1;
   const int64_t nx = g->n[0], ny = g->n[1], N = ntot(g);
 #ifdef _OPENMP
 #pragma omp parallel for schedule(static) num_threads(g_threads)
 #endif
   for (int64_t pt = 0; pt < N; ++pt) {
-        const int64_t x = pt % nx, y = (pt / nx) % ny, z = pt / (nx * ny);
-        orc_tap taps[16];
-        double f = 0.0;
-        for (int a = 0; a < g->dim; ++a) {
-          int nt1 = point_taps(g, keff, x, y, z, a, 1, taps);
-          double d1 = eval_taps(g, lev, x, y, z, a, taps, nt1);
-          int nt2 = point_taps(g, keff, x, y, z, a, 2, taps);
-          double d2 = eval_taps(g, lev, x, y, z, a, taps, nt2);
-          f = f + (-g->c[a] * d1 + g->alpha * d2);
-        }
-        out[pt] = lev[0][pt] + g->dt * f;
+    const int64_t x = pt % nx, y = (pt / nx) % ny, z = pt / (nx * ny);
+    orc_tap taps[32];
+    double f = 0.0;
+    for (int a = 0; a < g->dim; ++a) {
+      int nt1 = point_taps(g, keff, x, y, z, a, 1, taps);
+      double d1 = eval_taps(g, lev, x, y, z, a, taps, nt1);
+      int nt2 = point_taps(g, keff, x, y, z, a, 2, taps);
+      double d2 = eval_taps(g, lev, x, y, z, a, taps, nt2);
+      f = f + (-g->c[a] * d1 + g->alpha * d2);
+    }
+    f_out[pt] = f;
   }
   return 0;
+}
+
+/* One forward-Euler step, Eq. "time_disc" with one level: U^{n+1} = U^n + dt f^n. */
+int orc_step(const orc_cfg *g, const double *const *lev, const int32_t *keff, double *out) {
+  if (orc_check(g)) return -1;
+  const int64_t N = ntot(g);
+  double *f = (double *)malloc(sizeof(double) * (size_t)N);
+  if (!f) return -2;
+  orc_rhs(g, lev, keff, f);
+  for (int64_t pt = 0; pt < N; ++pt) out[pt] = lev[0][pt] + g->dt * f[pt];
+  free(f);
+  return 0;
+}
+
+/* Adams-Bashforth weights (Eq. "time_disc"; Eq. "time_ab2" for two levels; the three-level weights are the
+ * textbook ones): beta[m] multiplies f^{n-m}.  A run starts with fewer levels: Euler, then AB2, then AB3. */
+static int ab_weights(int levels, double beta[3]) {
+  if (levels <= 1) { beta[0] = 1.0; return 1; }
+  if (levels == 2) { beta[0] = 1.5; beta[1] = -0.5; return 2; }
+  beta[0] = 23.0 / 12.0; beta[1] = -16.0 / 12.0; beta[2] = 5.0 / 12.0;
+  return 3;
 }
 
 /* Draw the delays of step n for every PE side (raw, logged) and clamp them (effective). */
@@ -383,21 +427,52 @@ int orc_run(const orc_cfg *g, const double *u0, int64_t nsteps, double *u_out, u
   if (orc_check(g) || nsteps < 0) return -1;
   const int T = orc_time_width(g->order, g->scheme);
   const int R = g->L + T;
+  const int ts = g->tsteps < 1 ? 1 : g->tsteps;
   const int64_t N = ntot(g), nb = orc_num_sides(g);
   double *ring = (double *)malloc(sizeof(double) * (size_t)(R * N));
+  double *fring = (double *)malloc(sizeof(double) * (size_t)(ts * N));
   int32_t *keff = (int32_t *)malloc(sizeof(int32_t) * (size_t)nb);
   const double **lev = (const double **)malloc(sizeof(double *) * (size_t)R);
-  if (!ring || !keff || !lev) { free(ring); free(keff); free(lev); return -2; }
+  if (!ring || !fring || !keff || !lev) { free(ring); free(fring); free(keff); free(lev); return -2; }
   if (u0) memcpy(ring, u0, sizeof(double) * (size_t)N); else orc_initial(g, ring);
   if (history) memcpy(history, ring, sizeof(double) * (size_t)N);
+  /* Multistep start (paper silent): from Eq. "IC" the right-hand sides of the ts-1 levels before t = 0 are
+   * those of the analytic solution at t = -m dt (synchronous stencils), so every step uses the full-order
+   * weights; from a caller's field the run starts with Euler, then AB2. */
+  int prehistory = 0;
+  if (ts > 1 && !u0) {
+    int32_t *zero = (int32_t *)calloc((size_t)nb, sizeof(int32_t));
+    double *ua = (double *)malloc(sizeof(double) * (size_t)N);
+    if (!zero || !ua) { free(zero); free(ua); free(ring); free(fring); free(keff); free(lev); return -2; }
+    for (int m = 1; m < ts; ++m) {
+      orc_analytic(g, -(double)m * g->dt, ua);
+      const double *l0[1] = {ua};
+      orc_rhs(g, l0, zero, fring + ((ts - m) % ts) * N);
+    }
+    free(zero); free(ua);
+    prehistory = 1;
+  }
   for (int64_t n = 0; n < nsteps; ++n) {
     draw_delays(g, n, T, delay_log ? delay_log + n * nb : NULL, keff);
     for (int m = 0; m < R - 1; ++m) lev[m] = (n - m >= 0) ? ring + ((n - m) % R) * N : NULL;
-    orc_step(g, lev, keff, ring + ((n + 1) % R) * N);
-    if (history) memcpy(history + (n + 1) * N, ring + ((n + 1) % R) * N, sizeof(double) * (size_t)N);
+    double *next = ring + ((n + 1) % R) * N;
+    if (ts == 1) {
+      orc_step(g, lev, keff, next);
+    } else {
+      /* U^{n+1} = U^n + dt sum_m beta_m f^{n-m} */
+      orc_rhs(g, lev, keff, fring + (n % ts) * N);
+      double beta[3];
+      const int nl = ab_weights(prehistory ? ts : (int)(n + 1 < ts ? n + 1 : ts), beta);
+      for (int64_t pt = 0; pt < N; ++pt) {
+        double sum = 0.0;
+        for (int m = 0; m < nl; ++m) sum = sum + beta[m] * fring[(((n - m) % ts + ts) % ts) * N + pt];
+        next[pt] = lev[0][pt] + g->dt * sum;
+      }
+    }
+    if (history) memcpy(history + (n + 1) * N, next, sizeof(double) * (size_t)N);
   }
   memcpy(u_out, ring + (nsteps % R) * N, sizeof(double) * (size_t)N);
-  free(ring); free(keff); free(lev);
+  free(ring); free(fring); free(keff); free(lev);
   return 0;
 }
 
@@ -451,7 +526,7 @@ int orc_error_stats(const orc_cfg *g, const double *u, int64_t n, double *out) {
  * lambda^n_i through the identity part of the Euler step.  dJ/dalpha = sum_n dt <lambda^{n+1}, D2 U>. */
 int orc_adjoint(const orc_cfg *g, const double *u0, int64_t nsteps, const double *u_target, double *grad_u0,
                 double *grad_alpha, double *J) {
-  if (orc_check(g) || nsteps < 0) return -1;
+  if (orc_check(g) || nsteps < 0 || g->tsteps > 1) return -1; /* the adjoint covers forward Euler */
   const int T = orc_time_width(g->order, g->scheme);
   const int64_t N = ntot(g), nb = orc_num_sides(g);
   const int64_t nx = g->n[0], ny = g->n[1], nz = g->n[2];
@@ -479,7 +554,7 @@ int orc_adjoint(const orc_cfg *g, const double *u0, int64_t nsteps, const double
           double lam = lam_next[i];
           adj[n * N + i] = adj[n * N + i] + lam;
           for (int a = 0; a < g->dim; ++a) {
-            orc_tap taps[16];
+            orc_tap taps[32];
             for (int deriv = 1; deriv <= 2; ++deriv) {
               int nt = point_taps(g, kn, x, y, z, a, deriv, taps);
               double fac = deriv == 1 ? -g->c[a] : g->alpha;

@@ -111,7 +111,7 @@ def _cond_rows(d, a, r=2):
 
 
 CASES = []
-for order in (2, 4):
+for order in (2, 4, 6):
     h = order // 2
     S = 8
     for pos in list(range(h)) + list(range(S - h, S)):
@@ -132,7 +132,7 @@ def test_at_taps_satisfy_taylor_conditions(order, pos, S, k, deriv):
         assert _moment(taps, p, q) == want, (p, q)
 
 
-@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("order", [2, 4, 6])
 @pytest.mark.parametrize("deriv", [1, 2])
 def test_at_taps_reduce_to_central_difference_at_k0(order, deriv):
     sync = oracle.taps(order, oracle.SYNC, deriv, 0, 8, 1, 0, 0, 1.0)
@@ -145,7 +145,7 @@ def test_at_taps_reduce_to_central_difference_at_k0(order, deriv):
         assert _moment(sync, p, 0) == want
 
 
-@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("order", [2, 4, 6])
 def test_standard_scheme_read_asynchronously_breaks_a_condition(order):
     """Eq. "general_deriv_async": the standard stencil at delayed levels violates the (0,1) row for d=2,
     which is why its accuracy drops (Sec. 2)."""
@@ -426,3 +426,67 @@ def test_adjoint_matches_central_differences(dim):
     d2 = (Ja(a0 + h / 2) - Ja(a0 - h / 2)) / h
     fd = (4 * d2 - d1) / 3
     assert ga == pytest.approx(fd, rel=1e-6)
+
+
+def test_printed_leading_async_term_of_the_sixth_order_row():
+    """(2,6,2): (49/864) k(k+1)(k+2)(k+3) u^(0,4) dt^4/dx^2 (the left row read with U_{i-3}); sign from the
+    four-level extrapolation remainder, which leaves the halo low by u_tttt prod(k+m) dt^4 / 4!."""
+    dx, dt, omega = 3e-3, 1e-3, 1.3
+    u4 = omega ** 4 * np.sin(0.4)  # d4/dt4 of sin(x - omega t + 0.4) at (0, 0)
+    for k in (1, 2, 3):
+        for side, pos, kl, kr in (("left", 0, k, 0), ("right", 15, 0, k)):
+            def evaluate(scheme):
+                taps = oracle.taps(6, scheme, 2, pos, 16, 1, kl, kr, dx)
+                return sum(c * _history_value(j * dx, -l * dt, omega) for j, l, c in taps)
+            lead = (49.0 / 864.0) * k * (k + 1) * (k + 2) * (k + 3) * u4 * dt ** 4 / dx ** 2
+            # next term: the buffer cells sit 1..3 dx from x_i, a relative O(dx cot 0.4) ~ 2 % shift
+            assert evaluate(oracle.AT) - evaluate(oracle.SYNC) == pytest.approx(-lead, rel=5e-2), (k, side)
+
+
+@pytest.mark.parametrize("tsteps,order", [(2, 4), (3, 6), (2, 2)])
+def test_multistep_sync_run_matches_its_fourier_recurrence(tsteps, order):
+    """Adams-Bashforth (Eq. "time_ab2"; three levels: 23/12, -16/12, 5/12) on one Fourier mode: the amplitude obeys
+    a_{n+1} = a_n + dt sum_m beta_m lam a_{n-m}, lam the symbol of the central stencils, with the levels before
+    t = 0 taken from the analytic solution a(t) = exp((-alpha kappa^2 - i c kappa) t) a_0."""
+    spec, _ = W.wl_1d(60, 5, order, 3, 0, 15, (2, 5), scheme=W.SYNC, tsteps=tsteps, r_alpha=0.05)
+    u, _, _ = oracle.run(oracle.Config(spec), 150)
+    n = spec["n"][0]
+    dx, dt, c, al = 2 * np.pi / n, spec["dt"], spec["c"][0], spec["alpha"]
+    beta = {2: [1.5, -0.5], 3: [23 / 12, -16 / 12, 5 / 12]}[tsteps]
+    x = np.arange(n) * dx
+    ref = np.zeros(n)
+    for A, ph, kap in zip(spec["amp"][0], spec["phase"][0], spec["kappa"][0]):
+        th = kap * dx
+        if order == 2:
+            s1, s2 = np.sin(th) / dx, (2 * np.cos(th) - 2) / dx ** 2
+        elif order == 4:
+            s1, s2 = _symbols(4, kap, dx)
+        else:
+            s1 = (45 * 2 * np.sin(th) - 9 * 2 * np.sin(2 * th) + 2 * np.sin(3 * th)) / (60 * dx)
+            s2 = (2 * 2 * np.cos(3 * th) - 27 * 2 * np.cos(2 * th) + 270 * 2 * np.cos(th) - 490) / (180 * dx ** 2)
+        lam = -c * 1j * s1 + al * s2
+        mu = -al * kap ** 2 - 1j * c * kap
+        f_hist = [lam * np.exp(mu * (-m * dt)) for m in range(1, tsteps)]  # f^{-1}, f^{-2}
+        a = 1.0 + 0j
+        hist = [lam * a] + f_hist
+        for _ in range(150):
+            a = a + dt * sum(b * fm for b, fm in zip(beta, hist))
+            hist = [lam * a] + hist[:-1]
+        ref += A * np.imag(a * np.exp(1j * (kap * x + ph)))
+    assert np.abs(u - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("case,ns,slope", [(4, (64, 128, 256), -4.0), (5, (96, 128, 192), -6.0)])
+def test_paper_cases_4_and_5_keep_their_design_order(case, ns, slope):
+    """Fig. "at-prob-all" (c), (d): with the time-expanded AT stencils and AB2 / AB3 the error against the
+    analytic solution falls at slope -4 (Case 4) and -6 (Case 5) whether the PEs run synchronously
+    (p_0 = 1) or with delays (p_0 = 0.7, 0)."""
+    for probs in ((1.0, 0.0, 0.0), (0.7, 0.2, 0.1), (0.0, 0.5, 0.5)):
+        errs = []
+        for n in ns:
+            spec = W.paper_case(case, n, 300, probs)
+            steps = int(round(0.1 / spec["dt"]))
+            cfg = oracle.Config(spec)
+            u, _, _ = oracle.run(cfg, steps, want_log=False, threads=4)
+            errs.append(oracle.error_stats(cfg, u, steps)["rms"])
+        assert abs(_slope(ns, errs) - slope) < 0.25, (probs, errs)

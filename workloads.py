@@ -42,9 +42,9 @@ def thresholds_from_probs(p) -> np.ndarray:
     return np.array([min(int(round(v * 2.0 ** 32)), 2 ** 32) for v in cum], dtype=np.uint64)
 
 
-def make(dim, n, pe, order, L, scheme, c, alpha, dt, seed, kappas, probs=None, ic_seed=None) -> dict:
+def make(dim, n, pe, order, L, scheme, c, alpha, dt, seed, kappas, probs=None, ic_seed=None, tsteps=1) -> dict:
     spec = {"dim": dim, "n": list(n), "pe": list(pe), "order": order, "L": L, "scheme": scheme,
-            "c": list(c), "alpha": float(alpha), "dt": float(dt), "seed": int(seed),
+            "c": list(c), "alpha": float(alpha), "dt": float(dt), "seed": int(seed), "tsteps": int(tsteps),
             "thresholds": None if probs is None else thresholds_from_probs(probs)}
     spec.update(ic_params(seed if ic_seed is None else ic_seed, dim, kappas))
     return spec
@@ -54,12 +54,13 @@ def dx_of(n: int) -> float:
     return TWO_PI / n
 
 
-def wl_1d(n, P, order, L, steps, seed, kappas, scheme=AT, c=1.0, alpha=0.1, r_alpha=0.1, probs=None):
+def wl_1d(n, P, order, L, steps, seed, kappas, scheme=AT, c=1.0, alpha=0.1, r_alpha=0.1, probs=None, tsteps=1):
     dt = r_alpha * dx_of(n) ** 2 / alpha
-    return make(1, [n], [P], order, L, scheme, [c], alpha, dt, seed, kappas, probs), steps
+    return make(1, [n], [P], order, L, scheme, [c], alpha, dt, seed, kappas, probs, tsteps=tsteps), steps
 
 
-def wl_3d(n, P, order, L, steps, seed, scheme=AT, c=(1.0, 1.0, 1.0), alpha=0.05, dt=None, kappas=(1, 2, 3)):
+def wl_3d(n, P, order, L, steps, seed, scheme=AT, c=(1.0, 1.0, 1.0), alpha=0.05, dt=None, kappas=(1, 2, 3),
+          tsteps=1):
     nn = list(n) if hasattr(n, "__len__") else [n, n, n]
     pp = list(P) if hasattr(P, "__len__") else [P, P, P]
     if dt is None:
@@ -67,7 +68,7 @@ def wl_3d(n, P, order, L, steps, seed, scheme=AT, c=(1.0, 1.0, 1.0), alpha=0.05,
         # forward Euler the order-4 AT stencils in 3D need r_alpha <= 1/16 per axis: their halo extrapolates
         # old levels, which amplifies the modes whose per-step factor 1 - 3 r_alpha 64/12 turns negative.
         dt = dx_of(max(nn)) ** 2
-    return make(3, nn, pp, order, L, scheme, list(c), alpha, dt, seed, kappas), steps
+    return make(3, nn, pp, order, L, scheme, list(c), alpha, dt, seed, kappas, tsteps=tsteps), steps
 
 
 def workload(name: str, scheme: int = AT):
@@ -85,6 +86,19 @@ def workload(name: str, scheme: int = AT):
     if name == "adjoint_256":
         return adjoint_spec(256, 4, 2000)
     raise KeyError(name)
+
+
+def paper_case(case: int, n: int, seed: int, p0_probs=(1.0, 0.0, 0.0), P: int = 16):
+    """Cases 4 and 5 of the paper's case table as used for Fig. "at-prob-all" (c), (d): kappa = {3,4,5},
+    A = {2, 0.5, 1.5}, P = 16, L = 3, phases random per seed.  Case 4: advection-diffusion, AB2, CD4 with
+    (1,4,2)/(2,4,2); Case 5: diffusion, AB3, CD6 with (2,6,2).  The figure does not give alpha, c or r_alpha:
+    alpha = 0.1, c = 1 (Case 4) or 0 (Case 5), r_alpha = 0.05 (Case 4) or 0.01 (Case 5): with the time-extrapolated
+    halos, AB2 and AB3 stay stable at every delay mix only at these smaller steps (the oracle diverges at
+    r_alpha = 0.1 / 0.02 when p_0 <= 0.3)."""
+    order, tsteps, c, r = (4, 2, 1.0, 0.05) if case == 4 else (6, 3, 0.0, 0.01)
+    spec, _ = wl_1d(n, P, order, 3, 0, seed, (3, 4, 5), c=c, alpha=0.1, r_alpha=r, probs=list(p0_probs), tsteps=tsteps)
+    spec["amp"] = np.array([[2.0, 0.5, 1.5]])
+    return spec
 
 
 def adjoint_spec(n=256, P=4, steps=2000, alpha=0.05, alpha_target=0.06, seed=5):
