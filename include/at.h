@@ -2,7 +2,8 @@
  * at.h -- C ABI of the GB300 (sm_103a) implementation of the asynchrony-tolerant (AT)
  * finite-difference method of Aditya & Donzis (arXiv:1702.00496).
  *
- * The hot path is the explicit forward-Euler step (Sec. 4.1, Eq. "time_disc" with one level) of
+ * The hot path is the explicit forward-Euler step (Sec. 4.1, Eq. "time_disc" with one level; Adams-Bashforth
+ * with two or three levels on request) of
  *     u_t + c . grad u = alpha lap u
  * on a periodic box [0, 2 pi)^dim (Sec. 5.1), split into emulated processing elements (PEs,
  * Sec. 2).  Interior points use central differences (Eq. "general_deriv_cds"); points within the
@@ -42,12 +43,12 @@ extern "C" {
 /* Spatial scheme at PE boundaries. */
 #define AT_SYNC 0      /* every delay is 0: standard central differences everywhere (Eq. "general_deriv") */
 #define AT_ASYNC_STD 1 /* central differences read at the delayed level n-k (Eq. "general_deriv_async") */
-#define AT_AT 2        /* asynchrony-tolerant, time-expanded stencils ((1,2,2)b/(2,2,2)b, (1,4,2)/(2,4,2)) */
+#define AT_AT 2        /* asynchrony-tolerant, time-expanded stencils ((1,2,2)b/(2,2,2)b, (1,4,2)/(2,4,2), (2,6,2)) */
 
 /* ------------------------------------------------------------------ scheme coefficients */
 typedef struct {
   int32_t deriv;  /* d: 1 or 2 */
-  int32_t order;  /* a: 2 or 4 (spatial order of accuracy) */
+  int32_t order;  /* a: 2, 4 or 6 (spatial order of accuracy) */
   int32_t L;      /* delays take values 0..L-1, L <= 8 */
   int32_t h;      /* half-width of the central stencil, a/2 */
   int32_t T;      /* successive delayed levels read at a buffer point, 1 + #{q >= 1 : 2q < d + a} */
@@ -64,7 +65,7 @@ typedef struct {
  * asynchronous Taylor terms u^(p,q), q >= 1, p + 2q < d + a (Eq. "cond", dt ~ dx^2).  Both systems are
  * solved in exact rational arithmetic with the rank tests of Sec. 3.2, and the expanded coefficients
  * are re-checked against every condition of Eq. "cond".  Host only; no CUDA call.
- * Errors: AT_ERR_ARG (deriv not 1/2, order not 2/4, L outside 1..8, out NULL), AT_ERR_SINGULAR,
+ * Errors: AT_ERR_ARG (deriv not 1/2, order not 2/4/6, L outside 1..8, out NULL), AT_ERR_SINGULAR,
  * AT_ERR_INCONSISTENT. */
 int at_coeffs(int32_t deriv, int32_t order, int32_t L, at_coeffs_t *out);
 
@@ -95,7 +96,7 @@ int at_delay(uint64_t seed, int64_t step, int64_t side, int32_t L, const uint64_
 /* ------------------------------------------------------------------ problem and handle */
 typedef struct {
   int32_t dim;     /* 1 or 3 */
-  int32_t order;   /* 2 or 4 */
+  int32_t order;   /* 2, 4 or 6 */
   int32_t L;       /* delays 0..L-1, 1 <= L <= 8 */
   int32_t scheme;  /* AT_SYNC, AT_ASYNC_STD or AT_AT */
   int64_t n[3];    /* points per axis (axes beyond dim hold 1) */
@@ -109,18 +110,25 @@ typedef struct {
   const double *amp;          /* host [dim][nmodes]: A in Eq. "IC" */
   const double *phase;        /* host [dim][nmodes]: phi in Eq. "IC" */
   const int32_t *kappa;       /* host [dim][nmodes]: wavenumbers in Eq. "IC" */
+  int32_t tsteps;  /* time integrator (Sec. 4.1, Eq. "time_disc"): 0 or 1 forward Euler, 2 Adams-Bashforth with two
+                    * levels (Eq. "time_ab2"), 3 with three levels (weights 23/12, -16/12, 5/12).  A multistep run
+                    * from Eq. "IC" takes the right-hand sides of the tsteps-1 levels before t = 0 from the analytic
+                    * solution (central differences), so every step has full order; from a caller's field
+                    * (at_reset with u0_dev) it starts with forward Euler and raises the order step by step. */
 } at_config_t;
 
 typedef struct at_handle at_handle_t;
 
-/* Ring-buffer depth R = L + T (T from at_coeffs for this order and scheme; 1 for SYNC/ASYNC_STD) and
- * the number of PE sides 2*dim*prod(pe).  Host only.  Errors: AT_ERR_ARG. */
+/* Ring-buffer slots R = L + T + (tsteps > 1 ? tsteps - 1 : 0): L + T solution levels (T from at_coeffs for this
+ * order and scheme; 1 for SYNC/ASYNC_STD), then, for Adams-Bashforth, the stored right-hand sides dt f^{n-m}
+ * (m = 1..tsteps-1).  at_num_sides: the number of PE sides 2*dim*prod(pe).  Host only.  Errors: AT_ERR_ARG. */
 int at_ring_slots(const at_config_t *cfg, int32_t *R);
 int at_num_sides(const at_config_t *cfg, int64_t *sides);
 
 /* Create a solver on caller-owned device memory and write U^0 (Eq. "IC"; the 3D field is the product
  * of per-axis sums) into ring slot 0.
- *   ring_dev : R * n0*n1*n2 doubles (R from at_ring_slots); level m lives in slot m mod R.
+ *   ring_dev : R * n0*n1*n2 doubles (R from at_ring_slots), 16-byte aligned for the vectorised kernels; level m
+ *              lives in slot m mod (L + T), the right-hand sides of Adams-Bashforth in the slots after those.
  *   log_dev  : log_steps * sides bytes, may be NULL when log_steps == 0; receives the raw delay of
  *              every PE side at every step (step-major), so each run can be replayed and audited.
  * The handle copies cfg and its host arrays and allocates a small scratch block for reductions.
@@ -128,7 +136,7 @@ int at_num_sides(const at_config_t *cfg, int64_t *sides);
 int at_init(const at_config_t *cfg, double *ring_dev, int64_t ring_len, uint8_t *log_dev, int64_t log_steps,
             void *stream, at_handle_t **out);
 
-/* Advance nsteps forward-Euler steps (the hot path).  Each step draws the delays of every PE side,
+/* Advance nsteps steps (the hot path; forward Euler or Adams-Bashforth per cfg->tsteps).  Each step draws the delays of every PE side,
  * extrapolates the halo each side reads from the delayed ring slots, and applies the fused stencil.
  * Enqueued on the handle's stream; returns without waiting.  Errors: AT_ERR_ARG, AT_ERR_STATE (the
  * delay log would overflow), AT_ERR_CUDA. */

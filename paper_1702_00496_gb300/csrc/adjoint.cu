@@ -140,7 +140,8 @@ __device__ __forceinline__ void adjoint_group(const AdjParams &a, const uint8_t 
   const int64_t i0 = row + x0;
   const double *ln = a.lam + ((n + 1) % a.Rl) * N;
   double d[4] = {0.0, 0.0, 0.0, 0.0};
-  if (a.alpha) group_eval<DIM, H, LdgNC, true>(f, keff, f.ring + (n % f.R) * N, n, x0, y, z, d);
+  double uc[4];
+  if (a.alpha) group_eval<DIM, H, LdgNC, true>(f, keff, f.ring + (n % f.R) * N, n, x0, y, z, d, uc);
   int pidx[3] = {x0 / f.S[0], 0, 0}, pos[3] = {0, 0, 0};
   pos[0] = x0 - pidx[0] * f.S[0];
   if (DIM == 3) {
@@ -488,8 +489,16 @@ cudaError_t copy_field(double *dst, const double *src, int64_t n, cudaStream_t s
 
 }  // namespace
 
+// The transposed step covers forward Euler with stencils of half-width 1 or 2.
+static int adjoint_supported(const at_handle *hd) {
+  if (hd->sp.ts > 1) return fail(AT_ERR_ARG, "adjoint: only forward Euler (tsteps 0 or 1) is supported");
+  if (hd->sp.h > 2) return fail(AT_ERR_ARG, "adjoint: only orders 2 and 4 are supported");
+  return AT_OK;
+}
+
 extern "C" int at_adjoint_workspace(at_handle_t *hd, int64_t nsteps, int64_t ckpt_every, int64_t *work_len) {
   if (!hd || nsteps < 0 || ckpt_every < 0 || !work_len) return fail(AT_ERR_ARG, "at_adjoint_workspace: bad argument");
+  if (int rc = adjoint_supported(hd)) return rc;
   *work_len = layout(hd, nsteps, ckpt_every).total;
   return AT_OK;
 }
@@ -497,6 +506,7 @@ extern "C" int at_adjoint_workspace(at_handle_t *hd, int64_t nsteps, int64_t ckp
 extern "C" int at_adjoint_forward(at_handle_t *hd, int64_t nsteps, int64_t ckpt_every, double *work_dev,
                                   int64_t work_len) {
   if (!hd || nsteps < 0 || ckpt_every < 0 || !work_dev) return fail(AT_ERR_ARG, "at_adjoint_forward: bad argument");
+  if (int rc = adjoint_supported(hd)) return rc;
   if (hd->step != 0) return fail(AT_ERR_STATE, "at_adjoint_forward: the handle must be at step 0 (at_reset)");
   const AdjLayout L = layout(hd, nsteps, ckpt_every);
   if (work_len < L.total) return fail(AT_ERR_ARG, "at_adjoint_forward: workspace too small");
@@ -525,6 +535,7 @@ extern "C" int at_adjoint_forward(at_handle_t *hd, int64_t nsteps, int64_t ckpt_
 extern "C" int at_adjoint_backward(at_handle_t *hd, const double *lambda_dev, double *grad_u0_dev,
                                    double *grad_alpha_host) {
   if (!hd || !lambda_dev || !grad_u0_dev) return fail(AT_ERR_ARG, "at_adjoint_backward: bad argument");
+  if (int rc = adjoint_supported(hd)) return rc;
   const bool want_alpha = grad_alpha_host != nullptr;
   if (hd->adj_nsteps < 0 || hd->step != hd->adj_nsteps)
     return fail(AT_ERR_STATE, "at_adjoint_backward: needs the at_adjoint_forward pass right before");

@@ -30,10 +30,14 @@ int cuda_fail(cudaError_t e, const char *where) {
 
 int time_width(const at_config_t *c) { return c->scheme == AT_AT ? c->order / 2 + 1 : 1; }
 
+// Time levels of the integrator: 1 (forward Euler), 2 (AB2) or 3 (AB3); 0 means 1.
+int time_levels(const at_config_t *c) { return c->tsteps < 2 ? 1 : c->tsteps; }
+
 int check_config(const at_config_t *c) {
   if (!c) return fail(AT_ERR_ARG, "config is NULL");
   if (c->dim != 1 && c->dim != 3) return fail(AT_ERR_ARG, "dim must be 1 or 3");
-  if (c->order != 2 && c->order != 4) return fail(AT_ERR_ARG, "order must be 2 or 4");
+  if (c->order != 2 && c->order != 4 && c->order != 6) return fail(AT_ERR_ARG, "order must be 2, 4 or 6");
+  if (c->tsteps < 0 || c->tsteps > 3) return fail(AT_ERR_ARG, "tsteps must be 0..3");
   if (c->scheme < AT_SYNC || c->scheme > AT_AT) return fail(AT_ERR_ARG, "scheme must be AT_SYNC, AT_ASYNC_STD or AT_AT");
   if (c->L < 1 || c->L > AT_MAX_L) return fail(AT_ERR_ARG, "L must be in 1..8");
   if (c->nmodes < 1 || c->nmodes > AT_MAX_MODES) return fail(AT_ERR_ARG, "nmodes must be in 1..16");
@@ -66,7 +70,8 @@ extern "C" int at_ring_slots(const at_config_t *cfg, int32_t *R) {
   int rc = check_config(cfg);
   if (rc) return rc;
   if (!R) return fail(AT_ERR_ARG, "R is NULL");
-  *R = cfg->L + time_width(cfg);
+  const int ts = time_levels(cfg);
+  *R = cfg->L + time_width(cfg) + (ts > 1 ? ts - 1 : 0);
   return AT_OK;
 }
 
@@ -100,11 +105,17 @@ int at_prepare_params(const at_config_t *cfg, double *ring_dev, uint8_t *log_dev
   p.ntot = cfg->n[0] * cfg->n[1] * cfg->n[2];
   p.nb = sides_of(cfg);
   p.dim = cfg->dim; p.h = h; p.T = T; p.R = cfg->L + T; p.L = cfg->L; p.scheme = cfg->scheme;
+  p.ts = time_levels(cfg);
+  p.frhs = p.ts > 1 && ring_dev ? ring_dev + (int64_t)p.R * p.ntot : nullptr;
+  // Adams-Bashforth weights of dt f^{n-m} with l = 1, 2, 3 stored levels (Eq. "time_ab2" for two levels; the
+  // three-level weights are the standard ones)
+  const double beta[3][3] = {{1.0, 0.0, 0.0}, {1.5, -0.5, 0.0}, {23.0 / 12.0, -16.0 / 12.0, 5.0 / 12.0}};
+  std::memcpy(p.beta, beta, sizeof(beta));
   p.seed = cfg->seed;
   p.use_thr = cfg->thresholds != nullptr;
   if (cfg->thresholds)
     for (int m = 0; m + 1 < cfg->L; ++m) p.thr[m] = cfg->thresholds[m];
-  double s0 = 1.0, q0 = 0.0;
+  double s0 = p.ts > 1 ? 0.0 : 1.0, q0 = 0.0;
   for (int a = 0; a < 3; ++a) {
     p.n[a] = (int32_t)cfg->n[a];
     p.pe[a] = cfg->pe[a];
@@ -126,16 +137,38 @@ int at_prepare_params(const at_config_t *cfg, double *ring_dev, uint8_t *log_dev
   return AT_OK;
 }
 
+// Start of an Adams-Bashforth history.  With the analytic initial condition the right-hand sides of the ts-1
+// levels before t = 0 are those of the analytic solution at t = -m dt with central differences (the paper does
+// not say how its multistep runs start; this keeps every step at the full order); from a caller's field the run
+// starts with forward Euler and raises the order as right-hand sides accumulate.  Ring slot 1 (level 1, which
+// the first step writes) holds the analytic field meanwhile.
+static cudaError_t ab_start(at_handle *hd, bool analytic) {
+  const StepParams &p = hd->sp;
+  if (p.ts <= 1) return cudaSuccess;
+  const int ns = p.ts - 1;
+  cudaError_t e = cudaSuccess;
+  if (analytic) {
+    double *tmp = p.ring + p.ntot;
+    for (int m = 1; m < p.ts && e == cudaSuccess; ++m) {
+      const int slot = ((-m) % ns + ns) % ns;
+      e = launch_wave_field(hd->wp, -(double)m * hd->cfg.dt, hd->d_tables, tmp, hd->stream);
+      if (e == cudaSuccess) e = launch_sync_rhs(p, tmp, p.frhs + (int64_t)slot * p.ntot, hd->stream);
+    }
+  }
+  if (e == cudaSuccess) e = launch_step_counter(hd->d_step + 1, analytic ? -(int64_t)ns : 0, true, hd->stream);
+  return e;
+}
+
 extern "C" int at_init(const at_config_t *cfg, double *ring_dev, int64_t ring_len, uint8_t *log_dev,
                        int64_t log_steps, void *stream, at_handle_t **out) {
   int rc = check_config(cfg);
   if (rc) return rc;
   if (!out || !ring_dev) return fail(AT_ERR_ARG, "ring_dev and out are required");
   if (log_steps < 0 || (log_steps > 0 && !log_dev)) return fail(AT_ERR_ARG, "log_dev required when log_steps > 0");
-  const int T = time_width(cfg);
-  const int R = cfg->L + T;
+  int32_t R = 0;
+  at_ring_slots(cfg, &R);
   const int64_t ntot = cfg->n[0] * cfg->n[1] * cfg->n[2];
-  if (ring_len < (int64_t)R * ntot) return fail(AT_ERR_ARG, "ring_len < R * points");
+  if (ring_len < (int64_t)R * ntot) return fail(AT_ERR_ARG, "ring_len < R * points (R from at_ring_slots)");
 
   at_handle *hd = new (std::nothrow) at_handle();
   if (!hd) return fail(AT_ERR_ARG, "out of host memory");
@@ -212,8 +245,10 @@ extern "C" int at_init(const at_config_t *cfg, double *ring_dev, int64_t ring_le
   hd->d_result = hd->d_partials + (size_t)AT_STAT_BLOCKS * AT_STAT_FIELDS;
   hd->d_tables = hd->d_result + 16;
   p.status = hd->d_status;
+  p.ab_first = hd->d_step + 1;
   if ((e = cudaMemsetAsync(hd->d_status, 0, sizeof(int32_t), hd->stream)) != cudaSuccess ||
       (e = launch_wave_field(w, 0.0, hd->d_tables, ring_dev, hd->stream)) != cudaSuccess ||
+      (e = ab_start(hd, true)) != cudaSuccess ||
       (e = launch_draw_delays(p, 0, hd->stream)) != cudaSuccess) {
     cudaFree(hd->scratch);
     delete hd;
@@ -278,6 +313,7 @@ extern "C" int at_reset(at_handle_t *hd, const double *u0_dev) {
                         hd->stream);
   else
     e = launch_wave_field(hd->wp, 0.0, hd->d_tables, hd->sp.ring, hd->stream);
+  if (e == cudaSuccess) e = ab_start(hd, u0_dev == nullptr);
   if (e == cudaSuccess) e = launch_draw_delays(hd->sp, 0, hd->stream);
   if (e != cudaSuccess) return cuda_fail(e, "at_reset");
   hd->step = 0;

@@ -233,8 +233,8 @@ void at_internal_set_error(const char *msg) {
 extern "C" const char *at_last_error(void) { return g_err; }
 
 extern "C" int at_coeffs(int32_t deriv, int32_t order, int32_t L, at_coeffs_t *out) {
-  if (!out || (deriv != 1 && deriv != 2) || (order != 2 && order != 4) || L < 1 || L > 8) {
-    at_internal_set_error("at_coeffs: deriv must be 1|2, order 2|4, 1 <= L <= 8, out non-NULL");
+  if (!out || (deriv != 1 && deriv != 2) || (order != 2 && order != 4 && order != 6) || L < 1 || L > 8) {
+    at_internal_set_error("at_coeffs: deriv must be 1|2, order 2|4|6, 1 <= L <= 8, out non-NULL");
     return AT_ERR_ARG;
   }
   g_overflow = false;
@@ -283,7 +283,7 @@ extern "C" int at_coeffs(int32_t deriv, int32_t order, int32_t L, at_coeffs_t *o
 
 extern "C" int at_stencil_taps(int32_t deriv, int32_t order, int32_t scheme, int32_t k, int32_t pos, int32_t side,
                                int32_t cap, int32_t *j_out, int32_t *l_out, double *c_out, int32_t *ntaps) {
-  if ((deriv != 1 && deriv != 2) || (order != 2 && order != 4) || scheme < 0 || scheme > 2 || k < 0 || k > 7 ||
+  if ((deriv != 1 && deriv != 2) || (order != 2 && order != 4 && order != 6) || scheme < 0 || scheme > 2 || k < 0 || k > 7 ||
       pos < 0 || side < 0 || side > 1 || cap < 0 || !j_out || !l_out || !c_out || !ntaps) {
     at_internal_set_error("at_stencil_taps: bad argument");
     return AT_ERR_ARG;

@@ -31,6 +31,8 @@ struct MemberParams {
   StepParams p;
   double amp[AT_MAX_MODES];        // A of Eq. "IC"
   double amp_final[AT_MAX_MODES];  // A exp(-alpha kappa^2 t_final)
+  double amp_pre[2][AT_MAX_MODES]; // Adams-Bashforth pre-history: A exp(alpha kappa^2 m dt), m = 1, 2
+  double shift_pre[2];             // and its phase shift c t = -c m dt
   double phase[AT_MAX_MODES];
   double kappa[AT_MAX_MODES];
   double dx, shift_final;          // grid spacing, c * t_final
@@ -46,9 +48,34 @@ __device__ double wave_1d(const MemberParams &m, const double *amp, double shift
   return s;
 }
 
+// Adams-Bashforth pre-history of a realization (the same start as a single problem): dt f of the analytic
+// solution at t = -m dt, m = 1..ts-1, with central differences, into the right-hand-side slot of level -m.
+// The member's PE split is switched off in the shared parameters meanwhile; ring slot 1 holds the field.
+template <int H>
+__device__ void member_prehistory(MemberParams &m) {
+  const int N = m.p.n[0], ns = m.p.ts - 1;
+  double *tmp = m.p.ring + m.p.ntot;
+  const int use_pe = m.p.use_pe[0];
+  __syncthreads();
+  if (threadIdx.x == 0) m.p.use_pe[0] = 0;
+  for (int mm = 1; mm <= ns; ++mm) {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tmp[i] = wave_1d(m, m.amp_pre[mm - 1], m.shift_pre[mm - 1], i);
+    __syncthreads();
+    double *out = m.p.frhs + (int64_t)(((-mm) % ns + ns) % ns) * m.p.ntot;
+    for (int k = threadIdx.x; k < (N >> 2); k += blockDim.x) {
+      double f[4], uc[4];
+      atfd::group_eval<1, H, atfd::LdCoherent, false>(m.p, nullptr, tmp, 0, k << 2, 0, 0, f, uc);
+      for (int q = 0; q < 4; ++q) out[(k << 2) + q] = f[q];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) m.p.use_pe[0] = use_pe;
+  __syncthreads();
+}
+
 // One realization, all steps: the delays of step n+1 are drawn (into the other half of the shared delay
 // buffer) while step n is computed; one barrier per step publishes both the new level and the new delays.
-template <int H>
+template <int H, bool AB>
 __device__ void run_member(const StepParams &p, uint8_t *keff_sh, int64_t nsteps) {
   const int groups = p.n[0] >> 2;
   atfd::draw_sides(p, 0, threadIdx.x, blockDim.x, keff_sh);
@@ -59,11 +86,15 @@ __device__ void run_member(const StepParams &p, uint8_t *keff_sh, int64_t nsteps
     if (n + 1 < nsteps) atfd::draw_sides(p, n + 1, threadIdx.x, blockDim.x, keff_sh + ((n + 1) & 1) * p.nb);
     const uint8_t *keff = keff_sh + (n & 1) * p.nb;
     for (int k = threadIdx.x; k < groups; k += blockDim.x)
-      atfd::group_update<1, H, atfd::LdCoherent>(p, keff, un, out, n, (int)(atfd::group_1d_order(p, k) << 2), 0, 0);
+      atfd::group_update<1, H, atfd::LdCoherent, AB>(p, keff, un, out, n, (int)(atfd::group_1d_order(p, k) << 2), 0,
+                                                     0);
     __syncthreads();
   }
 }
 
+// HMAX: the largest stencil half-width among the members; AB: some member uses Adams-Bashforth.  The host picks
+// the smallest variant that covers every member, so the common case keeps the register budget of H <= 2 Euler.
+template <int HMAX, bool AB>
 __global__ void __launch_bounds__(1024, 1) ensemble_kernel(const MemberParams *__restrict__ members,
                                                        const int32_t *__restrict__ order, int32_t count, int64_t nsteps,
                                                        int32_t *counter, double *__restrict__ member_stats) {
@@ -86,8 +117,18 @@ __global__ void __launch_bounds__(1024, 1) ensemble_kernel(const MemberParams *_
     const int N = m.p.n[0];
     for (int i = threadIdx.x; i < N; i += blockDim.x) m.p.ring[i] = wave_1d(m, m.amp, 0.0, i);
     __syncthreads();
-    if (m.p.h == 1) run_member<1>(m.p, keff_sh, nsteps);
-    else run_member<2>(m.p, keff_sh, nsteps);
+    if (AB && m.p.ts > 1) {
+      if (m.p.h == 1) member_prehistory<1>(m);
+      else if (HMAX == 2 || m.p.h == 2) member_prehistory<2>(m);
+      else member_prehistory<HMAX>(m);
+      if (m.p.h == 1) run_member<1, AB>(m.p, keff_sh, nsteps);
+      else if (HMAX == 2 || m.p.h == 2) run_member<2, AB>(m.p, keff_sh, nsteps);
+      else run_member<HMAX, AB>(m.p, keff_sh, nsteps);
+    } else {
+      if (m.p.h == 1) run_member<1, false>(m.p, keff_sh, nsteps);
+      else if (HMAX == 2 || m.p.h == 2) run_member<2, false>(m.p, keff_sh, nsteps);
+      else run_member<HMAX, false>(m.p, keff_sh, nsteps);
+    }
     // statistics of E = U^nsteps - u_a(x, nsteps dt), as in the single-problem reduction
     const double *u = m.p.ring + (nsteps % m.p.R) * m.p.ntot;
     double acc[kStatFields];
@@ -257,7 +298,10 @@ extern "C" int at_ensemble_create(const at_config_t *members, int32_t count, int
       m.phase[q] = c.phase[q];
       m.kappa[q] = (double)c.kappa[q];
       m.amp_final[q] = tf == 0.0 ? c.amp[q] : c.amp[q] * std::exp(-c.alpha * m.kappa[q] * m.kappa[q] * tf);
+      for (int mm = 1; mm <= 2; ++mm)
+        m.amp_pre[mm - 1][q] = c.amp[q] * std::exp(c.alpha * m.kappa[q] * m.kappa[q] * (double)mm * c.dt);
     }
+    for (int mm = 1; mm <= 2; ++mm) m.shift_pre[mm - 1] = -c.c[0] * (double)mm * c.dt;
     m.group = groups[c.n[0]];
     e->member_n.push_back(c.n[0]);
     ring_off += (int64_t)R * c.n[0];
@@ -278,16 +322,26 @@ extern "C" int at_ensemble_create(const at_config_t *members, int32_t count, int
   const size_t b_order = sizeof(int32_t) * (size_t)count;
   const size_t b_stats = sizeof(double) * (size_t)count * kStatFields;
   const size_t b_sum = sizeof(double) * 3 * (size_t)e->ngroups;
+  const size_t b_first = sizeof(int64_t) * (size_t)count;
   auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-  cudaError_t err = cudaMalloc(&e->scratch, up(b_members) + up(b_order) + 256 + up(b_stats) + up(b_sum));
+  cudaError_t err =
+      cudaMalloc(&e->scratch, up(b_members) + up(b_order) + 256 + up(b_stats) + up(b_sum) + up(b_first));
   if (err != cudaSuccess) { delete e; return cuda_fail(err, "at_ensemble_create: cudaMalloc"); }
   char *base = (char *)e->scratch;
   e->d_members = (MemberParams *)base; base += up(b_members);
   e->d_order = (int32_t *)base; base += up(b_order);
   e->d_counter = (int32_t *)base; base += 256;
   e->d_member_stats = (double *)base; base += up(b_stats);
-  e->d_summary = (double *)base;
-  if ((err = cudaMemcpy(e->d_members, host.data(), b_members, cudaMemcpyHostToDevice)) != cudaSuccess ||
+  e->d_summary = (double *)base; base += up(b_sum);
+  // every member starts from Eq. "IC" with the analytic pre-history: ts-1 right-hand sides stored before step 0
+  int64_t *d_first = (int64_t *)base;
+  std::vector<int64_t> first(count);
+  for (int r = 0; r < count; ++r) {
+    first[r] = -(int64_t)(host[r].p.ts - 1);
+    host[r].p.ab_first = d_first + r;
+  }
+  if ((err = cudaMemcpy(d_first, first.data(), b_first, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (err = cudaMemcpy(e->d_members, host.data(), b_members, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (err = cudaMemcpy(e->d_order, order.data(), b_order, cudaMemcpyHostToDevice)) != cudaSuccess) {
     cudaFree(e->scratch); delete e;
     return cuda_fail(err, "at_ensemble_create: upload");
@@ -301,7 +355,15 @@ extern "C" int at_ensemble_create(const at_config_t *members, int32_t count, int
     return fail(AT_ERR_ARG, "at_ensemble_create: a member has too many PE sides");
   }
   e->dyn_smem = dyn_smem;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, ensemble_kernel, threads, dyn_smem);
+  int hmax = 1;
+  bool any_ab = false;
+  for (int r = 0; r < count; ++r) {
+    hmax = std::max(hmax, (int)host[r].p.h);
+    any_ab = any_ab || host[r].p.ts > 1;
+  }
+  auto kernel = hmax <= 2 ? (any_ab ? ensemble_kernel<2, true> : ensemble_kernel<2, false>)
+                          : (any_ab ? ensemble_kernel<3, true> : ensemble_kernel<3, false>);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kernel, threads, dyn_smem);
   if (ctas_per_sm <= 0) ctas_per_sm = fit;
   if (ctas_per_sm > fit) ctas_per_sm = fit;
   if (ctas_per_sm < 1) ctas_per_sm = 1;
@@ -316,7 +378,7 @@ extern "C" int at_ensemble_create(const at_config_t *members, int32_t count, int
   err = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   if (err == cudaSuccess) {
     reset_counter<<<1, 1, 0, cap>>>(e->d_counter);
-    ensemble_kernel<<<e->blocks, threads, e->dyn_smem, cap>>>(e->d_members, e->d_order, count, nsteps, e->d_counter,
+    kernel<<<e->blocks, threads, e->dyn_smem, cap>>>(e->d_members, e->d_order, count, nsteps, e->d_counter,
                                                     e->d_member_stats);
     summary_kernel<<<1, 128, 0, cap>>>(e->d_member_stats, e->d_members, count, e->ngroups, e->d_summary);
     err = cudaStreamEndCapture(cap, &e->graph);

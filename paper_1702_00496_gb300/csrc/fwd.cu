@@ -1,16 +1,18 @@
 // fwd.cu -- the fused forward step of the asynchrony-tolerant (AT) scheme on sm_103a.
 //
 // One launch advances U^n -> U^{n+1} by forward Euler (Sec. 4.1, Eq. "time_disc" with one level):
-//     U^{n+1}_i = U^n_i + dt sum_a ( -c_a D1_a U + alpha D2_a U )_i
+//     U^{n+1}_i = U^n_i + dt sum_a ( -c_a D1_a U + alpha D2_a U )_i = U^n_i + dt f^n_i
 // with the central differences and the AT tables folded into merged per-axis coefficients
 //     s_{a,j} = dt ( -c_a cd1_j / dx_a + alpha cd2_j / dx_a^2 ),   s0 = 1 + sum_a s_{a,0},
-// so an interior point costs one multiply and 2*h*dim fused multiply-adds.
+// so an interior point costs one multiply and 2*h*dim fused multiply-adds.  With two or three time levels
+// (Adams-Bashforth, Eq. "time_disc"; Eq. "time_ab2") the chain, with s0 lacking the 1, forms dt f^n; the launch
+// adds the stored dt f^{n-1}, dt f^{n-2} of the previous launches with their weights and stores dt f^n.
 //
 // Points within h of a PE boundary (the set I_B of Sec. 2) read, for each stencil point across that
 // boundary (a buffer point), the extrapolated halo value
 //     u~ = sum_{m<T} w_m(k) U^{n-k-m}                                   (k = that side's delay)
 // where w_m(k) are the stage-2 weights of Example 3.  Since sum_m w_m(k) CD(.. U^{n-k-m} ..) =
-// CD(.. u~ ..) for the time-expanded tables ((1,2,2)b, (2,2,2)b, (1,4,2), (2,4,2)), the halo value is
+// CD(.. u~ ..) for the time-expanded tables ((1,2,2)b, (2,2,2)b, (1,4,2), (2,4,2), (2,6,2)), the halo value is
 // formed once and shared by the first- and second-derivative taps.  The delay k of every PE side is
 // drawn from Philox (Sec. 5.1) keyed by (seed, step, side) once per step -- by the launch of the previous
 // step, into a double-buffered array -- and clamped so that no level before 0 is read.
@@ -28,7 +30,7 @@ using namespace atfd;
 // Grouped kernel: a thread updates four consecutive x points per iteration (grid-stride); every thread
 // also draws the delays of one slice of the PE sides for step n+1 into the other half of the double-buffered
 // delay array, so the next launch finds them ready.
-template <int DIM, int H>
+template <int DIM, int H, bool AB>
 __global__ void __launch_bounds__(512) forward_group_kernel(const StepParams p, const int64_t n_off,
                                                             const int64_t *n_base) {
   const int64_t n = n_off + (n_base ? *n_base : 0);
@@ -42,19 +44,30 @@ __global__ void __launch_bounds__(512) forward_group_kernel(const StepParams p, 
   for (int64_t k = tid; k < groups; k += nthreads) {
     if (DIM == 1) {
       const int64_t g = group_1d_order(p, k);
-      group_update<1, H, LdgNC>(p, keff, un, out, n, (int)(g << 2), 0, 0);
+      group_update<1, H, LdgNC, AB>(p, keff, un, out, n, (int)(g << 2), 0, 0);
     } else {
       const int64_t g = p.order ? (int64_t)p.order[k] : k;
       const int64_t r = g / gx;
       const int x0 = (int)(g - r * gx) << 2;
       const int z = (int)(r / p.n[1]), y = (int)(r - (int64_t)z * p.n[1]);
-      group_update<3, H, LdgNC>(p, keff, un, out, n, x0, y, z);
+      group_update<3, H, LdgNC, AB>(p, keff, un, out, n, x0, y, z);
     }
   }
 }
 
+__device__ __forceinline__ void point_coords(const StepParams &p, int dim, int64_t i, int c[3]) {
+  c[0] = (int)i; c[1] = 0; c[2] = 0;
+  if (dim == 3) {
+    const int nx = p.n[0], ny = p.n[1];
+    const int64_t yz = i / nx;
+    c[0] = (int)(i - yz * nx);
+    c[2] = (int)(yz / ny);
+    c[1] = (int)(yz - (int64_t)c[2] * ny);
+  }
+}
+
 // Fallback for shapes the grouped kernel does not take (n[0] not a multiple of 4, odd slots).
-template <int DIM, int H>
+template <int DIM, int H, bool AB>
 __global__ void __launch_bounds__(512) forward_point_kernel(const StepParams p, const int64_t n_off,
                                                             const int64_t *n_base) {
   const int64_t n = n_off + (n_base ? *n_base : 0);
@@ -63,16 +76,41 @@ __global__ void __launch_bounds__(512) forward_point_kernel(const StepParams p, 
   const uint8_t *keff = p.keff + (n & 1) * p.nb;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nthreads = (int64_t)gridDim.x * blockDim.x;
   draw_sides(p, n + 1, tid, nthreads, p.keff + ((n + 1) & 1) * p.nb);
-  const int nx = p.n[0], ny = DIM == 3 ? p.n[1] : 1;
   for (int64_t i = tid; i < p.ntot; i += nthreads) {
-    int c[3] = {(int)i, 0, 0};
-    if (DIM == 3) {
-      const int64_t yz = i / nx;
-      c[0] = (int)(i - yz * nx);
-      c[2] = (int)(yz / ny);
-      c[1] = (int)(yz - (int64_t)c[2] * ny);
+    int c[3];
+    point_coords(p, DIM, i, c);
+    double r[1] = {point_update<DIM, H, LdgNC>(p, keff, un, n, i, c)};
+    if (AB) {
+      const double u[1] = {un[i]};
+      ab_combine<1>(p, n, i, u, r);
     }
-    out[i] = point_update<DIM, H, LdgNC>(p, keff, un, n, i, c);
+    out[i] = r[0];
+  }
+}
+
+// dt f(u) with central differences everywhere (p carries no PE split and s0 without the 1): the right-hand
+// sides before the first step of an Adams-Bashforth run.
+template <int DIM, int H>
+__global__ void __launch_bounds__(256) sync_rhs_kernel(const StepParams p, const double *__restrict__ u,
+                                                       double *__restrict__ out, int grouped) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nthreads = (int64_t)gridDim.x * blockDim.x;
+  if (grouped) {
+    const int gx = p.n[0] >> 2;
+    for (int64_t g = tid; g < p.ntot / 4; g += nthreads) {
+      const int64_t r = g / gx;
+      const int x0 = (int)(g - r * gx) << 2;
+      const int z = (int)(r / p.n[1]), y = (int)(r - (int64_t)z * p.n[1]);
+      double f[4], uc[4];
+      group_eval<DIM, H, LdgNC, false>(p, p.keff, u, 0, x0, y, z, f, uc);
+      const int64_t i0 = (DIM == 3 ? ((int64_t)z * p.n[1] + y) * p.n[0] : 0) + x0;
+      for (int q = 0; q < 4; ++q) out[i0 + q] = f[q];
+    }
+  } else {
+    for (int64_t i = tid; i < p.ntot; i += nthreads) {
+      int c[3];
+      point_coords(p, DIM, i, c);
+      out[i] = point_update<DIM, H, LdgNC>(p, p.keff, u, 0, i, c);
+    }
   }
 }
 
@@ -98,35 +136,71 @@ cudaError_t launch_draw_delays(const StepParams &p, int64_t n, cudaStream_t st) 
   return cudaGetLastError();
 }
 
+namespace {
+
+// groups of four x points must not straddle a PE and must start on 16 bytes
+bool grouped_shape(const StepParams &p, const void *base) {
+  return p.n[0] % 4 == 0 && (!p.use_pe[0] || p.S[0] % 4 == 0) && (reinterpret_cast<uintptr_t>(base) % 16) == 0 &&
+         (p.frhs == nullptr || (reinterpret_cast<uintptr_t>(p.frhs) % 16) == 0);
+}
+
+template <int DIM, int H, bool AB>
+void launch_typed(const StepParams &p, bool grouped, int blocks, int threads, int64_t n, const int64_t *n_base,
+                  cudaStream_t st) {
+  if (grouped) forward_group_kernel<DIM, H, AB><<<blocks, threads, 0, st>>>(p, n, n_base);
+  else forward_point_kernel<DIM, H, AB><<<blocks, threads, 0, st>>>(p, n, n_base);
+}
+
+template <int DIM, bool AB>
+void launch_h(const StepParams &p, bool grouped, int blocks, int threads, int64_t n, const int64_t *n_base,
+              cudaStream_t st) {
+  if (p.h == 1) launch_typed<DIM, 1, AB>(p, grouped, blocks, threads, n, n_base, st);
+  else if (p.h == 2) launch_typed<DIM, 2, AB>(p, grouped, blocks, threads, n, n_base, st);
+  else launch_typed<DIM, 3, AB>(p, grouped, blocks, threads, n, n_base, st);
+}
+
+int sm_count() {
+  int sms = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+}  // namespace
+
 cudaError_t launch_forward_step(const StepParams &p, int64_t n, const int64_t *n_base, cudaStream_t st) {
   const int threads = p.threads > 0 ? p.threads : 256;
-  int sms = 152;
-  {
-    int dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  }
-  const int max_blocks = sms * (p.blocks_per_sm > 0 ? p.blocks_per_sm : 32);
-  auto grid = [&](int64_t work) { int64_t b = (work + threads - 1) / threads; return (int)(b < max_blocks ? b : max_blocks); };
-  // groups of four x points must not straddle a PE and must start on 16 bytes
-  const bool grouped = p.n[0] % 4 == 0 && (!p.use_pe[0] || p.S[0] % 4 == 0) &&
-                       (reinterpret_cast<uintptr_t>(p.ring) % 16) == 0;
-  if (grouped) {
-    const int64_t groups = p.ntot / 4;
-    if (p.dim == 1) {
-      if (p.h == 1) forward_group_kernel<1, 1><<<grid(groups), threads, 0, st>>>(p, n, n_base);
-      else forward_group_kernel<1, 2><<<grid(groups), threads, 0, st>>>(p, n, n_base);
-    } else {
-      if (p.h == 1) forward_group_kernel<3, 1><<<grid(groups), threads, 0, st>>>(p, n, n_base);
-      else forward_group_kernel<3, 2><<<grid(groups), threads, 0, st>>>(p, n, n_base);
-    }
+  const int max_blocks = sm_count() * (p.blocks_per_sm > 0 ? p.blocks_per_sm : 32);
+  const bool grouped = grouped_shape(p, p.ring);
+  const int64_t work = grouped ? p.ntot / 4 : p.ntot;
+  const int64_t b = (work + threads - 1) / threads;
+  const int blocks = (int)(b < max_blocks ? b : max_blocks);
+  const bool ab = p.ts > 1;
+  if (p.dim == 1) {
+    if (ab) launch_h<1, true>(p, grouped, blocks, threads, n, n_base, st);
+    else launch_h<1, false>(p, grouped, blocks, threads, n, n_base, st);
   } else {
-    if (p.dim == 1) {
-      if (p.h == 1) forward_point_kernel<1, 1><<<grid(p.ntot), threads, 0, st>>>(p, n, n_base);
-      else forward_point_kernel<1, 2><<<grid(p.ntot), threads, 0, st>>>(p, n, n_base);
-    } else {
-      if (p.h == 1) forward_point_kernel<3, 1><<<grid(p.ntot), threads, 0, st>>>(p, n, n_base);
-      else forward_point_kernel<3, 2><<<grid(p.ntot), threads, 0, st>>>(p, n, n_base);
-    }
+    if (ab) launch_h<3, true>(p, grouped, blocks, threads, n, n_base, st);
+    else launch_h<3, false>(p, grouped, blocks, threads, n, n_base, st);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sync_rhs(const StepParams &p, const double *u, double *out, cudaStream_t st) {
+  StepParams q = p;
+  q.use_pe[0] = q.use_pe[1] = q.use_pe[2] = 0;  // no PE boundary: central differences at every point
+  const bool grouped = grouped_shape(q, u) && (reinterpret_cast<uintptr_t>(out) % 16) == 0;
+  const int64_t work = grouped ? q.ntot / 4 : q.ntot;
+  const int64_t b = (work + 255) / 256, cap = (int64_t)sm_count() * 8;
+  const int blocks = (int)(b < cap ? b : cap);
+  const int g = grouped ? 1 : 0;
+  if (q.dim == 1) {
+    if (q.h == 1) sync_rhs_kernel<1, 1><<<blocks, 256, 0, st>>>(q, u, out, g);
+    else if (q.h == 2) sync_rhs_kernel<1, 2><<<blocks, 256, 0, st>>>(q, u, out, g);
+    else sync_rhs_kernel<1, 3><<<blocks, 256, 0, st>>>(q, u, out, g);
+  } else {
+    if (q.h == 1) sync_rhs_kernel<3, 1><<<blocks, 256, 0, st>>>(q, u, out, g);
+    else if (q.h == 2) sync_rhs_kernel<3, 2><<<blocks, 256, 0, st>>>(q, u, out, g);
+    else sync_rhs_kernel<3, 3><<<blocks, 256, 0, st>>>(q, u, out, g);
   }
   return cudaGetLastError();
 }

@@ -9,7 +9,7 @@
 
 #define AT_MAX_L 8
 #define AT_MAX_T 4
-#define AT_MAX_H 2
+#define AT_MAX_H 3
 #define AT_MAX_MODES 16
 #define AT_STAT_FIELDS 9
 #define AT_STAT_BLOCKS 1024
@@ -24,6 +24,11 @@ struct StepParams {
   int64_t log_steps;      // rows of the log
   const int32_t *order;   // 3D: group visiting order (interior groups first, then edge groups), or nullptr
   int32_t *status;        // sticky device status word
+  double *frhs;           // Adams-Bashforth: ts-1 slots of ntot holding dt f^{n-m}, m = 1..ts-1, in slot
+                          // (n-m) mod (ts-1); nullptr for forward Euler
+  const int64_t *ab_first;  // device: first step whose right-hand side is stored (-(ts-1) after an analytic
+                            // pre-history, 0 after a caller's field); steps before ts-1 stored levels use
+                            // the lower-order weights
   int64_t ntot;           // points
   int64_t nb;             // PE sides, 2 * dim * prod(pe)
   int32_t n[3];           // points per axis
@@ -31,6 +36,7 @@ struct StepParams {
   int32_t pe[3];          // PEs per axis
   int32_t use_pe[3];      // axis has PE boundaries (pe > 1)
   int32_t dim, h, T, R, L, scheme;
+  int32_t ts;             // time levels of the integrator: 1 forward Euler, 2 AB2, 3 AB3
   int32_t use_thr;        // thresholds given (else uniform bins)
   uint64_t seed;
   uint64_t thr[AT_MAX_L]; // L-1 bin edges on the 32-bit word
@@ -38,6 +44,8 @@ struct StepParams {
   int32_t blocks_per_sm;  // and a cap on blocks per SM for its grid-stride loop
   double zero;            // +0.0, kept opaque so the compiler issues an FMA rather than a multiply
   double s0;              // merged centre coefficient: 1 + dt sum_a (-c_a cd1_0/dx_a + alpha cd2_0/dx_a^2)
+                          // (without the 1 for ts > 1, where the chain forms dt f^n)
+  double beta[3][3];      // Adams-Bashforth weights beta[l-1][m] of dt f^{n-m} with l stored levels
   double s[3][2 * AT_MAX_H + 1];  // merged off-centre coefficients per axis (index j+h)
   double q0;                      // d s0 / d alpha = dt sum_a cd2_0 / dx_a^2
   double q[3][2 * AT_MAX_H + 1];  // d s_{a,j} / d alpha = dt cd2_j / dx_a^2
@@ -68,6 +76,8 @@ cudaError_t launch_forward_step(const StepParams &p, int64_t n_off, const int64_
 cudaError_t launch_step_counter(int64_t *n_base, int64_t v, bool set, cudaStream_t st);
 // Draw the delays of step n into keff + (n & 1) * nb (and log row n): the set-up before a first step.
 cudaError_t launch_draw_delays(const StepParams &p, int64_t n, cudaStream_t st);
+// Adams-Bashforth pre-history: dt f of the field u with synchronous stencils into out (ntot doubles).
+cudaError_t launch_sync_rhs(const StepParams &p, const double *u, double *out, cudaStream_t st);
 cudaError_t launch_wave_field(const WaveParams &w, double t, double *tables, double *out, cudaStream_t st);
 cudaError_t launch_error_stats(const WaveParams &w, const StepParams &p, const double *u, double t,
                                double *tables, double *partials, double *result, cudaStream_t st);

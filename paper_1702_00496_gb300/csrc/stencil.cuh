@@ -2,13 +2,17 @@
 // persistent ensemble kernel (ensemble.cu).
 //
 // A thread updates a group of four consecutive x points (x0 a multiple of 4) of one (y, z) row.  It loads
-// the level-n values its merged stencil needs -- the x window x0-2 .. x0+5 and, in 3D, the four values of
-// rows y +- j and z +- j -- and replaces every value that lies outside the group's PE (a buffer point,
-// Sec. 2) by the halo value its PE side sees:
+// the level-n values its merged stencil needs -- the x window x0-W .. x0+3+W (W = h rounded up to even, so the
+// window starts on 16 bytes) and, in 3D, the four values of rows y +- j and z +- j -- and replaces every value
+// that lies outside the group's PE (a buffer point, Sec. 2) by the halo value its PE side sees:
 //     u~ = sum_{m<T} w_m(k) U^{n-k-m}     (k: that side's effective delay for step n; k = 0 keeps U^n)
 // Groups never straddle a PE (PE widths are multiples of 4 on these paths), so each loaded value is either
 // inside the PE or a buffer point of exactly one side.  The update is then the same chain of FMAs for every
 // group:  r = fma(s0, u_i, +0), the taps of axis x in offset order, then axis y, then axis z.
+//
+// With Adams-Bashforth time stepping (Sec. 4.1, Eq. "time_disc" with two or three levels) the same chain,
+// without the 1 in s0, gives dt f^n; the update adds the stored dt f^{n-1}, dt f^{n-2} with their weights and
+// keeps dt f^n in place of the oldest one.
 //
 // Delays are drawn once per PE side and step (Philox, Sec. 5.1) by a draw pass into a small array of
 // effective delays (uint8, clamped so that no level before 0 is read); the raw draw goes to the delay log.
@@ -87,13 +91,21 @@ __device__ __forceinline__ int64_t side_of(const StepParams &p, const int pidx[3
   return 2 * (int64_t)DIM * pe + 2 * a + hi;
 }
 
-// The merged stencil of the four points x0..x0+3 of row (y, z) into r[4]; requires n[0] % 4 == 0 and a
-// 16-byte aligned slot.  keff: effective delays of step n.  ALPHA = true evaluates the alpha derivative of the
-// step instead (coefficients q0, q: dt times the AT second derivative).
+// Half-width of the x window of a group: h rounded up to an even count, so the window's loads start on 16 bytes.
+template <int H>
+struct XWin {
+  static constexpr int W = (H + 1) / 2 * 2;
+  static constexpr int N = 4 + 2 * W;
+};
+
+// The merged stencil of the four points x0..x0+3 of row (y, z) into r[4] (and their level-n values into uc[4]);
+// requires n[0] % 4 == 0 and a 16-byte aligned slot.  keff: effective delays of step n.  ALPHA = true evaluates
+// the alpha derivative of the step instead (coefficients q0, q: dt times the AT second derivative).
 template <int DIM, int H, class LD, bool ALPHA>
 __device__ __forceinline__ void group_eval(const StepParams &p, const uint8_t *__restrict__ keff,
                                            const double *__restrict__ un, int64_t n, int x0, int y, int z,
-                                           double r[4]) {
+                                           double r[4], double uc[4]) {
+  constexpr int W = XWin<H>::W, NW = XWin<H>::N;
   const int nx = p.n[0];
   const int sn = (int)(n % p.R);
   const int64_t row = DIM == 3 ? ((int64_t)z * p.n[1] + y) * nx : 0;
@@ -104,31 +116,36 @@ __device__ __forceinline__ void group_eval(const StepParams &p, const uint8_t *_
     pidx[1] = y / p.S[1]; pos[1] = y - pidx[1] * p.S[1];
     pidx[2] = z / p.S[2]; pos[2] = z - pidx[2] * p.S[2];
   }
-  // x window: cells x0-2 .. x0+5 of the row
-  double v[8];
-  if (x0 >= 2 && x0 + 6 <= nx) {
-    const double2 a = LD::ld2(un + i0 - 2), b = LD::ld2(un + i0), c = LD::ld2(un + i0 + 2), d = LD::ld2(un + i0 + 4);
-    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y; v[6] = d.x; v[7] = d.y;
+  // x window: cells x0-W .. x0+3+W of the row
+  double v[NW];
+  if (x0 >= W && x0 + 4 + W <= nx) {
+#pragma unroll
+    for (int t = 0; t < NW; t += 2) {
+      const double2 a = LD::ld2(un + i0 - W + t);
+      v[t] = a.x; v[t + 1] = a.y;
+    }
   } else {
 #pragma unroll
-    for (int t = 0; t < 8; ++t) v[t] = LD::ld(un + row + wrap_coord(x0 - 2 + t, nx));
+    for (int t = 0; t < NW; ++t) v[t] = LD::ld(un + row + wrap_coord(x0 - W + t, nx));
   }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) uc[q] = v[W + q];
   if (p.use_pe[0] && (pos[0] < H || pos[0] + 3 >= p.S[0] - H)) {
     const int kl = keff[side_of<DIM>(p, pidx, 0, 0)], kr = keff[side_of<DIM>(p, pidx, 0, 1)];
 #pragma unroll
-    for (int t = 2 - H; t <= 5 + H; ++t) {
-      const int rel = pos[0] - 2 + t;
+    for (int t = W - H; t <= W + 3 + H; ++t) {
+      const int rel = pos[0] - W + t;
       const int k = rel < 0 ? kl : (rel >= p.S[0] ? kr : 0);
-      if (k > 0) v[t] = halo_value<LD>(p, row + wrap_coord(x0 - 2 + t, nx), sn, k);
+      if (k > 0) v[t] = halo_value<LD>(p, row + wrap_coord(x0 - W + t, nx), sn, k);
     }
   }
   const double c0 = ALPHA ? p.q0 : p.s0;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    double acc = fma(c0, v[q + 2], p.zero);
+    double acc = fma(c0, v[q + W], p.zero);
 #pragma unroll
     for (int j = -H; j <= H; ++j)
-      if (j != 0) acc = fma(ALPHA ? p.q[0][j + H] : p.s[0][j + H], v[q + 2 + j], acc);
+      if (j != 0) acc = fma(ALPHA ? p.q[0][j + H] : p.s[0][j + H], v[q + W + j], acc);
     r[q] = acc;
   }
   if (DIM == 3) {
@@ -164,14 +181,64 @@ __device__ __forceinline__ void group_eval(const StepParams &p, const uint8_t *_
   }
 }
 
-// Update the four points x0..x0+3 of row (y, z) (the forward step).
-template <int DIM, int H, class LD>
+// NP consecutive stored right-hand sides (16-byte aligned for NP > 1).
+template <int NP>
+__device__ __forceinline__ void ab_load(const double *src, double a[NP]) {
+  if constexpr (NP == 1) {
+    a[0] = src[0];
+  } else {
+#pragma unroll
+    for (int q = 0; q < NP; q += 2) {
+      const double2 v = *reinterpret_cast<const double2 *>(src + q);
+      a[q] = v.x; a[q + 1] = v.y;
+    }
+  }
+}
+
+// Adams-Bashforth combination of NP consecutive points starting at i (16-byte aligned for NP = 4): r holds
+// dt f^n and becomes U^{n+1} = U^n + sum_{m<l} beta_m dt f^{n-m} (l = levels stored so far, at most ts); dt f^n
+// takes the slot of the oldest right-hand side, which only this thread reads, after the read.
+template <int NP>
+__device__ __forceinline__ void ab_combine(const StepParams &p, int64_t n, int64_t i, const double u[NP],
+                                           double r[NP]) {
+  const int64_t stored = n - *p.ab_first + 1;
+  const int l = stored < p.ts ? (int)stored : p.ts;
+  const double *beta = p.beta[l - 1];
+  const bool two = p.ts == 3;  // two stored slots, else one
+  double *f_now = p.frhs + (two ? (n & 1) : 0) * p.ntot + i;          // dt f^{n-2} (AB3) or dt f^{n-1} (AB2)
+  const double *f_1 = p.frhs + (two ? ((n - 1) & 1) : 0) * p.ntot + i;  // dt f^{n-1}
+  double t[NP], a[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) t[q] = fma(beta[0], r[q], p.zero);
+  if (l > 1) {
+    ab_load<NP>(f_1, a);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) t[q] = fma(beta[1], a[q], t[q]);
+  }
+  if (l > 2) {
+    ab_load<NP>(f_now, a);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) t[q] = fma(beta[2], a[q], t[q]);
+  }
+  if constexpr (NP == 1) {
+    f_now[0] = r[0];
+  } else {
+#pragma unroll
+    for (int q = 0; q < NP; q += 2) *reinterpret_cast<double2 *>(f_now + q) = make_double2(r[q], r[q + 1]);
+  }
+#pragma unroll
+  for (int q = 0; q < NP; ++q) r[q] = u[q] + t[q];
+}
+
+// Update the four points x0..x0+3 of row (y, z) (the forward step; AB: Adams-Bashforth, else forward Euler).
+template <int DIM, int H, class LD, bool AB = false>
 __device__ __forceinline__ void group_update(const StepParams &p, const uint8_t *__restrict__ keff,
                                              const double *__restrict__ un, double *__restrict__ out, int64_t n,
                                              int x0, int y, int z) {
-  double r[4];
-  group_eval<DIM, H, LD, false>(p, keff, un, n, x0, y, z, r);
+  double r[4], uc[4];
+  group_eval<DIM, H, LD, false>(p, keff, un, n, x0, y, z, r, uc);
   const int64_t i0 = (DIM == 3 ? ((int64_t)z * p.n[1] + y) * p.n[0] : 0) + x0;
+  if (AB) ab_combine<4>(p, n, i0, uc, r);
   reinterpret_cast<double2 *>(out + i0)[0] = make_double2(r[0], r[1]);
   reinterpret_cast<double2 *>(out + i0)[1] = make_double2(r[2], r[3]);
 }

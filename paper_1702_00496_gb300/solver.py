@@ -9,8 +9,9 @@ from . import binding as B
 class Solver:
     """One AT problem on the GPU.
 
-    The ring buffer holds R = L + T full time levels (level m in slot m mod R); the delay log holds the
-    raw delay of every PE side at every step, so the run can be replayed.  All arithmetic happens in
+    The ring buffer holds the L + T time levels (level m in slot m mod (L + T)) and, for Adams-Bashforth, the
+    stored right-hand sides after them; the delay log holds the raw delay of every PE side at every step, so
+    the run can be replayed.  All arithmetic happens in
     libatfd's kernels; this class only allocates memory and forwards calls.
     """
 
@@ -45,9 +46,9 @@ class Solver:
 
     def field(self) -> torch.Tensor:
         """View of U^n inside the ring (shape (nx,) or (nz, ny, nx))."""
-        n = self.n
-        slot = n % self.R
-        return self.ring[slot * self.cfg.ntot:(slot + 1) * self.cfg.ntot].view(self.cfg.shape)
+        _, ptr = B.at_state(self.h)
+        off = (ptr - self.ring.data_ptr()) // self.ring.element_size()
+        return self.ring[off:off + self.cfg.ntot].view(self.cfg.shape)
 
     def delays(self) -> torch.Tensor:
         """Raw delays logged so far, [steps, sides] uint8."""
@@ -117,7 +118,8 @@ class Ensemble:
     def field(self, r: int) -> torch.Tensor:
         """Member r's field at its final step (valid after run())."""
         c = self.cfgs[r]
-        slot = self.nsteps % self.R[r]
+        levels = self.R[r] - (c.tsteps - 1)  # slots after the L + T levels hold Adams-Bashforth right-hand sides
+        slot = self.nsteps % levels
         o = self.ring_off[r] + slot * c.ntot
         return self.ring[o:o + c.ntot]
 

@@ -53,7 +53,9 @@ def test_example3_two_stage_coefficients():
 
 
 @pytest.mark.parametrize("deriv,order,cd,den", [(1, 2, [-1, 0, 1], 2), (2, 2, [1, -2, 1], 1),
-                                                 (1, 4, [1, -8, 0, 8, -1], 12), (2, 4, [-1, 16, -30, 16, -1], 12)])
+                                                 (1, 4, [1, -8, 0, 8, -1], 12), (2, 4, [-1, 16, -30, 16, -1], 12),
+                                                 (1, 6, [-1, 9, -45, 0, 45, -9, 1], 60),
+                                                 (2, 6, [2, -27, 270, -490, 270, -27, 2], 180)])
 def test_central_weights_and_time_width(deriv, order, cd, den):
     c = P.at_coeffs(deriv, order, 3)
     got = [Fraction(c.cd_num[j], c.cd_den) for j in range(2 * c.h + 1)]
@@ -63,6 +65,9 @@ def test_central_weights_and_time_width(deriv, order, cd, den):
         w = [Fraction(c.w_num[k][m], c.w_den[k]) for m in range(c.T)]
         if order == 2:
             assert w == [k + 1, -k]
+        if order == 6:  # the weights of the (2,6,2) rows: a cubic in k per delayed level
+            assert w == [Fraction(k ** 3 + 6 * k ** 2 + 11 * k + 6, 6), -Fraction(k ** 3 + 5 * k ** 2 + 6 * k, 2),
+                         Fraction(k ** 3 + 4 * k ** 2 + 3 * k, 2), -Fraction(k ** 3 + 3 * k ** 2 + 2 * k, 6)]
 
 
 def _merge(taps):
@@ -72,7 +77,7 @@ def _merge(taps):
     return {key: v for key, v in out.items() if v != 0.0}
 
 
-@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("order", [2, 4, 6])
 @pytest.mark.parametrize("deriv", [1, 2])
 @pytest.mark.parametrize("scheme", [P.AT_SYNC, P.AT_ASYNC_STD, P.AT_AT])
 def test_derived_taps_equal_the_oracle_tables(order, deriv, scheme):
@@ -118,7 +123,7 @@ def test_example1_closed_form_and_degenerate_cases():
 
 
 def test_coeffs_argument_errors():
-    for args in [(3, 2, 3), (1, 3, 3), (1, 2, 0), (1, 2, 9)]:
+    for args in [(3, 2, 3), (1, 3, 3), (1, 8, 3), (1, 2, 0), (1, 2, 9)]:
         with pytest.raises(B.ATError) as e:
             P.at_coeffs(*args)
         assert e.value.code == B.AT_ERR_ARG
@@ -147,10 +152,15 @@ def test_ring_depth_and_side_count():
     assert P.at_ring_slots(cfg) == 3 + 2 and P.at_num_sides(cfg) == 6 * 512
     spec["scheme"] = W.ASYNC_STD
     assert P.at_ring_slots(B.Config(spec)) == 3 + 1
+    # Adams-Bashforth: tsteps - 1 stored right-hand sides after the L + T levels
+    for tsteps, extra in ((0, 0), (1, 0), (2, 1), (3, 2)):
+        spec, _ = W.wl_1d(256, 8, 6, 3, 0, 1, (1, 2), tsteps=tsteps)
+        assert P.at_ring_slots(B.Config(spec)) == 3 + 4 + extra
 
 
-@pytest.mark.parametrize("field,value", [("n", [100]), ("pe", [3]), ("order", 6), ("L", 0), ("L", 9),
-                                         ("scheme", 5), ("dim", 2), ("dt", -1.0), ("pe", [128])])
+@pytest.mark.parametrize("field,value", [("n", [100]), ("pe", [3]), ("order", 8), ("order", 3), ("L", 0), ("L", 9),
+                                         ("scheme", 5), ("dim", 2), ("dt", -1.0), ("pe", [128]), ("tsteps", 4),
+                                         ("tsteps", -1)])
 def test_invalid_configs_are_rejected_on_the_host(field, value):
     spec, _ = W.wl_1d(256, 8, 4, 3, 0, 1, (1, 2))
     spec[field] = value
