@@ -33,7 +33,7 @@ METRIC = "grid-point updates/s (FP64)"
 PEAK_FP64_FLOPS = 152 * 2 * 2 * 2.07e9  # 152 SMs x 2 FP64 FMA lanes/clk x 2 flop x 2.07 GHz max clock
 # DRAM bytes (read + write) per launch of the step kernel from one ncu capture of the current kernel source
 # (profiles/forward_group_kernel_1d_n16m.md); None where no capture of the current source exists.
-MEASURED_TRAFFIC = {("1d_n16m", "forward_group_kernel<1,2>"): 134.798080e6 + 83.307264e6}
+MEASURED_TRAFFIC = {}
 
 
 def measured_peaks():
@@ -123,10 +123,41 @@ def aggregate_rate(units_per_rank: float, world: int, seconds: float) -> float:
     return world * units_per_rank / seconds
 
 
+def time_levels(spec) -> int:
+    return max(1, int(spec.get("tsteps", 1)))
+
+
 def flops_per_update(spec) -> int:
-    """FP64 flops of the merged stencil per interior point: 1 multiply + 2*h*dim FMAs (2 flops each)."""
+    """FP64 flops per interior point: the merged stencil, 1 multiply + 2*h*dim FMAs (2 flops each); with
+    Adams-Bashforth (ts levels) also the weighted sum of the right-hand sides, 1 multiply + (ts-1) FMAs, and the
+    final add."""
     h = spec["order"] // 2
-    return 1 + 2 * (2 * h * spec["dim"])
+    f = 1 + 2 * (2 * h * spec["dim"])
+    ts = time_levels(spec)
+    if ts > 1:
+        f += 1 + 2 * (ts - 1) + 1
+    return f
+
+
+def bytes_per_update(spec) -> int:
+    """Algorithmic HBM bytes per point and step: read U^n, write U^{n+1}; with Adams-Bashforth also read the ts-1
+    stored right-hand sides and write dt f^n (halo reads of delayed levels are not counted)."""
+    ts = time_levels(spec)
+    return 16 + (8 * ts if ts > 1 else 0)
+
+
+def launches_per_run(spec, T: int) -> int:
+    """Kernels of this library one timed run launches: the reset (initial field, Adams-Bashforth pre-history and
+    its history counter, the first delay draw), T forward steps (one counter update before the captured graphs,
+    each 50-step graph holding 50 step kernels and a counter kernel; the remainder launched one by one) and the
+    error statistics."""
+    dim, ts = spec["dim"], time_levels(spec)
+    wave = 1 if dim == 1 else 2
+    reset = wave + 1 + (((ts - 1) * (wave + 1) + 1) if ts > 1 else 0)
+    chunks = T // 50
+    step = (1 + 51 * chunks if chunks else 0) + (T - 50 * chunks)
+    stats = 2 if dim == 1 else 3
+    return reset + step + stats
 
 
 def cpu_sample(spec, nsteps: int, threads: int) -> float:
@@ -409,9 +440,9 @@ def main():
     peaks = measured_peaks()
     flops_launch = flops_per_update(spec) * ntot
     achieved = flops_launch / (kern_ms / 1e3)
-    bytes_launch = 16 * ntot  # read U^n, write U^{n+1} (halo reads of delayed levels not counted)
+    bytes_launch = bytes_per_update(spec) * ntot
     hbm = peaks.get("hbm_gbs")
-    kname = f"forward_group_kernel<{spec['dim']},{spec['order'] // 2}>"
+    kname = f"forward_group_kernel<{spec['dim']},{spec['order'] // 2},{'true' if time_levels(spec) > 1 else 'false'}>"
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": PEAK_FP64_FLOPS / 1e12, "unit": "TFLOP/s",
                 "frac": achieved / PEAK_FP64_FLOPS, "traffic": MEASURED_TRAFFIC.get((args.workload, kname)),
                 "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
@@ -434,12 +465,12 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": args.workload, "points": ntot, "pes": spec["pe"], "order": spec["order"],
-                           "L": spec["L"], "time_steps_per_step": T, "l2": "flushed (512 MiB write) each step",
+                           "L": spec["L"], "time_levels": time_levels(spec), "time_steps_per_step": T, "l2": "flushed (512 MiB write) each step",
                            "replicas": world, "launch": {"threads": launch[0], "blocks_per_sm": launch[1]}},
                 "e2e": {"value": e2e_value, "unit": "updates/s", "h2d_bytes_per_step": 8 * ntot,
                         "d2h_bytes_per_step": 8 * ntot + 8 * 9},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
-                "gpu_launches": args.steps * (T + 3),
+                "gpu_launches": args.steps * launches_per_run(spec, T),
                 "final_rms_error": last["rms"]}
         print(json.dumps(line), flush=True)
     solver.close()

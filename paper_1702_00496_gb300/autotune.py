@@ -44,7 +44,7 @@ def _device_key() -> str:
 
 def forward_signature(spec: dict) -> str:
     return (f"{_device_key()}|fwd|dim{spec['dim']}|n{'x'.join(map(str, spec['n']))}|pe{'x'.join(map(str, spec['pe']))}"
-            f"|o{spec['order']}|L{spec['L']}|s{spec['scheme']}")
+            f"|o{spec['order']}|L{spec['L']}|s{spec['scheme']}|t{max(1, int(spec.get('tsteps', 1)))}")
 
 
 def tune_forward(solver, spec: dict, sample_steps: int = 50, use_cache: bool = True):
