@@ -129,13 +129,12 @@ def time_levels(spec) -> int:
 
 def flops_per_update(spec) -> int:
     """FP64 flops per interior point: the merged stencil, 1 multiply + 2*h*dim FMAs (2 flops each); with
-    Adams-Bashforth (ts levels) also the weighted sum of the right-hand sides, 1 multiply + (ts-1) FMAs, and the
-    final add."""
+    Adams-Bashforth (ts levels) also the ts FMAs that add the weighted right-hand sides to U^n."""
     h = spec["order"] // 2
     f = 1 + 2 * (2 * h * spec["dim"])
     ts = time_levels(spec)
     if ts > 1:
-        f += 1 + 2 * (ts - 1) + 1
+        f += 2 * ts
     return f
 
 
@@ -198,6 +197,21 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+SWEEPS = ("sweep_scaling", "sweep_kmom")
+
+
+def sweep_members(name: str):
+    """Member lists of the paper's sweeps (Sec. 5.2) with synchronous twins: (specs, steps, groups, twins).
+    sweep_scaling: Fig. "at-ord2-procs", Case 1 with p_k = {0.2, 0.5, 0.3}, P in {2..32} at N = 512, strong
+    (P = 16) and weak (P/N = 1/16) series over N in {128..1024}, 32 realizations each, every member to t = 0.1.
+    sweep_kmom: Fig. "at-kmom", Case 4 at N = 512, P = 16, L in {2, 3, 4} with p_k = 1/L, 64 realizations each."""
+    if name == "sweep_scaling":
+        ns = (128, 256, 512, 1024)
+        grids = [(512, P) for P in (2, 4, 8, 16, 32)] + [(n, 16) for n in ns] + [(n, n // 16) for n in ns]
+        return W.scaling_members(1, grids, range(800, 832))
+    return W.moment_members(4, (2, 3, 4), range(900, 964))
+
+
 def run_ensemble(args, rank: int, world: int, local: int):
     """1024 1D realizations (N_r in 2^10..2^16, L_r in 2..4, 5000 steps) in one persistent graph launch, against
     the same realizations run one problem at a time through the single-problem path (graph-captured steps)."""
@@ -205,18 +219,25 @@ def run_ensemble(args, rank: int, world: int, local: int):
     import torch.distributed as dist
     from paper_1702_00496_gb300 import Ensemble, Solver
 
-    specs, T = W.ensemble_members()
-    if args.time_steps is not None:
-        T = args.time_steps
+    groups_in = twins = None
+    if args.workload == "ensemble":
+        specs, T = W.ensemble_members()
+        if args.time_steps is not None:
+            T = args.time_steps
+        steps = [T] * len(specs)
+    else:
+        specs, steps, groups_in, twins = sweep_members(args.workload)
+        T = None
     for s in specs:
         s["seed"] = replica_seed(s["seed"], rank, 100000)
-    updates = sum(s["n"][0] for s in specs) * T
+    updates = sum(s["n"][0] * st for s, st in zip(specs, steps))
     stream = torch.cuda.current_stream()
     threads, ctas = args.threads, args.ctas_per_sm
     if threads == 0:
         from paper_1702_00496_gb300 import autotune
-        threads, ctas = autotune.tune_ensemble(specs, T, device=f"cuda:{local}", use_cache=not args.retune)
-    ens = Ensemble(specs, T, threads=threads, ctas_per_sm=ctas, device=f"cuda:{local}", stream=stream)
+        threads, ctas = autotune.tune_ensemble(specs, steps, device=f"cuda:{local}", use_cache=not args.retune)
+    ens = Ensemble(specs, steps, threads=threads, ctas_per_sm=ctas, device=f"cuda:{local}", stream=stream,
+                   groups=groups_in, twins=twins)
     for _ in range(args.warmup):
         ens.run()
     torch.cuda.synchronize()
@@ -236,7 +257,7 @@ def run_ensemble(args, rank: int, world: int, local: int):
     ms = max_over_ranks(ms, world, f"cuda:{local}")
     # the same realizations one problem at a time: reset, T steps, statistics, in sequence
     one = None
-    if not args.skip_one_at_a_time:
+    if not args.skip_one_at_a_time and T is not None:
         solvers = [Solver(s, device=f"cuda:{local}", stream=stream) for s in specs]
         for sv in solvers:  # builds each solver's captured step graph outside the timed region
             sv.step(50)
@@ -256,11 +277,12 @@ def run_ensemble(args, rank: int, world: int, local: int):
         line = {"metric": METRIC + " -- batched ensemble", "value": world * updates / (ms / 1e3), "unit": "updates/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": "ensemble", "members": len(specs), "time_steps": T,
-                           "total_points": sum(s["n"][0] for s in specs),
+                "config": {"workload": args.workload, "members": len(specs),
+                           "time_steps": T if T is not None else [min(steps), max(steps)],
+                           "total_points": sum(s["n"][0] for s in specs), "point_updates": updates,
                            "launch": {"threads": threads, "ctas_per_sm": ctas}},
                 "one_at_a_time_ms": one, "speedup_vs_one_at_a_time": (one / ms) if one else None,
-                "groups": groups, "clocks": clocks, "gpu_launches": args.steps * 3}
+                "groups": groups, "clocks": clocks, "gpu_launches": args.steps * 4}
         print(json.dumps(line), flush=True)
 
 
@@ -349,7 +371,7 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    if args.workload == "ensemble":
+    if args.workload == "ensemble" or args.workload in SWEEPS:
         return run_ensemble(args, rank, world, local)
     if args.workload == "adjoint_256":
         return run_adjoint(args, rank, world, local)

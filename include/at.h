@@ -213,30 +213,59 @@ int at_adjoint_backward(at_handle_t *hd, const double *lambda_dev, double *grad_
 
 /* ------------------------------------------------------------------ batched ensemble */
 /* The error of an AT scheme is a statistical quantity (Sec. 4: ensemble average over delay realizations,
- * Eq. "aveE_split"; Sec. 5.1: averages over runs with random phases).  An ensemble runs `count` independent
- * 1D problems -- each with its own n[0] and PE width (multiples of 4), L, seed, initial condition and dt -- for
- * `nsteps` steps each, inside one persistent kernel captured in a CUDA graph: CTAs take realizations from a
- * work counter in longest-first order, so uneven grid sizes balance over the SMs.
+ * Eq. "aveE_split"; Sec. 5.1: averages over runs with random phases; Sec. 5.2, Figs. "at-ord2-procs" and
+ * "at-kmom": error against P, N and the delay moments, and the asynchronous part E - E_s against a synchronous
+ * but otherwise identical run).  An ensemble runs `count` independent 1D problems -- each with its own n[0] and
+ * PE width (multiples of 4), order, time integrator, L, delay probabilities, seed, initial condition, dt and step
+ * count -- inside one persistent kernel captured in a CUDA graph: CTAs take realizations from a work counter in
+ * longest-first order (cost n[0] x steps), so uneven runs balance over the SMs.
  *
- * at_ensemble_sizes: doubles of ring and bytes of delay log the members need (members stored one after
- * another, member r's ring holding its own R_r slots).
- * at_ensemble_create: members are copied; ring_dev (ring_len doubles) and the optional log_dev (log_len bytes,
- * NULL for no log) are borrowed.  threads per CTA is 128, 256, 512 or 1024 (0: 1024); ctas_per_sm <= 0
- * takes the occupancy limit.  Errors: AT_ERR_ARG (non-1D member, n[0] % 4 != 0, sizes), AT_ERR_CUDA.
+ * at_member_t describes how member r runs:
+ *   nsteps : steps it runs (0..2^32-1); its statistics are taken at t = nsteps * dt.
+ *   group  : label of its summary group (>= 0), or -1 for "its grid size n[0]"; the summary averages over the
+ *            members that share a key (the label, or n[0]).
+ *   twin   : index of another member with the same n[0] whose final field this member's final field is compared
+ *            with (RMS and mean absolute value over the points of U - U_twin; e.g. its synchronous twin, so the
+ *            asynchronous part of the error is measured on the same initial condition), or -1.
+ *
+ * at_ensemble_sizes: validates the members and runs and gives the doubles of ring and bytes of delay log they
+ *   need (members stored one after another; member r's ring holds its own at_ring_slots slots, its log
+ *   nsteps_r x sides_r bytes).
+ * at_ensemble_create: members and runs are copied; ring_dev (ring_len doubles, 16-byte aligned) and the optional
+ *   log_dev (log_len bytes, NULL for no log) are borrowed.  threads per CTA is 128, 256, 512 or 1024 (0: 1024);
+ *   ctas_per_sm <= 0 takes the occupancy limit.  Every member starts from Eq. "IC" (with the analytic
+ *   pre-history for Adams-Bashforth).  Errors: AT_ERR_ARG (non-1D member, n[0] or the PE width not a multiple
+ *   of 4, bad nsteps, group or twin, sizes), AT_ERR_CUDA.
  * at_ensemble_run: one graph launch on the ensemble's stream (asynchronous).
- * at_ensemble_stats: blocks; per_member[r] (up to cap entries) receives member r's error statistics at its
- * final step (the at_error_stats fields); for each distinct grid size g < *ngroups (ascending, up to cap):
- * group_n[g], the ensemble mean group_mean[g] and unbiased variance group_var[g] of the members' RMS
- * errors, and the member count group_count[g].  Any output pointer may be NULL.
- * Errors: AT_ERR_CUDA, AT_ERR_NONFINITE. */
+ * at_ensemble_stats: blocks; per_member[r] (up to cap entries) receives member r's error statistics at its final
+ *   step (the at_error_stats fields) and per_member_diff[2r], [2r+1] the RMS and the mean absolute value of
+ *   U - U_twin (0 without a twin); groups[g] (g < *ngroups, ascending keys, up to gcap entries) the group's key,
+ *   member count, the ensemble mean and unbiased variance of the members' RMS errors, the mean of their mean
+ *   absolute errors and, over its members with a twin, mean and variance of both twin differences.
+ *   Any output pointer but ngroups may be NULL.  Errors: AT_ERR_CUDA, AT_ERR_NONFINITE. */
 typedef struct at_ensemble at_ensemble_t;
-int at_ensemble_sizes(const at_config_t *members, int32_t count, int64_t nsteps, int64_t *ring_len, int64_t *log_len);
-int at_ensemble_create(const at_config_t *members, int32_t count, int64_t nsteps, double *ring_dev, int64_t ring_len,
-                       uint8_t *log_dev, int64_t log_len, int32_t threads, int32_t ctas_per_sm, void *stream,
-                       at_ensemble_t **out);
+typedef struct {
+  int64_t nsteps;
+  int32_t group;
+  int32_t twin;
+} at_member_t;
+typedef struct {
+  int64_t key;                 /* group label, or the grid size n[0] */
+  int32_t count;               /* members in the group */
+  int32_t ntwin;               /* members of the group that have a twin */
+  double rms_mean, rms_var;    /* mean and unbiased variance of the members' RMS errors */
+  double abs_mean;             /* mean of the members' mean absolute errors */
+  double diff_mean, diff_var;  /* mean and unbiased variance of the RMS of U - U_twin over the members with a twin */
+  double dabs_mean, dabs_var;  /* the same for the mean absolute value of U - U_twin */
+} at_group_stats_t;
+int at_ensemble_sizes(const at_config_t *members, const at_member_t *runs, int32_t count, int64_t *ring_len,
+                      int64_t *log_len);
+int at_ensemble_create(const at_config_t *members, const at_member_t *runs, int32_t count, double *ring_dev,
+                       int64_t ring_len, uint8_t *log_dev, int64_t log_len, int32_t threads, int32_t ctas_per_sm,
+                       void *stream, at_ensemble_t **out);
 int at_ensemble_run(at_ensemble_t *ens);
-int at_ensemble_stats(at_ensemble_t *ens, at_stats_t *per_member, int32_t cap, int32_t *ngroups, int64_t *group_n,
-                      double *group_mean, double *group_var, int32_t *group_count);
+int at_ensemble_stats(at_ensemble_t *ens, at_stats_t *per_member, double *per_member_diff, int32_t cap,
+                      at_group_stats_t *groups, int32_t gcap, int32_t *ngroups);
 int at_ensemble_destroy(at_ensemble_t *ens);
 
 /* One-line description of the last error on this thread ("" if none). */

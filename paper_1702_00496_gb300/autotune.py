@@ -76,21 +76,28 @@ def tune_forward(solver, spec: dict, sample_steps: int = 50, use_cache: bool = T
     return t, b
 
 
-def ensemble_signature(specs, nsteps: int) -> str:
+def ensemble_signature(specs, nsteps) -> str:
+    steps = [int(nsteps)] * len(specs) if not hasattr(nsteps, "__len__") else [int(v) for v in nsteps]
     sizes = sorted(s["n"][0] for s in specs)
-    return f"{_device_key()}|ens|count{len(specs)}|n{sizes[0]}-{sizes[-1]}|sum{sum(sizes)}|steps{nsteps}"
+    work = sum(s["n"][0] * st for s, st in zip(specs, steps))
+    return (f"{_device_key()}|ens|count{len(specs)}|n{sizes[0]}-{sizes[-1]}|sum{sum(sizes)}|steps{max(steps)}"
+            f"|work{work}|o{max(s['order'] for s in specs)}|t{max(int(s.get('tsteps', 1)) for s in specs)}")
 
 
-def tune_ensemble(specs, nsteps: int, sample_steps: int = 200, device="cuda", use_cache: bool = True):
-    """Pick (threads, ctas_per_sm) for an ensemble by timing candidates on a temporal sample."""
+def tune_ensemble(specs, nsteps, sample_steps: int = 200, device="cuda", use_cache: bool = True):
+    """Pick (threads, ctas_per_sm) for an ensemble by timing candidates on a temporal sample: every member runs
+    the same fraction of its steps (at most sample_steps for the longest), so the load balance is preserved."""
     from .solver import Ensemble
     key = ensemble_signature(specs, nsteps)
     if use_cache and key in _load_cache():
         return tuple(_load_cache()[key]["best"])
+    steps = [int(nsteps)] * len(specs) if not hasattr(nsteps, "__len__") else [int(v) for v in nsteps]
+    frac = min(1.0, sample_steps / max(1, max(steps)))
+    sample = [max(1, int(round(st * frac))) if st > 0 else 0 for st in steps]
     stream = torch.cuda.current_stream()
     times = {}
     for t, c in ENSEMBLE_CANDIDATES:
-        ens = Ensemble(specs, min(sample_steps, nsteps), threads=t, ctas_per_sm=c, device=device, stream=stream)
+        ens = Ensemble(specs, sample, threads=t, ctas_per_sm=c, device=device, stream=stream)
         ens.run()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)

@@ -49,6 +49,16 @@ class at_config_t(C.Structure):
                 ("phase", C.POINTER(C.c_double)), ("kappa", C.POINTER(C.c_int32)), ("tsteps", C.c_int32)]
 
 
+class at_member_t(C.Structure):
+    _fields_ = [("nsteps", C.c_int64), ("group", C.c_int32), ("twin", C.c_int32)]
+
+
+class at_group_stats_t(C.Structure):
+    _fields_ = [("key", C.c_int64), ("count", C.c_int32), ("ntwin", C.c_int32), ("rms_mean", C.c_double),
+                ("rms_var", C.c_double), ("abs_mean", C.c_double), ("diff_mean", C.c_double),
+                ("diff_var", C.c_double), ("dabs_mean", C.c_double), ("dabs_var", C.c_double)]
+
+
 class at_stats_t(C.Structure):
     _fields_ = [("rms", C.c_double), ("max_abs", C.c_double), ("mean_abs", C.c_double), ("mean", C.c_double),
                 ("rms_I", C.c_double), ("rms_B", C.c_double), ("ua_rms", C.c_double),
@@ -96,10 +106,12 @@ def load(build_if_missing: bool = True):
     L.at_adjoint_workspace.argtypes = [vp, i64, i64, C.POINTER(i64)]
     L.at_adjoint_forward.argtypes = [vp, i64, i64, vp, i64]
     L.at_adjoint_backward.argtypes = [vp, vp, vp, C.POINTER(C.c_double)]
-    L.at_ensemble_sizes.argtypes = [C.POINTER(at_config_t), i32, i64, C.POINTER(i64), C.POINTER(i64)]
-    L.at_ensemble_create.argtypes = [C.POINTER(at_config_t), i32, i64, vp, i64, vp, i64, i32, i32, vp, C.POINTER(vp)]
+    L.at_ensemble_sizes.argtypes = [C.POINTER(at_config_t), C.POINTER(at_member_t), i32, C.POINTER(i64),
+                                    C.POINTER(i64)]
+    L.at_ensemble_create.argtypes = [C.POINTER(at_config_t), C.POINTER(at_member_t), i32, vp, i64, vp, i64, i32,
+                                     i32, vp, C.POINTER(vp)]
     L.at_ensemble_run.argtypes = [vp]
-    L.at_ensemble_stats.argtypes = [vp, C.POINTER(at_stats_t), i32, C.POINTER(i32), C.POINTER(i64), dp, dp,
+    L.at_ensemble_stats.argtypes = [vp, C.POINTER(at_stats_t), dp, i32, C.POINTER(at_group_stats_t), i32,
                                     C.POINTER(i32)]
     L.at_ensemble_destroy.argtypes = [vp]
     _lib = L
@@ -253,18 +265,35 @@ def _config_array(cfgs):
     return arr
 
 
-def at_ensemble_sizes(cfgs, nsteps: int):
+def _runs_array(count: int, nsteps, groups=None, twins=None):
+    """at_member_t[count] from a step count (int: every member, or one per member), optional group labels and
+    optional twin indices (-1: none)."""
+    steps = [int(nsteps)] * count if not hasattr(nsteps, "__len__") else [int(v) for v in nsteps]
+    if len(steps) != count:
+        raise ValueError("one step count per member")
+    arr = (at_member_t * count)()
+    for r in range(count):
+        arr[r].nsteps = steps[r]
+        arr[r].group = -1 if groups is None else int(groups[r])
+        arr[r].twin = -1 if twins is None else int(twins[r])
+    return arr
+
+
+def at_ensemble_sizes(cfgs, nsteps, groups=None, twins=None):
     """(ring doubles, log bytes) the members need."""
     arr = _config_array(cfgs)
+    runs = _runs_array(len(cfgs), nsteps, groups, twins)
     ring, log = C.c_int64(), C.c_int64()
-    _check(load().at_ensemble_sizes(arr, len(cfgs), int(nsteps), C.byref(ring), C.byref(log)), "at_ensemble_sizes")
+    _check(load().at_ensemble_sizes(arr, runs, len(cfgs), C.byref(ring), C.byref(log)), "at_ensemble_sizes")
     return ring.value, log.value
 
 
-def at_ensemble_create(cfgs, nsteps, ring, log=None, threads=0, ctas_per_sm=0, stream=None):
+def at_ensemble_create(cfgs, nsteps, ring, log=None, threads=0, ctas_per_sm=0, stream=None, groups=None,
+                       twins=None):
     arr = _config_array(cfgs)
+    runs = _runs_array(len(cfgs), nsteps, groups, twins)
     h = C.c_void_p()
-    _check(load().at_ensemble_create(arr, len(cfgs), int(nsteps), C.c_void_p(ring.data_ptr()), ring.numel(),
+    _check(load().at_ensemble_create(arr, runs, len(cfgs), C.c_void_p(ring.data_ptr()), ring.numel(),
                                      C.c_void_p(log.data_ptr()) if log is not None else None,
                                      log.numel() if log is not None else 0, int(threads), int(ctas_per_sm),
                                      _stream_ptr(stream), C.byref(h)), "at_ensemble_create")
@@ -276,17 +305,25 @@ def at_ensemble_run(h) -> None:
 
 
 def at_ensemble_stats(h, count: int):
-    """Returns (per-member stats dicts, groups: list of dicts with n, mean, var, count)."""
+    """Returns (per-member stats dicts with the twin differences under "diff" (RMS) and "dabs" (mean absolute),
+    groups: list of dicts with key, count, mean, var (of the RMS errors), abs_mean (of the mean absolute errors),
+    ntwin, diff_mean, diff_var, dabs_mean, dabs_var)."""
     per = (at_stats_t * count)()
+    diff = (C.c_double * (2 * count))()
     cap = max(count, 64)
+    grp = (at_group_stats_t * cap)()
     ng = C.c_int32()
-    gn = (C.c_int64 * cap)()
-    gm = (C.c_double * cap)()
-    gv = (C.c_double * cap)()
-    gc = (C.c_int32 * cap)()
-    _check(load().at_ensemble_stats(h, per, count, C.byref(ng), gn, gm, gv, gc), "at_ensemble_stats")
-    groups = [{"n": gn[g], "mean": gm[g], "var": gv[g], "count": gc[g]} for g in range(ng.value)]
-    return [per[r].as_dict() for r in range(count)], groups
+    _check(load().at_ensemble_stats(h, per, diff, count, grp, cap, C.byref(ng)), "at_ensemble_stats")
+    groups = [{"key": grp[g].key, "count": grp[g].count, "mean": grp[g].rms_mean, "var": grp[g].rms_var,
+               "abs_mean": grp[g].abs_mean, "ntwin": grp[g].ntwin, "diff_mean": grp[g].diff_mean,
+               "diff_var": grp[g].diff_var, "dabs_mean": grp[g].dabs_mean, "dabs_var": grp[g].dabs_var}
+              for g in range(ng.value)]
+    members = []
+    for r in range(count):
+        d = per[r].as_dict()
+        d["diff"], d["dabs"] = diff[2 * r], diff[2 * r + 1]
+        members.append(d)
+    return members, groups
 
 
 def at_ensemble_destroy(h) -> None:

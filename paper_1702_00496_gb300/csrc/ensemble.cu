@@ -36,7 +36,9 @@ struct MemberParams {
   double phase[AT_MAX_MODES];
   double kappa[AT_MAX_MODES];
   double dx, shift_final;          // grid spacing, c * t_final
-  int32_t nmodes, group;
+  int64_t steps;                   // steps this member runs
+  int32_t nmodes, group;           // group: index of the member's summary group
+  int32_t twin;                    // member whose final field this one is compared with, or -1
 };
 
 constexpr int kStatFields = AT_STAT_FIELDS;
@@ -96,7 +98,7 @@ __device__ void run_member(const StepParams &p, uint8_t *keff_sh, int64_t nsteps
 // the smallest variant that covers every member, so the common case keeps the register budget of H <= 2 Euler.
 template <int HMAX, bool AB>
 __global__ void __launch_bounds__(1024, 1) ensemble_kernel(const MemberParams *__restrict__ members,
-                                                       const int32_t *__restrict__ order, int32_t count, int64_t nsteps,
+                                                       const int32_t *__restrict__ order, int32_t count,
                                                        int32_t *counter, double *__restrict__ member_stats) {
   __shared__ MemberParams m;
   __shared__ int32_t item;
@@ -121,16 +123,16 @@ __global__ void __launch_bounds__(1024, 1) ensemble_kernel(const MemberParams *_
       if (m.p.h == 1) member_prehistory<1>(m);
       else if (HMAX == 2 || m.p.h == 2) member_prehistory<2>(m);
       else member_prehistory<HMAX>(m);
-      if (m.p.h == 1) run_member<1, AB>(m.p, keff_sh, nsteps);
-      else if (HMAX == 2 || m.p.h == 2) run_member<2, AB>(m.p, keff_sh, nsteps);
-      else run_member<HMAX, AB>(m.p, keff_sh, nsteps);
+      if (m.p.h == 1) run_member<1, AB>(m.p, keff_sh, m.steps);
+      else if (HMAX == 2 || m.p.h == 2) run_member<2, AB>(m.p, keff_sh, m.steps);
+      else run_member<HMAX, AB>(m.p, keff_sh, m.steps);
     } else {
-      if (m.p.h == 1) run_member<1, false>(m.p, keff_sh, nsteps);
-      else if (HMAX == 2 || m.p.h == 2) run_member<2, false>(m.p, keff_sh, nsteps);
-      else run_member<HMAX, false>(m.p, keff_sh, nsteps);
+      if (m.p.h == 1) run_member<1, false>(m.p, keff_sh, m.steps);
+      else if (HMAX == 2 || m.p.h == 2) run_member<2, false>(m.p, keff_sh, m.steps);
+      else run_member<HMAX, false>(m.p, keff_sh, m.steps);
     }
-    // statistics of E = U^nsteps - u_a(x, nsteps dt), as in the single-problem reduction
-    const double *u = m.p.ring + (nsteps % m.p.R) * m.p.ntot;
+    // statistics of E = U^steps - u_a(x, steps dt), as in the single-problem reduction
+    const double *u = m.p.ring + (m.steps % m.p.R) * m.p.ntot;
     double acc[kStatFields];
 #pragma unroll
     for (int f = 0; f < kStatFields; ++f) acc[f] = 0.0;
@@ -176,26 +178,91 @@ __global__ void __launch_bounds__(1024, 1) ensemble_kernel(const MemberParams *_
   }
 }
 
-// Per grid size g: mean and unbiased variance of the members' RMS errors, summed in member order.
-__global__ void summary_kernel(const double *__restrict__ member_stats, const MemberParams *__restrict__ members,
-                               int32_t count, int32_t ngroups, double *__restrict__ out /* [ngroups][3] */) {
+// The member's final field against its twin's: RMS and mean absolute value over the points of U - U_twin (0
+// without a twin), into diff[2r], diff[2r+1]; one block per member, the block's partial sums combined in a fixed
+// order (deterministic).
+__global__ void __launch_bounds__(256) twin_diff_kernel(const MemberParams *__restrict__ members,
+                                                        double *__restrict__ diff) {
+  __shared__ double red[2][8];
+  const MemberParams &a = members[blockIdx.x];
+  if (a.twin < 0) {
+    if (threadIdx.x < 2) diff[2 * (int64_t)blockIdx.x + threadIdx.x] = 0.0;
+    return;
+  }
+  const MemberParams &b = members[a.twin];
+  const double *ua = a.p.ring + (a.steps % a.p.R) * a.p.ntot;
+  const double *ub = b.p.ring + (b.steps % b.p.R) * b.p.ntot;
+  double s2 = 0.0, s1 = 0.0;
+  for (int64_t i = threadIdx.x; i < a.p.ntot; i += blockDim.x) {
+    const double d = ua[i] - ub[i];
+    s2 = fma(d, d, s2);
+    s1 += fabs(d);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    s1 += __shfl_down_sync(0xffffffffu, s1, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = s2;
+    red[1][threadIdx.x >> 5] = s1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t2 = 0.0, t1 = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      t2 += red[0][w];
+      t1 += red[1][w];
+    }
+    diff[2 * (int64_t)blockIdx.x] = sqrt(t2 / (double)a.p.ntot);
+    diff[2 * (int64_t)blockIdx.x + 1] = t1 / (double)a.p.ntot;
+  }
+}
+
+constexpr int kGroupFields = 9;
+
+// Per summary group g, summed in member order: mean and unbiased variance of the members' RMS errors, the mean of
+// their mean absolute errors, and -- over the members that have a twin -- mean and unbiased variance of the RMS
+// and of the mean absolute value of U - U_twin.  out[g] = {rms mean, rms var, count, diff-RMS mean, diff-RMS var,
+// members with a twin, diff-abs mean, diff-abs var, mean-abs-error mean}.
+__global__ void summary_kernel(const double *__restrict__ member_stats, const double *__restrict__ member_diff,
+                               const MemberParams *__restrict__ members, int32_t count, int32_t ngroups,
+                               double *__restrict__ out /* [ngroups][kGroupFields] */) {
   for (int g = threadIdx.x; g < ngroups; g += blockDim.x) {
-    double s = 0.0, c = 0.0;
+    double s = 0.0, sa = 0.0, c = 0.0, sd = 0.0, sda = 0.0, cd = 0.0;
     for (int r = 0; r < count; ++r)
       if (members[r].group == g) {
-        s += sqrt(member_stats[(int64_t)r * kStatFields] / (double)members[r].p.ntot);
+        const double N = (double)members[r].p.ntot;
+        s += sqrt(member_stats[(int64_t)r * kStatFields] / N);
+        sa += member_stats[(int64_t)r * kStatFields + 2] / N;
         c += 1.0;
+        if (members[r].twin >= 0) {
+          sd += member_diff[2 * (int64_t)r];
+          sda += member_diff[2 * (int64_t)r + 1];
+          cd += 1.0;
+        }
       }
-    const double mean = c > 0 ? s / c : 0.0;
-    double v = 0.0;
+    const double mean = c > 0 ? s / c : 0.0, dmean = cd > 0 ? sd / cd : 0.0, damean = cd > 0 ? sda / cd : 0.0;
+    double v = 0.0, vd = 0.0, vda = 0.0;
     for (int r = 0; r < count; ++r)
       if (members[r].group == g) {
         const double d = sqrt(member_stats[(int64_t)r * kStatFields] / (double)members[r].p.ntot) - mean;
         v += d * d;
+        if (members[r].twin >= 0) {
+          const double e = member_diff[2 * (int64_t)r] - dmean, f = member_diff[2 * (int64_t)r + 1] - damean;
+          vd += e * e;
+          vda += f * f;
+        }
       }
-    out[3 * g] = mean;
-    out[3 * g + 1] = c > 1 ? v / (c - 1.0) : 0.0;
-    out[3 * g + 2] = c;
+    double *o = out + kGroupFields * (int64_t)g;
+    o[0] = mean;
+    o[1] = c > 1 ? v / (c - 1.0) : 0.0;
+    o[2] = c;
+    o[3] = dmean;
+    o[4] = cd > 1 ? vd / (cd - 1.0) : 0.0;
+    o[5] = cd;
+    o[6] = damean;
+    o[7] = cd > 1 ? vda / (cd - 1.0) : 0.0;
+    o[8] = c > 0 ? sa / c : 0.0;
   }
 }
 
@@ -219,26 +286,26 @@ const double kTwoPi = 6.283185307179586476925286766559005768;
 
 struct at_ensemble {
   int32_t count = 0, ngroups = 0;
-  int64_t nsteps = 0;
   cudaStream_t stream = nullptr;
   void *scratch = nullptr;
   MemberParams *d_members = nullptr;
   int32_t *d_order = nullptr;
   int32_t *d_counter = nullptr;
   double *d_member_stats = nullptr;
+  double *d_member_diff = nullptr;
   double *d_summary = nullptr;
-  std::vector<int64_t> group_n;
-  std::vector<int64_t> member_n;
+  std::vector<int64_t> group_key;
+  std::vector<int64_t> member_n, member_steps;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int threads = 256, blocks = 0;
   size_t dyn_smem = 0;
 };
 
-// Ring and log sizes (in doubles and bytes) the members need, laid out member after member.
-extern "C" int at_ensemble_sizes(const at_config_t *members, int32_t count, int64_t nsteps, int64_t *ring_len,
-                                 int64_t *log_len) {
-  if (!members || count < 1 || nsteps < 0 || !ring_len || !log_len) return fail(AT_ERR_ARG, "at_ensemble_sizes: bad argument");
+// Ring and log sizes (in doubles and bytes) the members need, laid out member after member; validates the runs.
+extern "C" int at_ensemble_sizes(const at_config_t *members, const at_member_t *runs, int32_t count,
+                                 int64_t *ring_len, int64_t *log_len) {
+  if (!members || !runs || count < 1 || !ring_len || !log_len) return fail(AT_ERR_ARG, "at_ensemble_sizes: bad argument");
   int64_t ring = 0, log = 0;
   for (int r = 0; r < count; ++r) {
     int32_t R;
@@ -248,30 +315,35 @@ extern "C" int at_ensemble_sizes(const at_config_t *members, int32_t count, int6
     if ((rc = at_num_sides(members + r, &nb))) return rc;
     if (members[r].dim != 1 || members[r].n[0] % 4 || (members[r].pe[0] > 1 && (members[r].n[0] / members[r].pe[0]) % 4))
       return fail(AT_ERR_ARG, "ensemble members must be 1D with N and the PE width multiples of 4");
+    const at_member_t &u = runs[r];
+    if (u.nsteps < 0 || u.nsteps > 0xFFFFFFFFll) return fail(AT_ERR_ARG, "ensemble: nsteps must be in 0..2^32-1");
+    if (u.group < -1) return fail(AT_ERR_ARG, "ensemble: group must be >= -1");
+    if (u.twin < -1 || u.twin >= count || u.twin == r || (u.twin >= 0 && members[u.twin].n[0] != members[r].n[0]))
+      return fail(AT_ERR_ARG, "ensemble: twin must be -1 or another member with the same n[0]");
     ring += (int64_t)R * members[r].n[0];
-    log += nsteps * nb;
+    log += u.nsteps * nb;
   }
   *ring_len = ring;
   *log_len = log;
   return AT_OK;
 }
 
-extern "C" int at_ensemble_create(const at_config_t *members, int32_t count, int64_t nsteps, double *ring_dev,
-                                  int64_t ring_len, uint8_t *log_dev, int64_t log_len, int32_t threads,
-                                  int32_t ctas_per_sm, void *stream, at_ensemble_t **out) {
+extern "C" int at_ensemble_create(const at_config_t *members, const at_member_t *runs, int32_t count,
+                                  double *ring_dev, int64_t ring_len, uint8_t *log_dev, int64_t log_len,
+                                  int32_t threads, int32_t ctas_per_sm, void *stream, at_ensemble_t **out) {
   int64_t need_ring, need_log;
-  int rc = at_ensemble_sizes(members, count, nsteps, &need_ring, &need_log);
+  int rc = at_ensemble_sizes(members, runs, count, &need_ring, &need_log);
   if (rc) return rc;
   if (!out || !ring_dev || ring_len < need_ring) return fail(AT_ERR_ARG, "at_ensemble_create: ring too small");
   if (log_dev && log_len < need_log) return fail(AT_ERR_ARG, "at_ensemble_create: log too small");
-  if (nsteps > 0xFFFFFFFFll) return fail(AT_ERR_ARG, "at_ensemble_create: step counter exceeds 32 bits");
   if (threads == 0) threads = 1024;
   if (threads != 128 && threads != 256 && threads != 512 && threads != 1024)
     return fail(AT_ERR_ARG, "threads must be 128, 256, 512 or 1024");
 
   std::vector<MemberParams> host(count);
   std::map<int64_t, int> groups;
-  for (int r = 0; r < count; ++r) groups[members[r].n[0]] = 0;
+  auto key_of = [&](int r) { return runs[r].group >= 0 ? (int64_t)runs[r].group : members[r].n[0]; };
+  for (int r = 0; r < count; ++r) groups[key_of(r)] = 0;
   int gi = 0;
   for (auto &kv : groups) kv.second = gi++;
   at_ensemble *e = new (std::nothrow) at_ensemble();
@@ -286,6 +358,7 @@ extern "C" int at_ensemble_create(const at_config_t *members, int32_t count, int
     at_num_sides(&c, &nb);
     MemberParams &m = host[r];
     std::memset(&m, 0, sizeof(m));
+    const int64_t nsteps = runs[r].nsteps;
     rc = at_prepare_params(&c, ring_dev + ring_off, log_dev ? log_dev + log_off : nullptr, nsteps, &m.p);
     max_nb = std::max<int64_t>(max_nb, nb);
     if (rc) { delete e; return rc; }
@@ -302,36 +375,42 @@ extern "C" int at_ensemble_create(const at_config_t *members, int32_t count, int
         m.amp_pre[mm - 1][q] = c.amp[q] * std::exp(c.alpha * m.kappa[q] * m.kappa[q] * (double)mm * c.dt);
     }
     for (int mm = 1; mm <= 2; ++mm) m.shift_pre[mm - 1] = -c.c[0] * (double)mm * c.dt;
-    m.group = groups[c.n[0]];
+    m.group = groups[key_of(r)];
+    m.steps = nsteps;
+    m.twin = runs[r].twin;
     e->member_n.push_back(c.n[0]);
+    e->member_steps.push_back(nsteps);
     ring_off += (int64_t)R * c.n[0];
     log_off += nsteps * nb;
   }
-  for (auto &kv : groups) e->group_n.push_back(kv.first);
+  for (auto &kv : groups) e->group_key.push_back(kv.first);
   e->count = count;
   e->ngroups = (int32_t)groups.size();
-  e->nsteps = nsteps;
   e->stream = (cudaStream_t)stream;
   e->threads = threads;
-  // longest first (cost ~ N * steps, equal steps): largest grids start first
+  // longest first (cost ~ N * steps): the largest runs start first
   std::vector<int32_t> order(count);
   std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return members[a].n[0] > members[b].n[0]; });
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return (double)members[a].n[0] * (double)runs[a].nsteps > (double)members[b].n[0] * (double)runs[b].nsteps;
+  });
 
   const size_t b_members = sizeof(MemberParams) * (size_t)count;
   const size_t b_order = sizeof(int32_t) * (size_t)count;
   const size_t b_stats = sizeof(double) * (size_t)count * kStatFields;
-  const size_t b_sum = sizeof(double) * 3 * (size_t)e->ngroups;
+  const size_t b_diff = sizeof(double) * 2 * (size_t)count;
+  const size_t b_sum = sizeof(double) * kGroupFields * (size_t)e->ngroups;
   const size_t b_first = sizeof(int64_t) * (size_t)count;
   auto up = [](size_t b) { return (b + 255) / 256 * 256; };
   cudaError_t err =
-      cudaMalloc(&e->scratch, up(b_members) + up(b_order) + 256 + up(b_stats) + up(b_sum) + up(b_first));
+      cudaMalloc(&e->scratch, up(b_members) + up(b_order) + 256 + up(b_stats) + up(b_diff) + up(b_sum) + up(b_first));
   if (err != cudaSuccess) { delete e; return cuda_fail(err, "at_ensemble_create: cudaMalloc"); }
   char *base = (char *)e->scratch;
   e->d_members = (MemberParams *)base; base += up(b_members);
   e->d_order = (int32_t *)base; base += up(b_order);
   e->d_counter = (int32_t *)base; base += 256;
   e->d_member_stats = (double *)base; base += up(b_stats);
+  e->d_member_diff = (double *)base; base += up(b_diff);
   e->d_summary = (double *)base; base += up(b_sum);
   // every member starts from Eq. "IC" with the analytic pre-history: ts-1 right-hand sides stored before step 0
   int64_t *d_first = (int64_t *)base;
@@ -378,9 +457,11 @@ extern "C" int at_ensemble_create(const at_config_t *members, int32_t count, int
   err = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   if (err == cudaSuccess) {
     reset_counter<<<1, 1, 0, cap>>>(e->d_counter);
-    kernel<<<e->blocks, threads, e->dyn_smem, cap>>>(e->d_members, e->d_order, count, nsteps, e->d_counter,
+    kernel<<<e->blocks, threads, e->dyn_smem, cap>>>(e->d_members, e->d_order, count, e->d_counter,
                                                     e->d_member_stats);
-    summary_kernel<<<1, 128, 0, cap>>>(e->d_member_stats, e->d_members, count, e->ngroups, e->d_summary);
+    twin_diff_kernel<<<count, 256, 0, cap>>>(e->d_members, e->d_member_diff);
+    summary_kernel<<<1, 128, 0, cap>>>(e->d_member_stats, e->d_member_diff, e->d_members, count, e->ngroups,
+                                       e->d_summary);
     err = cudaStreamEndCapture(cap, &e->graph);
   }
   if (err == cudaSuccess) err = cudaGraphInstantiate(&e->exec, e->graph, 0);
@@ -401,43 +482,59 @@ extern "C" int at_ensemble_run(at_ensemble_t *e) {
   return AT_OK;
 }
 
-extern "C" int at_ensemble_stats(at_ensemble_t *e, at_stats_t *per_member, int32_t cap, int32_t *ngroups,
-                                 int64_t *group_n, double *group_mean, double *group_var, int32_t *group_count) {
+extern "C" int at_ensemble_stats(at_ensemble_t *e, at_stats_t *per_member, double *per_member_diff, int32_t cap,
+                                 at_group_stats_t *groups, int32_t gcap, int32_t *ngroups) {
   if (!e || !ngroups) return fail(AT_ERR_ARG, "at_ensemble_stats: bad argument");
-  std::vector<double> ms((size_t)e->count * kStatFields), sum(3 * (size_t)e->ngroups);
+  std::vector<double> ms((size_t)e->count * kStatFields), md(2 * (size_t)e->count),
+      sum(kGroupFields * (size_t)e->ngroups);
   cudaError_t err;
   if ((err = cudaMemcpyAsync(ms.data(), e->d_member_stats, ms.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                             e->stream)) != cudaSuccess ||
+      (err = cudaMemcpyAsync(md.data(), e->d_member_diff, md.size() * sizeof(double), cudaMemcpyDeviceToHost,
                              e->stream)) != cudaSuccess ||
       (err = cudaMemcpyAsync(sum.data(), e->d_summary, sum.size() * sizeof(double), cudaMemcpyDeviceToHost,
                              e->stream)) != cudaSuccess ||
       (err = cudaStreamSynchronize(e->stream)) != cudaSuccess)
     return cuda_fail(err, "at_ensemble_stats");
   *ngroups = e->ngroups;
-  if (per_member) {
-    for (int r = 0; r < e->count && r < cap; ++r) {
-      const double *s = &ms[(size_t)r * kStatFields];
-      const double N = (double)e->member_n[r];
-      at_stats_t &o = per_member[r];
-      o.rms = std::sqrt(s[0] / N);
-      o.max_abs = s[1];
-      o.mean_abs = s[2] / N;
-      o.mean = s[3] / N;
-      o.rms_I = s[7] > 0 ? std::sqrt(s[4] / s[7]) : 0.0;
-      o.rms_B = s[8] > 0 ? std::sqrt(s[5] / s[8]) : 0.0;
-      o.ua_rms = std::sqrt(s[6] / N);
-      o.n_I = (int64_t)s[7];
-      o.n_B = (int64_t)s[8];
-      o.step = e->nsteps;
+  for (int r = 0; r < e->count && r < cap; ++r) {
+    if (per_member_diff) {
+      per_member_diff[2 * r] = md[2 * r];
+      per_member_diff[2 * r + 1] = md[2 * r + 1];
     }
+    if (!per_member) continue;
+    const double *s = &ms[(size_t)r * kStatFields];
+    const double N = (double)e->member_n[r];
+    at_stats_t &o = per_member[r];
+    o.rms = std::sqrt(s[0] / N);
+    o.max_abs = s[1];
+    o.mean_abs = s[2] / N;
+    o.mean = s[3] / N;
+    o.rms_I = s[7] > 0 ? std::sqrt(s[4] / s[7]) : 0.0;
+    o.rms_B = s[8] > 0 ? std::sqrt(s[5] / s[8]) : 0.0;
+    o.ua_rms = std::sqrt(s[6] / N);
+    o.n_I = (int64_t)s[7];
+    o.n_B = (int64_t)s[8];
+    o.step = e->member_steps[r];
   }
-  for (int g = 0; g < e->ngroups && g < cap; ++g) {
-    if (group_n) group_n[g] = e->group_n[g];
-    if (group_mean) group_mean[g] = sum[3 * g];
-    if (group_var) group_var[g] = sum[3 * g + 1];
-    if (group_count) group_count[g] = (int32_t)sum[3 * g + 2];
+  for (int g = 0; groups && g < e->ngroups && g < gcap; ++g) {
+    const double *o = &sum[kGroupFields * (size_t)g];
+    at_group_stats_t &G = groups[g];
+    G.key = e->group_key[g];
+    G.count = (int32_t)o[2];
+    G.ntwin = (int32_t)o[5];
+    G.rms_mean = o[0];
+    G.rms_var = o[1];
+    G.abs_mean = o[8];
+    G.diff_mean = o[3];
+    G.diff_var = o[4];
+    G.dabs_mean = o[6];
+    G.dabs_var = o[7];
   }
   for (double v : ms)
     if (!std::isfinite(v)) return fail(AT_ERR_NONFINITE, "at_ensemble_stats: non-finite statistic");
+  for (double v : md)
+    if (!std::isfinite(v)) return fail(AT_ERR_NONFINITE, "at_ensemble_stats: non-finite twin difference");
   return AT_OK;
 }
 

@@ -196,8 +196,9 @@ __device__ __forceinline__ void ab_load(const double *src, double a[NP]) {
 }
 
 // Adams-Bashforth combination of NP consecutive points starting at i (16-byte aligned for NP = 4): r holds
-// dt f^n and becomes U^{n+1} = U^n + sum_{m<l} beta_m dt f^{n-m} (l = levels stored so far, at most ts); dt f^n
-// takes the slot of the oldest right-hand side, which only this thread reads, after the read.
+// dt f^n and becomes U^{n+1} = U^n + sum_{m<l} beta_m dt f^{n-m} (l = levels stored so far, at most ts), formed
+// as a chain of l FMAs onto U^n; dt f^n takes the slot of the oldest right-hand side, which only this thread
+// reads, after the read.
 template <int NP>
 __device__ __forceinline__ void ab_combine(const StepParams &p, int64_t n, int64_t i, const double u[NP],
                                            double r[NP]) {
@@ -207,19 +208,9 @@ __device__ __forceinline__ void ab_combine(const StepParams &p, int64_t n, int64
   const bool two = p.ts == 3;  // two stored slots, else one
   double *f_now = p.frhs + (two ? (n & 1) : 0) * p.ntot + i;          // dt f^{n-2} (AB3) or dt f^{n-1} (AB2)
   const double *f_1 = p.frhs + (two ? ((n - 1) & 1) : 0) * p.ntot + i;  // dt f^{n-1}
-  double t[NP], a[NP];
-#pragma unroll
-  for (int q = 0; q < NP; ++q) t[q] = fma(beta[0], r[q], p.zero);
-  if (l > 1) {
-    ab_load<NP>(f_1, a);
-#pragma unroll
-    for (int q = 0; q < NP; ++q) t[q] = fma(beta[1], a[q], t[q]);
-  }
-  if (l > 2) {
-    ab_load<NP>(f_now, a);
-#pragma unroll
-    for (int q = 0; q < NP; ++q) t[q] = fma(beta[2], a[q], t[q]);
-  }
+  double a1[NP], a2[NP];
+  if (l > 1) ab_load<NP>(f_1, a1);
+  if (l > 2) ab_load<NP>(f_now, a2);
   if constexpr (NP == 1) {
     f_now[0] = r[0];
   } else {
@@ -227,7 +218,15 @@ __device__ __forceinline__ void ab_combine(const StepParams &p, int64_t n, int64
     for (int q = 0; q < NP; q += 2) *reinterpret_cast<double2 *>(f_now + q) = make_double2(r[q], r[q + 1]);
   }
 #pragma unroll
-  for (int q = 0; q < NP; ++q) r[q] = u[q] + t[q];
+  for (int q = 0; q < NP; ++q) r[q] = fma(beta[0], r[q], u[q]);
+  if (l > 1) {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) r[q] = fma(beta[1], a1[q], r[q]);
+  }
+  if (l > 2) {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) r[q] = fma(beta[2], a2[q], r[q]);
+  }
 }
 
 // Update the four points x0..x0+3 of row (y, z) (the forward step; AB: Adams-Bashforth, else forward Euler).

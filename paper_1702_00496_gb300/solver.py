@@ -87,27 +87,35 @@ class Solver:
 
 
 class Ensemble:
-    """Many independent 1D realizations advanced in one persistent, graph-captured launch."""
+    """Many independent 1D realizations advanced in one persistent, graph-captured launch.
 
-    def __init__(self, specs, nsteps: int, log: bool = False, threads: int = 0, ctas_per_sm: int = 0,
-                 device: str | torch.device = "cuda", stream=None):
+    nsteps: one step count for every member, or one per member.  groups: optional summary-group labels (default:
+    group by grid size).  twins: optional index per member of the member whose final field it is compared with
+    (-1: none), e.g. its synchronous twin.
+    """
+
+    def __init__(self, specs, nsteps, log: bool = False, threads: int = 0, ctas_per_sm: int = 0,
+                 device: str | torch.device = "cuda", stream=None, groups=None, twins=None):
         B.load()
         self.cfgs = [B.Config(s) for s in specs]
-        self.nsteps = int(nsteps)
+        count = len(self.cfgs)
+        self.steps = ([int(nsteps)] * count if not hasattr(nsteps, "__len__") else [int(v) for v in nsteps])
+        self.nsteps = max(self.steps)
         self.device = torch.device(device)
-        ring_len, log_len = B.at_ensemble_sizes(self.cfgs, self.nsteps)
+        ring_len, log_len = B.at_ensemble_sizes(self.cfgs, self.steps, groups, twins)
         self.ring = torch.empty(ring_len, dtype=torch.float64, device=self.device)
         self.log = torch.zeros(log_len, dtype=torch.uint8, device=self.device) if log else None
         self.R = [B.at_ring_slots(c) for c in self.cfgs]
         self.sides = [B.at_num_sides(c) for c in self.cfgs]
         self.ring_off, self.log_off = [], []
         ro = lo = 0
-        for c, R, nb in zip(self.cfgs, self.R, self.sides):
+        for c, R, nb, st in zip(self.cfgs, self.R, self.sides, self.steps):
             self.ring_off.append(ro)
             self.log_off.append(lo)
             ro += R * c.ntot
-            lo += self.nsteps * nb
-        self.h = B.at_ensemble_create(self.cfgs, self.nsteps, self.ring, self.log, threads, ctas_per_sm, stream)
+            lo += st * nb
+        self.h = B.at_ensemble_create(self.cfgs, self.steps, self.ring, self.log, threads, ctas_per_sm, stream,
+                                      groups, twins)
 
     def run(self) -> None:
         B.at_ensemble_run(self.h)
@@ -119,7 +127,7 @@ class Ensemble:
         """Member r's field at its final step (valid after run())."""
         c = self.cfgs[r]
         levels = self.R[r] - (c.tsteps - 1)  # slots after the L + T levels hold Adams-Bashforth right-hand sides
-        slot = self.nsteps % levels
+        slot = self.steps[r] % levels
         o = self.ring_off[r] + slot * c.ntot
         return self.ring[o:o + c.ntot]
 
@@ -127,7 +135,7 @@ class Ensemble:
         if self.log is None:
             raise RuntimeError("ensemble was created without a delay log")
         o = self.log_off[r]
-        return self.log[o:o + self.nsteps * self.sides[r]].view(self.nsteps, self.sides[r])
+        return self.log[o:o + self.steps[r] * self.sides[r]].view(self.steps[r], self.sides[r])
 
     def close(self) -> None:
         if self.h is not None:

@@ -187,3 +187,21 @@ def test_ensemble_members_must_be_1d_with_aligned_sizes():
         with pytest.raises(B.ATError) as e:
             at_ensemble_sizes([B.Config(ok), B.Config(spec)], 10)
         assert e.value.code == B.AT_ERR_ARG
+
+
+def test_ensemble_runs_are_validated_and_sized_per_member():
+    from paper_1702_00496_gb300.binding import at_ensemble_sizes
+    a, _ = W.wl_1d(1024, 16, 4, 3, 0, 1, (1, 2))                # R = 6, 32 sides
+    b, _ = W.wl_1d(512, 8, 6, 3, 0, 2, (1, 2), tsteps=3)        # R = 3 + 4 + 2, 16 sides
+    c, _ = W.wl_1d(1024, 16, 2, 3, 0, 3, (1, 2), scheme=W.SYNC)  # R = 3 + 1, 32 sides
+    cfgs = [B.Config(s) for s in (a, b, c)]
+    ring, log = at_ensemble_sizes(cfgs, [10, 20, 30], twins=[2, -1, 0])
+    assert ring == 6 * 1024 + 9 * 512 + 4 * 1024 and log == 10 * 32 + 20 * 16 + 30 * 32
+    bad = [dict(nsteps=[10, -1, 5]), dict(nsteps=[10, 1, 1], twins=[0, -1, -1]), dict(nsteps=5, twins=[1, -1, -1]),
+           dict(nsteps=5, twins=[3, -1, -1]), dict(nsteps=5, groups=[-2, 0, 0]), dict(nsteps=[1 << 32, 1, 1])]
+    for kw in bad:
+        with pytest.raises(B.ATError) as e:
+            at_ensemble_sizes(cfgs, kw.pop("nsteps"), **kw)
+        assert e.value.code == B.AT_ERR_ARG
+    with pytest.raises(ValueError):
+        at_ensemble_sizes(cfgs, [1, 2])

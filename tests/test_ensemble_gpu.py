@@ -51,7 +51,7 @@ def test_mixed_ensemble_matches_oracle(threads, ctas):
     per, groups = _check_members(ens, specs, nsteps, range(len(specs)))
     # per grid size: mean and unbiased variance of the RMS errors
     for g in groups:
-        rms = np.array([per[r]["rms"] for r in range(len(specs)) if specs[r]["n"][0] == g["n"]])
+        rms = np.array([per[r]["rms"] for r in range(len(specs)) if specs[r]["n"][0] == g["key"]])
         assert g["count"] == len(rms)
         assert g["mean"] == pytest.approx(rms.mean(), rel=1e-12)
         if len(rms) > 1:

@@ -96,16 +96,65 @@ def workload(name: str, scheme: int = AT):
 
 
 def paper_case(case: int, n: int, seed: int, p0_probs=(1.0, 0.0, 0.0), P: int = 16):
-    """Cases 4 and 5 of the paper's case table as used for Fig. "at-prob-all" (c), (d): kappa = {3,4,5},
-    A = {2, 0.5, 1.5}, P = 16, L = 3, phases random per seed.  Case 4: advection-diffusion, AB2, CD4 with
-    (1,4,2)/(2,4,2); Case 5: diffusion, AB3, CD6 with (2,6,2).  The figure does not give alpha, c or r_alpha:
-    alpha = 0.1, c = 1 (Case 4) or 0 (Case 5), r_alpha = 0.05 (Case 4) or 0.01 (Case 5): with the time-extrapolated
+    """Cases 1, 4 and 5 of the paper's case table: kappa = {3,4,5}, A = {2, 0.5, 1.5} (as in Fig. "at-prob-all"),
+    L = len(p0_probs), alpha = 0.1, phases random per seed.  Case 1: advection-diffusion, forward Euler, CD2 with
+    (1,2,2)b/(2,2,2)b, r_alpha = 0.1 (Fig. "at-ord2-procs").  Case 4: advection-diffusion, AB2, CD4 with
+    (1,4,2)/(2,4,2); Case 5: diffusion, AB3, CD6 with (2,6,2).  The paper does not give c or r_alpha for Cases 4
+    and 5: c = 1 (Case 4) or 0 (Case 5), r_alpha = 0.05 (Case 4) or 0.01 (Case 5): with the time-extrapolated
     halos, AB2 and AB3 stay stable at every delay mix only at these smaller steps (the oracle diverges at
     r_alpha = 0.1 / 0.02 when p_0 <= 0.3)."""
-    order, tsteps, c, r = (4, 2, 1.0, 0.05) if case == 4 else (6, 3, 0.0, 0.01)
-    spec, _ = wl_1d(n, P, order, 3, 0, seed, (3, 4, 5), c=c, alpha=0.1, r_alpha=r, probs=list(p0_probs), tsteps=tsteps)
+    order, tsteps, c, r = {1: (2, 1, 1.0, 0.1), 4: (4, 2, 1.0, 0.05), 5: (6, 3, 0.0, 0.01)}[case]
+    probs = list(p0_probs)
+    spec, _ = wl_1d(n, P, order, len(probs), 0, seed, (3, 4, 5), c=c, alpha=0.1, r_alpha=r,
+                    probs=probs if len(probs) > 1 else None, tsteps=tsteps)
     spec["amp"] = np.array([[2.0, 0.5, 1.5]])
     return spec
+
+
+def steps_to(spec, t_final: float) -> int:
+    return int(round(t_final / spec["dt"]))
+
+
+def _with_sync_twins(specs, steps, groups, sync_group):
+    """Append a synchronous twin (same seed, initial condition and step) after each member; returns the lists
+    with the twin index of every member (-1 for the twins themselves)."""
+    k = len(specs)
+    twins = [k + i for i in range(k)] + [-1] * k
+    sync = []
+    for sp in specs:
+        t = dict(sp)
+        t["scheme"] = SYNC
+        sync.append(t)
+    return specs + sync, steps + steps, groups + [sync_group(g) for g in groups], twins
+
+
+def moment_members(case: int, Ls, seeds, n: int = 512, P: int = 16, t_final: float = 0.1):
+    """Members of the delay-moment sweep of Fig. "at-kmom" (N = 512, P = 16): for each L, uniform delays p_k = 1/L
+    (Eq. "aveE_scaling_gen_L"), one member per seed, each with a synchronous twin.  Group of an asynchronous
+    member: L; of its twin: 100 + L.  Returns (specs, steps, groups, twins)."""
+    specs, steps, groups = [], [], []
+    for L in Ls:
+        for sd in seeds:
+            sp = paper_case(case, n, sd, [1.0 / L] * L, P)
+            specs.append(sp)
+            steps.append(steps_to(sp, t_final))
+            groups.append(L)
+    return _with_sync_twins(specs, steps, groups, lambda g: 100 + g)
+
+
+def scaling_members(case: int, grids, seeds, probs=(0.2, 0.5, 0.3), t_final: float = 0.1):
+    """Members of the strong/weak scaling sweep of Fig. "at-ord2-procs": one member per (N, P) in `grids` and seed,
+    with p_k = {0.2, 0.5, 0.3}, each with a synchronous twin.  Group of grid i: i; of the twins: 1000 + i.  Each
+    member runs to t_final at its own dt (r_alpha fixed), so the step counts differ.  Returns (specs, steps,
+    groups, twins)."""
+    specs, steps, groups = [], [], []
+    for i, (n, P) in enumerate(grids):
+        for sd in seeds:
+            sp = paper_case(case, n, sd, list(probs), P)
+            specs.append(sp)
+            steps.append(steps_to(sp, t_final))
+            groups.append(i)
+    return _with_sync_twins(specs, steps, groups, lambda g: 1000 + g)
 
 
 def adjoint_spec(n=256, P=4, steps=2000, alpha=0.05, alpha_target=0.06, seed=5):
