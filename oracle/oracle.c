@@ -15,8 +15,9 @@
  *     by {p_0..p_{L-1}}.  The uniform draw is a Philox4x32-10 word (Salmon et al., SC'11), keyed by
  *     the seed and counted by (step, side), so any delay can be replayed.
  *   - spatial operators: the central differences and the AT stencils exactly as printed in the
- *     tables "atschemes-left" / "atschemes-right" ((1,2,2)b, (2,2,2)b, (1,4,2), (2,4,2)), written
- *     out as the explicit sum over (point, time level) pairs of Eq. "general_deriv_at2".
+ *     tables "atschemes-left" / "atschemes-right" ((1,2,2)b, (2,2,2)b, (1,4,2), (2,4,2), (2,6,2), and the
+ *     stencils expanded in space, (1,2,2)a, (2,2,2)a, (2,1,2)), written out as the explicit sum over
+ *     (point, time level) pairs of Eq. "general_deriv_at2".
  *     ASYNC_STD is the standard scheme read at delayed levels, Eq. "general_deriv_async".
  *   - time integration: forward Euler (one level of Eq. "time_disc"), or Adams-Bashforth with two (Eq.
  *     "time_ab2") or three levels, started with Euler and then AB2.
@@ -30,7 +31,14 @@
  *   - levels before 0 do not exist: a drawn delay k>0 is clamped to min(k, max(0, n-(T-1)));
  *   - for the 4th-order point one cell in from a PE edge only the outer stencil point is a
  *     buffer point, so only it is read at delayed levels (Eq. "general_deriv_async");
- *   - an axis split into a single PE has no PE boundary (its periodic wrap is local).
+ *   - an axis split into a single PE has no PE boundary (its periodic wrap is local);
+ *   - like every AT row, the stencils expanded in space (Cases 2 and 3) replace the central difference only
+ *     when the side's delay is k > 0: they do not reduce to it at k = 0, and used there they leave a jump
+ *     across the PE boundary undamped (both edge rows vanish on a step), which makes the synchronous run
+ *     first-order accurate, against the slope -2 Sec. 5.2 reports for p_0 = 1;
+ *   - (1,2,2)a at the left boundary is read with +U_{i-1}^{n-k}: the printed minus sign makes the row
+ *     inconsistent (its coefficients would not sum to zero), and the plus sign gives the mirror image of the
+ *     right-boundary row and of Example 1's uniform-delay scheme (Eq. "ex1-1").
  *
  * Compiled with -ffp-contract=off so every product and sum rounds as written.
  */
@@ -45,12 +53,14 @@
 #define ORC_SYNC 0
 #define ORC_ASYNC_STD 1
 #define ORC_AT 2
+#define ORC_AT_SPACE2 3 /* Case 3: (1,2,2)a and (2,2,2)a at PE edges (order 2) */
+#define ORC_AT_SPACE1 4 /* Case 2: (2,1,2) at PE edges (order 2, diffusion only) */
 
 typedef struct {
   int32_t dim;      /* 1 or 3 */
   int32_t order;    /* 2 or 4 */
   int32_t L;        /* delays take values 0..L-1 */
-  int32_t scheme;   /* ORC_SYNC, ORC_ASYNC_STD, ORC_AT */
+  int32_t scheme;   /* ORC_SYNC, ORC_ASYNC_STD, ORC_AT, ORC_AT_SPACE2, ORC_AT_SPACE1 */
   int64_t n[3];     /* points per axis; unused axes hold 1 */
   int32_t pe[3];    /* PEs per axis; unused axes hold 1 */
   int32_t nmodes;   /* initial-condition modes per axis */
@@ -116,6 +126,7 @@ int orc_delay_raw(uint64_t seed, int64_t step, int64_t side, int L, const uint64
 
 /* number of successive delayed levels a scheme reads at a buffer point */
 int orc_time_width(int order, int scheme) { return scheme == ORC_AT ? order / 2 + 1 : 1; }
+/* the stencils expanded in space read one delayed level (T = 1) */
 
 /* levels before 0 do not exist: clamp a drawn delay so that level n-k-(T-1) >= 0 */
 int orc_delay_effective(int k, int64_t n, int T) {
@@ -177,6 +188,50 @@ static void w_order6(int k, double w[4]) {
 
 static double dxpow(double dx, int d) { return d == 1 ? dx : dx * dx; }
 
+/* The AT stencils expanded in space (tables "atschemes-left/right"), at the PE-edge point of a second-order
+ * scheme; buffer points read at level n-k.  dxd = dx^d.  Returns the number of taps.
+ *   (1,2,2)a left : (3 U_{i+1} - 3 U_i + U_{i-1}^{n-k} - U_{i-2}^{n-k}) / (4 dx)          (sign of U_{i-1}: see top)
+ *   (1,2,2)a right: (U_{i+2}^{n-k} - U_{i+1}^{n-k} + 3 U_i - 3 U_{i-1}) / (4 dx)
+ *   (2,2,2)a left : (2 U_{i+2} - 4 U_{i+1} + 2 U_i + U_{i-1}^{n-k} - 2 U_{i-2}^{n-k} + U_{i-3}^{n-k}) / (3 dx^2)
+ *   (2,2,2)a right: (U_{i+3}^{n-k} - 2 U_{i+2}^{n-k} + U_{i+1}^{n-k} + 2 U_i - 4 U_{i-1} + 2 U_{i-2}) / (3 dx^2)
+ *   (2,1,2)  left : (U_{i+1} - U_i - U_{i-1}^{n-k} + U_{i-2}^{n-k}) / (2 dx^2)
+ *   (2,1,2)  right: (U_{i+2}^{n-k} - U_{i+1}^{n-k} - U_i + U_{i-1}) / (2 dx^2)
+ * The (2,1,2) rows give only a second derivative; a first derivative is not defined for that case (diffusion).
+ * Called for k > 0 only. */
+static int space_expanded_taps(int scheme, int deriv, int left, int k, double dxd, orc_tap *out) {
+  static const int A1L_j[4] = {1, 0, -1, -2}, A1L_d[4] = {0, 0, 1, 1};
+  static const double A1L_c[4] = {3.0, -3.0, 1.0, -1.0};
+  static const int A1R_j[4] = {2, 1, 0, -1}, A1R_d[4] = {1, 1, 0, 0};
+  static const double A1R_c[4] = {1.0, -1.0, 3.0, -3.0};
+  static const int A2L_j[6] = {2, 1, 0, -1, -2, -3}, A2L_d[6] = {0, 0, 0, 1, 1, 1};
+  static const double A2L_c[6] = {2.0, -4.0, 2.0, 1.0, -2.0, 1.0};
+  static const int A2R_j[6] = {3, 2, 1, 0, -1, -2}, A2R_d[6] = {1, 1, 1, 0, 0, 0};
+  static const double A2R_c[6] = {1.0, -2.0, 1.0, 2.0, -4.0, 2.0};
+  static const int S2L_j[4] = {1, 0, -1, -2}, S2L_d[4] = {0, 0, 1, 1};
+  static const double S2L_c[4] = {1.0, -1.0, -1.0, 1.0};
+  static const int S2R_j[4] = {2, 1, 0, -1}, S2R_d[4] = {1, 1, 0, 0};
+  static const double S2R_c[4] = {1.0, -1.0, -1.0, 1.0};
+  const int *js, *ds;
+  const double *cs;
+  int nt;
+  double den;
+  if (scheme == ORC_AT_SPACE2 && deriv == 1) {
+    js = left ? A1L_j : A1R_j; ds = left ? A1L_d : A1R_d; cs = left ? A1L_c : A1R_c; nt = 4; den = 4.0;
+  } else if (scheme == ORC_AT_SPACE2) {
+    js = left ? A2L_j : A2R_j; ds = left ? A2L_d : A2R_d; cs = left ? A2L_c : A2R_c; nt = 6; den = 3.0;
+  } else if (deriv == 2) {
+    js = left ? S2L_j : S2R_j; ds = left ? S2L_d : S2R_d; cs = left ? S2L_c : S2R_c; nt = 4; den = 2.0;
+  } else {
+    return 0;
+  }
+  for (int t = 0; t < nt; ++t) {
+    out[t].j = js[t];
+    out[t].l = ds[t] ? k : 0;
+    out[t].c = cs[t] / (den * dxd);
+  }
+  return nt;
+}
+
 /* Taps of one derivative (deriv = 1 or 2) at a point at position pos (0..S-1) of its PE along
  * one axis.  use_pe = 0 means the axis has no PE boundary.  kL / kR are the effective delays of the
  * PE's left / right buffer points.  Returns the number of taps written to out (at most 32). */
@@ -191,6 +246,8 @@ int orc_taps(int order, int scheme, int deriv, int64_t pos, int64_t S, int use_p
   const int right = use_pe && pos >= S - h;
   const int k = left ? kL : (right ? kR : 0);
   int nt = 0;
+  if ((left || right) && k > 0 && (scheme == ORC_AT_SPACE2 || scheme == ORC_AT_SPACE1))
+    return space_expanded_taps(scheme, deriv, left, k, dxpow(dx, deriv), out);
   if ((!left && !right) || scheme == ORC_SYNC || k == 0) {
     /* synchronous: Eq. "general_deriv" */
     for (int j = -h; j <= h; ++j) {
@@ -264,7 +321,9 @@ int orc_check(const orc_cfg *g) {
   if (g->dim != 1 && g->dim != 3) return -1;
   if (g->order != 2 && g->order != 4 && g->order != 6) return -1;
   if (g->tsteps < 0 || g->tsteps > 3) return -1;
-  if (g->scheme < 0 || g->scheme > 2) return -1;
+  if (g->scheme < 0 || g->scheme > 4) return -1;
+  if (g->scheme >= ORC_AT_SPACE2 && (g->order != 2 || g->tsteps > 1)) return -1; /* Cases 2 and 3: CD2, Euler */
+  if (g->scheme == ORC_AT_SPACE1 && (g->c[0] != 0.0 || g->c[1] != 0.0 || g->c[2] != 0.0)) return -1;
   if (g->L < 1 || g->L > 8) return -1;
   if (g->nmodes < 1) return -1;
   for (int a = 0; a < 3; ++a) {

@@ -20,7 +20,7 @@ from __future__ import annotations
 import math
 import numpy as np
 
-SYNC, ASYNC_STD, AT = 0, 1, 2
+SYNC, ASYNC_STD, AT, AT_SPACE2, AT_SPACE1 = 0, 1, 2, 3, 4
 TWO_PI = 2.0 * math.pi
 
 
@@ -96,16 +96,20 @@ def workload(name: str, scheme: int = AT):
 
 
 def paper_case(case: int, n: int, seed: int, p0_probs=(1.0, 0.0, 0.0), P: int = 16):
-    """Cases 1, 4 and 5 of the paper's case table: kappa = {3,4,5}, A = {2, 0.5, 1.5} (as in Fig. "at-prob-all"),
+    """Cases 1 to 5 of the paper's case table: kappa = {3,4,5}, A = {2, 0.5, 1.5} (as in Fig. "at-prob-all"),
     L = len(p0_probs), alpha = 0.1, phases random per seed.  Case 1: advection-diffusion, forward Euler, CD2 with
-    (1,2,2)b/(2,2,2)b, r_alpha = 0.1 (Fig. "at-ord2-procs").  Case 4: advection-diffusion, AB2, CD4 with
+    (1,2,2)b/(2,2,2)b, r_alpha = 0.1 (Fig. "at-ord2-procs").  Case 2: diffusion, forward Euler, CD2 with (2,1,2);
+    Case 3: advection-diffusion, forward Euler, CD2 with (1,2,2)a/(2,2,2)a; both at r_alpha = 0.1 (not given for
+    Fig. "at-prob-all"; Case 1's value).  Case 4: advection-diffusion, AB2, CD4 with
     (1,4,2)/(2,4,2); Case 5: diffusion, AB3, CD6 with (2,6,2).  The paper does not give c or r_alpha for Cases 4
     and 5: c = 1 (Case 4) or 0 (Case 5), r_alpha = 0.05 (Case 4) or 0.01 (Case 5): with the time-extrapolated
     halos, AB2 and AB3 stay stable at every delay mix only at these smaller steps (the oracle diverges at
     r_alpha = 0.1 / 0.02 when p_0 <= 0.3)."""
-    order, tsteps, c, r = {1: (2, 1, 1.0, 0.1), 4: (4, 2, 1.0, 0.05), 5: (6, 3, 0.0, 0.01)}[case]
+    order, tsteps, c, r, scheme = {1: (2, 1, 1.0, 0.1, AT), 2: (2, 1, 0.0, 0.1, AT_SPACE1),
+                                   3: (2, 1, 1.0, 0.1, AT_SPACE2), 4: (4, 2, 1.0, 0.05, AT),
+                                   5: (6, 3, 0.0, 0.01, AT)}[case]
     probs = list(p0_probs)
-    spec, _ = wl_1d(n, P, order, len(probs), 0, seed, (3, 4, 5), c=c, alpha=0.1, r_alpha=r,
+    spec, _ = wl_1d(n, P, order, len(probs), 0, seed, (3, 4, 5), scheme=scheme, c=c, alpha=0.1, r_alpha=r,
                     probs=probs if len(probs) > 1 else None, tsteps=tsteps)
     spec["amp"] = np.array([[2.0, 0.5, 1.5]])
     return spec
@@ -116,14 +120,16 @@ def steps_to(spec, t_final: float) -> int:
 
 
 def _with_sync_twins(specs, steps, groups, sync_group):
-    """Append a synchronous twin (same seed, initial condition and step) after each member; returns the lists
-    with the twin index of every member (-1 for the twins themselves)."""
+    """Append a synchronous twin after each member: the same scheme, initial condition and steps with every delay
+    0 (L = 1; for the time-expanded rows this is the central scheme, the stencils expanded in space keep their
+    edge form at k = 0).  Returns the lists with the twin index of every member (-1 for the twins themselves)."""
     k = len(specs)
     twins = [k + i for i in range(k)] + [-1] * k
     sync = []
     for sp in specs:
         t = dict(sp)
-        t["scheme"] = SYNC
+        t["L"] = 1
+        t["thresholds"] = None
         sync.append(t)
     return specs + sync, steps + steps, groups + [sync_group(g) for g in groups], twins
 
