@@ -44,6 +44,10 @@ extern "C" {
 #define AT_SYNC 0      /* every delay is 0: standard central differences everywhere (Eq. "general_deriv") */
 #define AT_ASYNC_STD 1 /* central differences read at the delayed level n-k (Eq. "general_deriv_async") */
 #define AT_AT 2        /* asynchrony-tolerant, time-expanded stencils ((1,2,2)b/(2,2,2)b, (1,4,2)/(2,4,2), (2,6,2)) */
+#define AT_AT_SPACE2 3 /* AT stencils expanded in space, (1,2,2)a/(2,2,2)a (Case 3): order 2, forward Euler; the
+                        * PE-edge point of a side with delay k > 0 uses the row, k = 0 the central difference */
+#define AT_AT_SPACE1 4 /* the first-order row expanded in space, (2,1,2) (Case 2): order 2, forward Euler, diffusion
+                        * only (c = 0); edge rows for k > 0 as for AT_AT_SPACE2 */
 
 /* ------------------------------------------------------------------ scheme coefficients */
 typedef struct {
@@ -71,9 +75,12 @@ int at_coeffs(int32_t deriv, int32_t order, int32_t L, at_coeffs_t *out);
 
 /* Expanded taps c~_{j,l} (Eq. "general_deriv_at2") of derivative `deriv` at a point `pos` cells in
  * from a PE edge (pos = 0 is the edge point) on side `side` (0: buffer points on the left, 1: on the
- * right), for scheme AT_SYNC / AT_ASYNC_STD / AT_AT and effective delay k.  Coefficients are in units
- * of 1/dx^d, taps with equal (j, l) merged.  Writes at most `cap` taps (j_out, l_out, c_out) and
- * stores their number in *ntaps.  Host only.  Errors: AT_ERR_ARG. */
+ * right), for scheme AT_SYNC / AT_ASYNC_STD / AT_AT / AT_AT_SPACE2 / AT_AT_SPACE1 and effective delay k.  The rows
+ * expanded in space are derived from their shapes ({i+1, i; i-1, i-2} for (1,2,2)a and (2,1,2), {i+2, i+1, i; i-1,
+ * i-2, i-3} for (2,2,2)a, buffer points at level n-k, mirrored for side 1) by the single system of Sec. 3.1-3.2.
+ * Coefficients are in units of 1/dx^d, taps with equal (j, l) merged.  Writes at most `cap` taps (j_out, l_out,
+ * c_out) and stores their number in *ntaps.  Host only.  Errors: AT_ERR_ARG (also: AT_AT_SPACE1 with deriv 1 at
+ * an edge point with k > 0, the space schemes with order != 2). */
 int at_stencil_taps(int32_t deriv, int32_t order, int32_t scheme, int32_t k, int32_t pos, int32_t side,
                     int32_t cap, int32_t *j_out, int32_t *l_out, double *c_out, int32_t *ntaps);
 

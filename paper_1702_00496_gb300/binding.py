@@ -16,7 +16,7 @@ from . import _build
 AT_OK = 0
 AT_ERR_ARG, AT_ERR_SINGULAR, AT_ERR_INCONSISTENT, AT_ERR_CUDA = -1, -2, -3, -4
 AT_ERR_TIMEOUT, AT_ERR_NONFINITE, AT_ERR_BOUNDS, AT_ERR_STATE = -5, -6, -7, -8
-AT_SYNC, AT_ASYNC_STD, AT_AT = 0, 1, 2
+AT_SYNC, AT_ASYNC_STD, AT_AT, AT_AT_SPACE2, AT_AT_SPACE1 = 0, 1, 2, 3, 4
 
 # every entry point include/at.h declares (checked by the CPU test of the boundary)
 EXPORTS = (

@@ -38,7 +38,12 @@ int check_config(const at_config_t *c) {
   if (c->dim != 1 && c->dim != 3) return fail(AT_ERR_ARG, "dim must be 1 or 3");
   if (c->order != 2 && c->order != 4 && c->order != 6) return fail(AT_ERR_ARG, "order must be 2, 4 or 6");
   if (c->tsteps < 0 || c->tsteps > 3) return fail(AT_ERR_ARG, "tsteps must be 0..3");
-  if (c->scheme < AT_SYNC || c->scheme > AT_AT) return fail(AT_ERR_ARG, "scheme must be AT_SYNC, AT_ASYNC_STD or AT_AT");
+  if (c->scheme < AT_SYNC || c->scheme > AT_AT_SPACE1)
+    return fail(AT_ERR_ARG, "scheme must be AT_SYNC, AT_ASYNC_STD, AT_AT, AT_AT_SPACE2 or AT_AT_SPACE1");
+  if (c->scheme >= AT_AT_SPACE2 && (c->order != 2 || c->tsteps > 1))
+    return fail(AT_ERR_ARG, "the rows expanded in space are second-order schemes with forward Euler (Cases 2, 3)");
+  if (c->scheme == AT_AT_SPACE1 && (c->c[0] != 0.0 || c->c[1] != 0.0 || c->c[2] != 0.0))
+    return fail(AT_ERR_ARG, "(2,1,2) gives only a second derivative: AT_AT_SPACE1 needs c = 0 (diffusion)");
   if (c->L < 1 || c->L > AT_MAX_L) return fail(AT_ERR_ARG, "L must be in 1..8");
   if (c->nmodes < 1 || c->nmodes > AT_MAX_MODES) return fail(AT_ERR_ARG, "nmodes must be in 1..16");
   if (!c->amp || !c->phase || !c->kappa) return fail(AT_ERR_ARG, "amp, phase and kappa are required");
@@ -88,6 +93,49 @@ extern "C" int at_delay(uint64_t seed, int64_t step, int64_t side, int32_t L, co
   return atfd::delay_draw(seed, (uint32_t)step, (uint32_t)side, L, thresholds_host);
 }
 
+// The merged edge rows of axis a for the schemes expanded in space: D1 and D2 rows from at_stencil_taps (derived
+// from their shapes), checked to be the same for every delay 1..L-1, merged as dt (-c_a D1/dx + alpha D2/dx^2).
+static int space_rows(const at_config_t *cfg, int a, double dx, StepParams *p) {
+  for (int side = 0; side < 2; ++side) {
+    int n = 0;
+    for (int deriv = 1; deriv <= 2; ++deriv) {
+      if (deriv == 1 && cfg->scheme == AT_AT_SPACE1) continue;  // diffusion only
+      int32_t j0[16], l0[16], nt0 = 0;
+      double c0[16];
+      for (int k = 1; k < cfg->L; ++k) {
+        int32_t jj[16], ll[16], nt = 0;
+        double cc[16];
+        int rc = at_stencil_taps(deriv, cfg->order, cfg->scheme, k, 0, side, 16, jj, ll, cc, &nt);
+        if (rc != AT_OK) return rc;
+        if (k == 1) {
+          nt0 = nt;
+          for (int t = 0; t < nt; ++t) { j0[t] = jj[t]; l0[t] = ll[t] ? 1 : 0; c0[t] = cc[t]; }
+        } else {
+          bool same = nt == nt0;
+          for (int t = 0; same && t < nt; ++t) same = jj[t] == j0[t] && (ll[t] ? 1 : 0) == l0[t] && cc[t] == c0[t];
+          if (!same) return fail(AT_ERR_INCONSISTENT, "edge row coefficients depend on the delay");
+        }
+      }
+      const double scale = deriv == 1 ? -cfg->c[a] / dx : cfg->alpha / (dx * dx);
+      for (int t = 0; t < nt0; ++t) {
+        int slot = -1;
+        for (int u = 0; u < n; ++u)
+          if (p->ej[a][side][u] == j0[t] && p->ebuf[a][side][u] == l0[t]) slot = u;
+        if (slot < 0) {
+          if (n == AT_MAX_ETAPS) return fail(AT_ERR_ARG, "edge row has too many taps");
+          slot = n++;
+          p->ej[a][side][slot] = (int8_t)j0[t];
+          p->ebuf[a][side][slot] = (int8_t)l0[t];
+          p->ec[a][side][slot] = 0.0;
+        }
+        p->ec[a][side][slot] += cfg->dt * scale * c0[t];
+      }
+    }
+    p->ecount[a][side] = n;
+  }
+  return AT_OK;
+}
+
 int at_prepare_params(const at_config_t *cfg, double *ring_dev, uint8_t *log_dev, int64_t log_steps, StepParams *out) {
   int rc = check_config(cfg);
   if (rc) return rc;
@@ -126,8 +174,9 @@ int at_prepare_params(const at_config_t *cfg, double *ring_dev, uint8_t *log_dev
     for (int j = -h; j <= h; ++j) {
       const double v = cfg->dt * (-cfg->c[a] * c1.cd[j + h] / dx + cfg->alpha * c2.cd[j + h] / (dx * dx));
       const double dv = cfg->dt * c2.cd[j + h] / (dx * dx);
-      if (j == 0) { s0 += v; q0 += dv; } else { p.s[a][j + h] = v; p.q[a][j + h] = dv; }
+      if (j == 0) { s0 += v; q0 += dv; p.sc[a] = v; } else { p.s[a][j + h] = v; p.q[a][j + h] = dv; }
     }
+    if (cfg->scheme >= AT_AT_SPACE2 && cfg->pe[a] > 1 && (rc = space_rows(cfg, a, dx, &p)) != AT_OK) return rc;
   }
   p.s0 = s0;
   p.q0 = q0;

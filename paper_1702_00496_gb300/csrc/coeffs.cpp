@@ -6,6 +6,8 @@
 //  at_stencil_taps   expanded taps c~_{j,l} (Eq. "general_deriv_at2") built from at_coeffs.
 //  at_solve_stencil  single-system derivation of Sec. 3.1-3.2 with the rank tests of Sec. 3.2
 //                    (used for Examples 1 and 2 and any user stencil).
+//  the stencils expanded in space ((1,2,2)a, (2,2,2)a, (2,1,2); Cases 3 and 2) are derived from their shapes by
+//  the same single-system procedure, for the edge point of each side.
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -184,6 +186,55 @@ struct Tap {
   Q c;
 };
 
+// Eq. "cond" with dt ~ dx^2 on an explicit stencil {(j_t, l_t)}: the single system of Sec. 3.1-3.2, rows
+// p + 2q < d + a.  Returns AT_OK with the unique coefficients, or the rank-test status.
+int solve_shape(int d, int a, const std::vector<int> &js, const std::vector<int> &ls, std::vector<Q> *x) {
+  std::vector<std::vector<Q>> m;
+  for (int p = 0; p < d + a; ++p)
+    for (int q = 0; p + 2 * q < d + a; ++q) {
+      std::vector<Q> row;
+      for (size_t t = 0; t < js.size(); ++t) row.push_back(qpow(Q(js[t]), p) * qpow(Q(-ls[t]), q) / Q(fact(p) * fact(q)));
+      row.push_back(Q((p == d && q == 0) ? 1 : 0));
+      m.push_back(row);
+    }
+  int rA, rAb;
+  solve_rank(m, (int)js.size(), &rA, &rAb, x);
+  if (rA != rAb) return AT_ERR_INCONSISTENT;
+  if (rA < (int)js.size()) return AT_ERR_SINGULAR;
+  return g_overflow ? AT_ERR_ARG : AT_OK;
+}
+
+// Shapes of the rows expanded in space at the edge point whose buffer points lie on the left (side 0): points
+// with flag 1 are buffer points, read at level n-k.  The right edge (side 1) uses the mirror image.
+//   (1,2,2)a: {i+1, i; i-1, i-2}      (2,2,2)a: {i+2, i+1, i; i-1, i-2, i-3}      (2,1,2): {i+1, i; i-1, i-2}
+// Returns the order a of the row, or 0 if the scheme defines no row for this derivative.
+int space_shape(int scheme, int d, std::vector<int> *js, std::vector<int> *buf) {
+  if (scheme == AT_AT_SPACE2 && d == 1) { *js = {1, 0, -1, -2}; *buf = {0, 0, 1, 1}; return 2; }
+  if (scheme == AT_AT_SPACE2 && d == 2) { *js = {2, 1, 0, -1, -2, -3}; *buf = {0, 0, 0, 1, 1, 1}; return 2; }
+  if (scheme == AT_AT_SPACE1 && d == 2) { *js = {1, 0, -1, -2}; *buf = {0, 0, 1, 1}; return 1; }
+  return 0;
+}
+
+// The row expanded in space of derivative d at the edge point of `side` for delay k >= 1, derived from its
+// shape.  Returns AT_OK, AT_ERR_ARG (no row for this derivative) or the rank-test status.
+int space_taps(int scheme, int d, int k, int side, std::vector<Tap> *taps) {
+  std::vector<int> js, buf;
+  const int a = space_shape(scheme, d, &js, &buf);
+  if (a == 0) return AT_ERR_ARG;
+  std::vector<int> ls(js.size());
+  for (size_t t = 0; t < js.size(); ++t) {
+    if (side == 1) js[t] = -js[t];
+    ls[t] = buf[t] ? k : 0;
+  }
+  std::vector<Q> x;
+  const int rc = solve_shape(d, a, js, ls, &x);
+  if (rc != AT_OK) return rc;
+  taps->clear();
+  for (size_t t = 0; t < js.size(); ++t)
+    if (!x[t].zero()) taps->push_back(Tap{js[t], ls[t], x[t]});
+  return AT_OK;
+}
+
 // Taps of the stencil at a point `pos` cells in from the edge whose buffer points lie on `side`.
 void expand(const Derived &D, int scheme, int k, int pos, int side, std::vector<Tap> *taps) {
   const int h = D.h;
@@ -283,9 +334,14 @@ extern "C" int at_coeffs(int32_t deriv, int32_t order, int32_t L, at_coeffs_t *o
 
 extern "C" int at_stencil_taps(int32_t deriv, int32_t order, int32_t scheme, int32_t k, int32_t pos, int32_t side,
                                int32_t cap, int32_t *j_out, int32_t *l_out, double *c_out, int32_t *ntaps) {
-  if ((deriv != 1 && deriv != 2) || (order != 2 && order != 4 && order != 6) || scheme < 0 || scheme > 2 || k < 0 || k > 7 ||
+  if ((deriv != 1 && deriv != 2) || (order != 2 && order != 4 && order != 6) || scheme < 0 || scheme > 4 || k < 0 || k > 7 ||
       pos < 0 || side < 0 || side > 1 || cap < 0 || !j_out || !l_out || !c_out || !ntaps) {
     at_internal_set_error("at_stencil_taps: bad argument");
+    return AT_ERR_ARG;
+  }
+  const bool space = scheme == AT_AT_SPACE2 || scheme == AT_AT_SPACE1;
+  if (space && order != 2) {
+    at_internal_set_error("at_stencil_taps: the rows expanded in space are second-order schemes (order 2)");
     return AT_ERR_ARG;
   }
   g_overflow = false;
@@ -293,7 +349,14 @@ extern "C" int at_stencil_taps(int32_t deriv, int32_t order, int32_t scheme, int
   int rc = derive(deriv, order, k + 1, &D);
   if (rc != AT_OK) return rc;
   std::vector<Tap> taps;
-  expand(D, scheme, k, pos, side, &taps);
+  if (space && k > 0 && pos == 0) {
+    if ((rc = space_taps(scheme, deriv, k, side, &taps)) != AT_OK) {
+      at_internal_set_error("at_stencil_taps: (2,1,2) defines no first derivative, or the row's system failed");
+      return rc;
+    }
+  } else {
+    expand(D, space ? AT_SYNC : scheme, k, pos, side, &taps);
+  }
   if ((int)taps.size() > cap) {
     at_internal_set_error("at_stencil_taps: cap too small");
     return AT_ERR_ARG;

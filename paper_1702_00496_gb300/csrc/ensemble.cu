@@ -77,7 +77,7 @@ __device__ void member_prehistory(MemberParams &m) {
 
 // One realization, all steps: the delays of step n+1 are drawn (into the other half of the shared delay
 // buffer) while step n is computed; one barrier per step publishes both the new level and the new delays.
-template <int H, bool AB>
+template <int H, bool AB, bool SPACE>
 __device__ void run_member(const StepParams &p, uint8_t *keff_sh, int64_t nsteps) {
   const int groups = p.n[0] >> 2;
   atfd::draw_sides(p, 0, threadIdx.x, blockDim.x, keff_sh);
@@ -88,15 +88,20 @@ __device__ void run_member(const StepParams &p, uint8_t *keff_sh, int64_t nsteps
     if (n + 1 < nsteps) atfd::draw_sides(p, n + 1, threadIdx.x, blockDim.x, keff_sh + ((n + 1) & 1) * p.nb);
     const uint8_t *keff = keff_sh + (n & 1) * p.nb;
     for (int k = threadIdx.x; k < groups; k += blockDim.x)
-      atfd::group_update<1, H, atfd::LdCoherent, AB>(p, keff, un, out, n, (int)(atfd::group_1d_order(p, k) << 2), 0,
+      if (SPACE)
+        atfd::group_step<1, H, atfd::LdCoherent, AB>(p, keff, un, out, n, (int)(atfd::group_1d_order(p, k) << 2), 0,
                                                      0);
+      else
+        atfd::group_update<1, H, atfd::LdCoherent, AB>(p, keff, un, out, n, (int)(atfd::group_1d_order(p, k) << 2),
+                                                       0, 0);
     __syncthreads();
   }
 }
 
-// HMAX: the largest stencil half-width among the members; AB: some member uses Adams-Bashforth.  The host picks
-// the smallest variant that covers every member, so the common case keeps the register budget of H <= 2 Euler.
-template <int HMAX, bool AB>
+// HMAX: the largest stencil half-width among the members; AB: some member uses Adams-Bashforth; SPACE: some member
+// uses rows expanded in space.  The host picks the smallest variant that covers every member, so the common case
+// keeps the register budget of the H <= 2 Euler step.
+template <int HMAX, bool AB, bool SPACE>
 __global__ void __launch_bounds__(1024, 1) ensemble_kernel(const MemberParams *__restrict__ members,
                                                        const int32_t *__restrict__ order, int32_t count,
                                                        int32_t *counter, double *__restrict__ member_stats) {
@@ -123,13 +128,13 @@ __global__ void __launch_bounds__(1024, 1) ensemble_kernel(const MemberParams *_
       if (m.p.h == 1) member_prehistory<1>(m);
       else if (HMAX == 2 || m.p.h == 2) member_prehistory<2>(m);
       else member_prehistory<HMAX>(m);
-      if (m.p.h == 1) run_member<1, AB>(m.p, keff_sh, m.steps);
-      else if (HMAX == 2 || m.p.h == 2) run_member<2, AB>(m.p, keff_sh, m.steps);
-      else run_member<HMAX, AB>(m.p, keff_sh, m.steps);
+      if (m.p.h == 1) run_member<1, AB, SPACE>(m.p, keff_sh, m.steps);
+      else if (HMAX == 2 || m.p.h == 2) run_member<2, AB, SPACE>(m.p, keff_sh, m.steps);
+      else run_member<HMAX, AB, SPACE>(m.p, keff_sh, m.steps);
     } else {
-      if (m.p.h == 1) run_member<1, false>(m.p, keff_sh, m.steps);
-      else if (HMAX == 2 || m.p.h == 2) run_member<2, false>(m.p, keff_sh, m.steps);
-      else run_member<HMAX, false>(m.p, keff_sh, m.steps);
+      if (m.p.h == 1) run_member<1, false, SPACE>(m.p, keff_sh, m.steps);
+      else if (HMAX == 2 || m.p.h == 2) run_member<2, false, SPACE>(m.p, keff_sh, m.steps);
+      else run_member<HMAX, false, SPACE>(m.p, keff_sh, m.steps);
     }
     // statistics of E = U^steps - u_a(x, steps dt), as in the single-problem reduction
     const double *u = m.p.ring + (m.steps % m.p.R) * m.p.ntot;
@@ -435,13 +440,20 @@ extern "C" int at_ensemble_create(const at_config_t *members, const at_member_t 
   }
   e->dyn_smem = dyn_smem;
   int hmax = 1;
-  bool any_ab = false;
+  bool any_ab = false, any_space = false;
   for (int r = 0; r < count; ++r) {
     hmax = std::max(hmax, (int)host[r].p.h);
     any_ab = any_ab || host[r].p.ts > 1;
+    any_space = any_space || host[r].p.scheme >= AT_AT_SPACE2;
   }
-  auto kernel = hmax <= 2 ? (any_ab ? ensemble_kernel<2, true> : ensemble_kernel<2, false>)
-                          : (any_ab ? ensemble_kernel<3, true> : ensemble_kernel<3, false>);
+  auto kernel = any_space ? ensemble_kernel<2, false, true>
+                : hmax <= 2 ? (any_ab ? ensemble_kernel<2, true, false> : ensemble_kernel<2, false, false>)
+                            : (any_ab ? ensemble_kernel<3, true, false> : ensemble_kernel<3, false, false>);
+  if (any_space && (hmax > 2 || any_ab)) {
+    // a mix of schemes expanded in space with order-6 or Adams-Bashforth members
+    kernel = hmax <= 2 ? (any_ab ? ensemble_kernel<2, true, true> : ensemble_kernel<2, false, true>)
+                       : (any_ab ? ensemble_kernel<3, true, true> : ensemble_kernel<3, false, true>);
+  }
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kernel, threads, dyn_smem);
   if (ctas_per_sm <= 0) ctas_per_sm = fit;
   if (ctas_per_sm > fit) ctas_per_sm = fit;

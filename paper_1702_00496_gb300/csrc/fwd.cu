@@ -44,13 +44,13 @@ __global__ void __launch_bounds__(512) forward_group_kernel(const StepParams p, 
   for (int64_t k = tid; k < groups; k += nthreads) {
     if (DIM == 1) {
       const int64_t g = group_1d_order(p, k);
-      group_update<1, H, LdgNC, AB>(p, keff, un, out, n, (int)(g << 2), 0, 0);
+      group_step<1, H, LdgNC, AB>(p, keff, un, out, n, (int)(g << 2), 0, 0);
     } else {
       const int64_t g = p.order ? (int64_t)p.order[k] : k;
       const int64_t r = g / gx;
       const int x0 = (int)(g - r * gx) << 2;
       const int z = (int)(r / p.n[1]), y = (int)(r - (int64_t)z * p.n[1]);
-      group_update<3, H, LdgNC, AB>(p, keff, un, out, n, x0, y, z);
+      group_step<3, H, LdgNC, AB>(p, keff, un, out, n, x0, y, z);
     }
   }
 }
@@ -79,7 +79,8 @@ __global__ void __launch_bounds__(512) forward_point_kernel(const StepParams p, 
   for (int64_t i = tid; i < p.ntot; i += nthreads) {
     int c[3];
     point_coords(p, DIM, i, c);
-    double r[1] = {point_update<DIM, H, LdgNC>(p, keff, un, n, i, c)};
+    double r[1] = {(H == 1 && p.scheme >= AT_AT_SPACE2) ? point_update_space<DIM, LdgNC>(p, keff, un, n, i, c)
+                                                        : point_update<DIM, H, LdgNC>(p, keff, un, n, i, c)};
     if (AB) {
       const double u[1] = {un[i]};
       ab_combine<1>(p, n, i, u, r);

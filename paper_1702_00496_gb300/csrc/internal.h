@@ -11,6 +11,7 @@
 #define AT_MAX_T 4
 #define AT_MAX_H 3
 #define AT_MAX_MODES 16
+#define AT_MAX_ETAPS 8
 #define AT_STAT_FIELDS 9
 #define AT_STAT_BLOCKS 1024
 
@@ -50,6 +51,14 @@ struct StepParams {
   double q0;                      // d s0 / d alpha = dt sum_a cd2_0 / dx_a^2
   double q[3][2 * AT_MAX_H + 1];  // d s_{a,j} / d alpha = dt cd2_j / dx_a^2
   double w[AT_MAX_L][AT_MAX_T];   // halo extrapolation weights w[k][m] of level n-k-m
+  double sc[3];                   // per-axis centre coefficient s_{a,0} (s0 = 1 + sc[0] + sc[1] + sc[2])
+  // Rows expanded in space (AT_AT_SPACE2 / AT_AT_SPACE1): merged taps dt (-c_a D1 + alpha D2) of the PE-edge
+  // point of axis a, side s (0: buffer points on the left), at offset ej, read at level n (ebuf 0) or n-k
+  // (ebuf 1); used when that side's delay is k > 0.
+  int32_t ecount[3][2];
+  int8_t ej[3][2][AT_MAX_ETAPS];
+  int8_t ebuf[3][2][AT_MAX_ETAPS];
+  double ec[3][2][AT_MAX_ETAPS];
 };
 
 // Initial-condition / analytic-solution parameters.

@@ -272,4 +272,89 @@ __device__ double point_update(const StepParams &p, const uint8_t *__restrict__ 
   return acc;
 }
 
+// Rows expanded in space (AT_AT_SPACE2 / AT_AT_SPACE1, order 2): a point at the edge of its PE along a split axis
+// (position 0 or S-1) whose side has delay k > 0 takes that axis's edge row -- in-PE taps at level n, buffer taps
+// at level n-k -- instead of the central taps; every other axis and point keeps the central difference.  One
+// point, any shape; the same FMA chain order as the central path (centre first, then axis by axis).
+template <int DIM, class LD>
+__device__ double point_update_space(const StepParams &p, const uint8_t *__restrict__ keff,
+                                     const double *__restrict__ un, int64_t n, int64_t i, const int c[3]) {
+  const int64_t stride[3] = {1, (int64_t)p.n[0], (int64_t)p.n[0] * p.n[1]};
+  const int sn = (int)(n % p.R);
+  int pidx[3] = {0, 0, 0}, krow[3] = {0, 0, 0}, srow[3] = {0, 0, 0};
+  double c0 = p.ts > 1 ? 0.0 : 1.0;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    pidx[a] = c[a] / p.S[a];
+    const int pos = c[a] - pidx[a] * p.S[a];
+    if (p.use_pe[a] && (pos == 0 || pos == p.S[a] - 1)) {
+      srow[a] = pos == 0 ? 0 : 1;
+      krow[a] = keff[side_of<DIM>(p, pidx, a, srow[a])];
+    }
+    if (krow[a] == 0) c0 += p.sc[a];
+  }
+  double acc = fma(c0, LD::ld(un + i), p.zero);
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    if (krow[a] > 0) {
+      const int s = srow[a], nt = p.ecount[a][s];
+      for (int t = 0; t < nt; ++t) {
+        const int cj = wrap_coord(c[a] + p.ej[a][s][t], p.n[a]);
+        const int64_t cell = i + (int64_t)(cj - c[a]) * stride[a];
+        const double *lvl = p.ebuf[a][s][t] ? p.ring + slot_back(sn, krow[a], p.R) * p.ntot : un;
+        acc = fma(p.ec[a][s][t], LD::ld(lvl + cell), acc);
+      }
+    } else {
+#pragma unroll
+      for (int j = -1; j <= 1; j += 2) {
+        const int cj = wrap_coord(c[a] + j, p.n[a]);
+        acc = fma(p.s[a][j + 1], LD::ld(un + i + (int64_t)(cj - c[a]) * stride[a]), acc);
+      }
+    }
+  }
+  return acc;
+}
+
+// Does the group x0..x0+3 of row (y, z) hold a PE-edge point of a split axis (AT_AT_SPACE2 / AT_AT_SPACE1)?
+template <int DIM>
+__device__ __forceinline__ bool group_at_space_edge(const StepParams &p, int x0, int y, int z) {
+  if (p.use_pe[0]) {
+    const int pos = x0 % p.S[0];
+    if (pos == 0 || pos + 4 == p.S[0]) return true;
+  }
+  if (DIM == 3) {
+    if (p.use_pe[1]) {
+      const int pos = y % p.S[1];
+      if (pos == 0 || pos == p.S[1] - 1) return true;
+    }
+    if (p.use_pe[2]) {
+      const int pos = z % p.S[2];
+      if (pos == 0 || pos == p.S[2] - 1) return true;
+    }
+  }
+  return false;
+}
+
+// One group of the forward step for every scheme: groups holding a PE-edge point of a scheme expanded in space
+// go point by point through its edge rows, all others through the grouped central / time-expanded path.
+template <int DIM, int H, class LD, bool AB>
+__device__ __forceinline__ void group_step(const StepParams &p, const uint8_t *__restrict__ keff,
+                                           const double *__restrict__ un, double *__restrict__ out, int64_t n,
+                                           int x0, int y, int z) {
+  if (H == 1 && !AB && p.scheme >= AT_AT_SPACE2 && group_at_space_edge<DIM>(p, x0, y, z)) {
+    const int64_t i0 = (DIM == 3 ? ((int64_t)z * p.n[1] + y) * p.n[0] : 0) + x0;
+    int c[3] = {x0, y, z};
+    double r[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      c[0] = x0 + q;
+      r[q] = point_update_space<DIM, LD>(p, keff, un, n, i0 + q, c);
+    }
+    reinterpret_cast<double2 *>(out + i0)[0] = make_double2(r[0], r[1]);
+    reinterpret_cast<double2 *>(out + i0)[1] = make_double2(r[2], r[3]);
+    return;
+  }
+  group_update<DIM, H, LD, AB>(p, keff, un, out, n, x0, y, z);
+}
+
 }  // namespace atfd

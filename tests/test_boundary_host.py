@@ -82,6 +82,33 @@ def _merge(taps):
 @pytest.mark.parametrize("scheme", [P.AT_SYNC, P.AT_ASYNC_STD, P.AT_AT])
 def test_derived_taps_equal_the_oracle_tables(order, deriv, scheme):
     """The library derives its stencils by solving Eq. "cond"; the oracle types them from the tables."""
+    _compare_taps(order, deriv, scheme)
+
+
+@pytest.mark.parametrize("deriv,scheme", [(1, P.AT_AT_SPACE2), (2, P.AT_AT_SPACE2), (2, P.AT_AT_SPACE1)])
+def test_derived_space_expanded_rows_equal_the_oracle_tables(deriv, scheme):
+    """(1,2,2)a, (2,2,2)a, (2,1,2): the library solves the single system on each row's shape."""
+    _compare_taps(2, deriv, scheme)
+
+
+def test_space_expanded_schemes_reject_what_they_do_not_define():
+    with pytest.raises(B.ATError):
+        P.at_stencil_taps(1, 2, P.AT_AT_SPACE1, 1, 0, 0)  # (2,1,2) has no first derivative
+    with pytest.raises(B.ATError):
+        P.at_stencil_taps(2, 4, P.AT_AT_SPACE2, 1, 0, 0)  # the rows are second order
+    for field, value in (("order", 4), ("tsteps", 2)):
+        spec, _ = W.wl_1d(256, 8, 2, 3, 0, 1, (1, 2), scheme=W.AT_SPACE2)
+        spec[field] = value
+        with pytest.raises(B.ATError):
+            P.at_ring_slots(B.Config(spec))
+    spec, _ = W.wl_1d(256, 8, 2, 3, 0, 1, (1, 2), scheme=W.AT_SPACE1)  # c = 1: (2,1,2) is for diffusion
+    with pytest.raises(B.ATError):
+        P.at_ring_slots(B.Config(spec))
+    spec["c"] = [0.0]
+    assert P.at_ring_slots(B.Config(spec)) == 3 + 1
+
+
+def _compare_taps(order, deriv, scheme):
     S = 10
     for k in range(4):
         for pos in range(order // 2):
