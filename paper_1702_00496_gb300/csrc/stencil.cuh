@@ -282,10 +282,11 @@ __device__ double point_update_space(const StepParams &p, const uint8_t *__restr
   const int64_t stride[3] = {1, (int64_t)p.n[0], (int64_t)p.n[0] * p.n[1]};
   const int sn = (int)(n % p.R);
   int pidx[3] = {0, 0, 0}, krow[3] = {0, 0, 0}, srow[3] = {0, 0, 0};
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) pidx[a] = c[a] / p.S[a];  // the whole PE index before any side lookup
   double c0 = p.ts > 1 ? 0.0 : 1.0;
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
-    pidx[a] = c[a] / p.S[a];
     const int pos = c[a] - pidx[a] * p.S[a];
     if (p.use_pe[a] && (pos == 0 || pos == p.S[a] - 1)) {
       srow[a] = pos == 0 ? 0 : 1;
