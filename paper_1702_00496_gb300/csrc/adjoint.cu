@@ -493,6 +493,7 @@ cudaError_t copy_field(double *dst, const double *src, int64_t n, cudaStream_t s
 static int adjoint_supported(const at_handle *hd) {
   if (hd->sp.ts > 1) return fail(AT_ERR_ARG, "adjoint: only forward Euler (tsteps 0 or 1) is supported");
   if (hd->sp.h > 2) return fail(AT_ERR_ARG, "adjoint: only orders 2 and 4 are supported");
+  if (hd->sp.scheme >= AT_AT_SPACE2) return fail(AT_ERR_ARG, "adjoint: the rows expanded in space are not supported");
   return AT_OK;
 }
 

@@ -12,6 +12,8 @@ themselves, not stand-ins for a dataset):
   3d_512_o2/4  3D, 512^3, 8x8x8 PEs,  order 2 or 4, L=3, dt = dx^2, 500 steps
   ensemble     1024 1D realizations, N_r in {2^10..2^16}, P_r=N_r/64, L_r in {2,3,4}, 5000 steps
   adjoint_256  3D 256^3, 4x4x4 PEs, order 4, L=3, 2000 steps
+  1d_n16m_case2  the paper's Case 2 scaled to N=2^24, 4096 PEs: CD2 + (2,1,2), Euler, diffusion, L=3, 1000 steps
+  1d_n16m_case3  the paper's Case 3 scaled to N=2^24, 4096 PEs: CD2 + (1,2,2)a/(2,2,2)a, Euler, L=3, 1000 steps
   1d_n16m_case4  the paper's Case 4 scaled to N=2^24, 4096 PEs: CD4 + (1,4,2)/(2,4,2), AB2, L=3, 1000 steps
   1d_n16m_case5  the paper's Case 5 scaled to N=2^24, 4096 PEs: CD6 + (2,6,2), AB3, L=3, 1000 steps
 """
@@ -87,7 +89,7 @@ def workload(name: str, scheme: int = AT):
         return wl_3d(256, 4, 4, 3, 500, 3, scheme)
     if name == "adjoint_256":
         return adjoint_spec(256, 4, 2000)
-    if name in ("1d_n16m_case4", "1d_n16m_case5"):
+    if name in ("1d_n16m_case2", "1d_n16m_case3", "1d_n16m_case4", "1d_n16m_case5"):
         spec = paper_case(int(name[-1]), 1 << 24, 2, (1 / 3, 1 / 3, 1 / 3), P=4096)
         if scheme != AT:
             spec["scheme"] = scheme
