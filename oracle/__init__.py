@@ -34,7 +34,7 @@ class OrcCfg(C.Structure):
         ("n", C.c_int64 * 3), ("pe", C.c_int32 * 3), ("nmodes", C.c_int32),
         ("c", C.c_double * 3), ("alpha", C.c_double), ("dt", C.c_double), ("seed", C.c_uint64),
         ("thresholds", C.POINTER(C.c_uint64)), ("amp", C.POINTER(C.c_double)),
-        ("phase", C.POINTER(C.c_double)), ("kappa", C.POINTER(C.c_int32)), ("tsteps", C.c_int32),
+        ("phase", C.POINTER(C.c_double)), ("kappa", C.POINTER(C.c_int32)), ("tsteps", C.c_int32), ("burgers", C.c_int32),
     ]
 
 
@@ -117,6 +117,7 @@ class Config:
         s.phase = self.phase.ctypes.data_as(C.POINTER(C.c_double))
         s.kappa = self.kappa.ctypes.data_as(C.POINTER(C.c_int32))
         s.tsteps = int(spec.get("tsteps", 1))
+        s.burgers = int(spec.get("burgers", 0))
         self.s = s
         self.shape = (int(n[2]), int(n[1]), int(n[0])) if dim == 3 else (int(n[0]),)
         self.ntot = int(n[0] * n[1] * n[2])

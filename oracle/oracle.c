@@ -21,6 +21,8 @@
  *     ASYNC_STD is the standard scheme read at delayed levels, Eq. "general_deriv_async".
  *   - time integration: forward Euler (one level of Eq. "time_disc"), or Adams-Bashforth with two (Eq.
  *     "time_ab2") or three levels, started with Euler and then AB2.
+ *   - the viscous Burgers' equation (Sec. 5.1: Eq. "general" with beta_1 = u, beta_2 = alpha; Case 6):
+ *     f = -U_i^n D1 U + alpha D2 U with the same AT D1 and D2, U_i^n the point's own (current) value.
  *   - error: E = U - u_a (Sec. 5.1, Eq. "ana_sol", with the travelling phase read as
  *     sin(kappa (x - c t) + phi)); averages over I, I_I and I_B (Sec. 4).
  *   - adjoint: the literal transpose of the forward step over the stored history.
@@ -73,6 +75,8 @@ typedef struct {
   const double *phase;        /* [dim][nmodes] */
   const int32_t *kappa;       /* [dim][nmodes] */
   int32_t tsteps;             /* time integration: 0 or 1 forward Euler, 2 AB2, 3 AB3 (Eq. "time_disc") */
+  int32_t burgers;            /* 1: the viscous Burgers' equation u_t + u u_x = alpha u_xx (Sec. 5.1, beta_1 = u,
+                                 beta_2 = alpha; Case 6), 1D with c = 0 */
 } orc_cfg;
 
 typedef struct {
@@ -323,6 +327,7 @@ int orc_check(const orc_cfg *g) {
   if (g->tsteps < 0 || g->tsteps > 3) return -1;
   if (g->scheme < 0 || g->scheme > 4) return -1;
   if (g->scheme >= ORC_AT_SPACE2 && (g->order != 2 || g->tsteps > 1)) return -1; /* Cases 2 and 3: CD2, Euler */
+  if (g->burgers != 0 && (g->burgers != 1 || g->dim != 1 || g->c[0] != 0.0 || g->scheme > ORC_AT)) return -1;
   if (g->scheme == ORC_AT_SPACE1 && (g->c[0] != 0.0 || g->c[1] != 0.0 || g->c[2] != 0.0)) return -1;
   if (g->L < 1 || g->L > 8) return -1;
   if (g->nmodes < 1) return -1;
@@ -428,7 +433,8 @@ int orc_rhs(const orc_cfg *g, const double *const *lev, const int32_t *keff, dou
       double d1 = eval_taps(g, lev, x, y, z, a, taps, nt1);
       int nt2 = point_taps(g, keff, x, y, z, a, 2, taps);
       double d2 = eval_taps(g, lev, x, y, z, a, taps, nt2);
-      f = f + (-g->c[a] * d1 + g->alpha * d2);
+      const double beta1 = g->burgers ? lev[0][pt] : g->c[a];  /* Burgers: the advecting speed is u itself */
+      f = f + (-beta1 * d1 + g->alpha * d2);
     }
     f_out[pt] = f;
   }
@@ -497,9 +503,10 @@ int orc_run(const orc_cfg *g, const double *u0, int64_t nsteps, double *u_out, u
   if (history) memcpy(history, ring, sizeof(double) * (size_t)N);
   /* Multistep start (paper silent): from Eq. "IC" the right-hand sides of the ts-1 levels before t = 0 are
    * those of the analytic solution at t = -m dt (synchronous stencils), so every step uses the full-order
-   * weights; from a caller's field the run starts with Euler, then AB2. */
+   * weights; from a caller's field, and for Burgers' equation (no analytic solution), the run starts with Euler,
+   * then AB2. */
   int prehistory = 0;
-  if (ts > 1 && !u0) {
+  if (ts > 1 && !u0 && !g->burgers) {
     int32_t *zero = (int32_t *)calloc((size_t)nb, sizeof(int32_t));
     double *ua = (double *)malloc(sizeof(double) * (size_t)N);
     if (!zero || !ua) { free(zero); free(ua); free(ring); free(fring); free(keff); free(lev); return -2; }
@@ -585,7 +592,7 @@ int orc_error_stats(const orc_cfg *g, const double *u, int64_t n, double *out) {
  * lambda^n_i through the identity part of the Euler step.  dJ/dalpha = sum_n dt <lambda^{n+1}, D2 U>. */
 int orc_adjoint(const orc_cfg *g, const double *u0, int64_t nsteps, const double *u_target, double *grad_u0,
                 double *grad_alpha, double *J) {
-  if (orc_check(g) || nsteps < 0 || g->tsteps > 1) return -1; /* the adjoint covers forward Euler */
+  if (orc_check(g) || nsteps < 0 || g->tsteps > 1 || g->burgers) return -1; /* forward Euler, linear equation */
   const int T = orc_time_width(g->order, g->scheme);
   const int64_t N = ntot(g), nb = orc_num_sides(g);
   const int64_t nx = g->n[0], ny = g->n[1], nz = g->n[2];

@@ -1,0 +1,56 @@
+"""The oracle's viscous Burgers' equation (Sec. 5.1, Eq. "general" with beta_1 = u, beta_2 = alpha; Case 6)
+against exact Cole-Hopf solutions: the reference is pinned to the PDE, and the runs converge at the design order of
+their stencils and time integrator -- with the time-expanded AT rows also under delays (Fig. "at-ord4-nl"), while
+the standard scheme read at delayed levels drops to first order.  CPU only."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from burgers_exact import cole_hopf
+
+ALPHA = 0.1
+
+
+def test_cole_hopf_reference_solves_burgers():
+    n, t, dt = 256, 0.3, 1e-5
+    k = np.fft.fftfreq(n, 1.0 / n)
+    u = cole_hopf(n, t, ALPHA)
+    ut = (cole_hopf(n, t + dt, ALPHA) - cole_hopf(n, t - dt, ALPHA)) / (2 * dt)
+    uh = np.fft.fft(u)
+    ux = np.fft.ifft(1j * k * uh).real
+    uxx = np.fft.ifft(-(k ** 2) * uh).real
+    assert np.abs(ut + u * ux - ALPHA * uxx).max() < 1e-7 * np.abs(ut).max()
+
+
+def _error(order, tsteps, scheme, probs, n, t_final=0.2):
+    spec, _ = W.wl_1d(n, 16, order, 3, 0, 7, (1,), scheme=scheme, c=0.0, alpha=ALPHA, r_alpha=0.05, probs=probs,
+                      tsteps=tsteps)
+    spec["burgers"] = 1
+    steps = W.steps_to(spec, t_final)
+    u, _, _ = oracle.run(oracle.Config(spec), steps, want_log=False, threads=4, u0=cole_hopf(n, 0.0, ALPHA))
+    return np.sqrt(np.mean((u - cole_hopf(n, steps * spec["dt"], ALPHA)) ** 2))
+
+
+@pytest.mark.parametrize("order,tsteps,scheme,probs,slope,tol", [
+    (2, 1, W.SYNC, None, -2.0, 0.1),
+    (4, 2, W.SYNC, None, -4.0, 0.15),
+    (4, 2, W.AT, (0.7, 0.2, 0.1), -4.0, 0.15),
+    (4, 2, W.AT, (0.3, 0.5, 0.2), -4.0, 0.15),
+    (4, 2, W.ASYNC_STD, (0.3, 0.5, 0.2), -1.0, 0.15),
+])
+def test_burgers_converges_at_the_design_order(order, tsteps, scheme, probs, slope, tol):
+    ns = (64, 128, 256)
+    errs = [_error(order, tsteps, scheme, probs, n) for n in ns]
+    assert abs(np.polyfit(np.log(ns), np.log(errs), 1)[0] - slope) < tol, errs
+
+
+def test_burgers_is_rejected_where_it_is_not_defined():
+    spec, _ = W.wl_1d(64, 4, 4, 3, 0, 1, (1,), c=1.0)
+    spec["burgers"] = 1  # c must be 0: the advecting speed is u
+    with pytest.raises(ValueError):
+        oracle.Config(spec)
+    spec, _ = W.wl_3d([8, 8, 8], [2, 2, 2], 2, 3, 0, 2, c=(0.0, 0.0, 0.0))
+    spec["burgers"] = 1  # one-dimensional only
+    with pytest.raises(ValueError):
+        oracle.Config(spec)
