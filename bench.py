@@ -156,7 +156,10 @@ def launches_per_run(spec, T: int) -> int:
     error statistics."""
     dim, ts = spec["dim"], time_levels(spec)
     wave = 1 if dim == 1 else 2
-    reset = wave + 1 + (((ts - 1) * (wave + 1) + 1) if ts > 1 else 0)
+    if spec.get("burgers", 0):  # no analytic pre-history: the history counter only
+        reset = wave + 1 + (1 if ts > 1 else 0)
+    else:
+        reset = wave + 1 + (((ts - 1) * (wave + 1) + 1) if ts > 1 else 0)
     chunks = T // 50
     step = (1 + 51 * chunks if chunks else 0) + (T - 50 * chunks)
     stats = 2 if dim == 1 else 3
@@ -395,6 +398,12 @@ def main():
     launch = autotune.tune_forward(solver, spec, use_cache=not args.retune)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device=f"cuda:{local}")  # 512 MiB > L2
     kern_ev = []
+    burgers = bool(spec.get("burgers", 0))
+    # Burgers' equation has no analytic solution: its run reports the statistics of U^T - U^0 (the RMS change)
+    u_ic = solver.field().clone() if burgers else None
+
+    def stats():
+        return solver.error_stats_ref(u_ic, 1) if burgers else solver.error_stats()
 
     def one_step(record=False):
         flush.zero_()
@@ -404,7 +413,7 @@ def main():
         e0.record(stream)
         solver.step(T)
         e1.record(stream)
-        st = solver.error_stats()  # blocks
+        st = stats()  # blocks
         if record:
             kern_ev.append((e0, e1))
         return st
@@ -448,7 +457,7 @@ def main():
         u0_dev.copy_(u0_host, non_blocking=True)
         solver.reset(u0_dev)
         solver.step(T)
-        st = solver.error_stats()
+        st = stats()
         out_host.copy_(solver.field().reshape(-1), non_blocking=True)
         torch.cuda.synchronize()
         return st
@@ -497,7 +506,7 @@ def main():
                         "d2h_bytes_per_step": 8 * ntot + 8 * 9},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
                 "gpu_launches": args.steps * launches_per_run(spec, T),
-                "final_rms_error": last["rms"]}
+                ("final_rms_change" if burgers else "final_rms_error"): last["rms"]}
         print(json.dumps(line), flush=True)
     solver.close()
     if world > 1:

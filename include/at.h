@@ -122,6 +122,10 @@ typedef struct {
                     * from Eq. "IC" takes the right-hand sides of the tsteps-1 levels before t = 0 from the analytic
                     * solution (central differences), so every step has full order; from a caller's field
                     * (at_reset with u0_dev) it starts with forward Euler and raises the order step by step. */
+  int32_t burgers; /* 0: u_t + c . grad u = alpha lap u; 1: the viscous Burgers' equation u_t + u u_x = alpha u_xx
+                    * (Sec. 5.1, Eq. "general" with beta_1 = u, beta_2 = alpha; Case 6): 1D, c = 0, schemes AT_SYNC,
+                    * AT_ASYNC_STD or AT_AT; D1 and D2 use the same AT stencils, u_i is the point's current value.
+                    * A multistep Burgers run starts with forward Euler (there is no analytic pre-history). */
 } at_config_t;
 
 typedef struct at_handle at_handle_t;
@@ -175,6 +179,14 @@ typedef struct {
   int64_t n_I, n_B, step;
 } at_stats_t;
 int at_error_stats(at_handle_t *hd, at_stats_t *out);
+
+/* The statistics of E = U^n - V for a caller's reference field V (device, 16-byte aligned) on a grid `refine`
+ * (>= 1) times finer on every axis of the problem -- n0*refine x n1*refine x n2*refine doubles for dim 3,
+ * n0*refine for dim 1 -- sampled at the coarse points (V at (refine x, refine y, refine z)); ua_rms is the RMS of
+ * the sampled reference.  The paper measures its Burgers runs (no analytic solution) this way, against a finer
+ * run.  at_error_stats rejects Burgers problems (AT_ERR_ARG); this entry point takes any problem.  Blocks.
+ * Errors: AT_ERR_ARG, AT_ERR_CUDA, AT_ERR_NONFINITE. */
+int at_error_stats_ref(at_handle_t *hd, const double *ref_dev, int32_t refine, at_stats_t *out);
 
 /* The statistics of at_error_stats for a field the caller holds (u_dev: device, n0*n1*n2 doubles of the problem
  * cfg at step `step`, t = step * dt), computed without allocating anything.  The paper has no counterpart: this

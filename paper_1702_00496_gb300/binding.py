@@ -25,6 +25,7 @@ EXPORTS = (
     "at_error_stats_noalloc",
     "at_adjoint_workspace", "at_adjoint_forward", "at_adjoint_backward",
     "at_ensemble_sizes", "at_ensemble_create", "at_ensemble_run", "at_ensemble_stats", "at_ensemble_destroy",
+    "at_error_stats_ref",
 )
 
 
@@ -46,7 +47,8 @@ class at_config_t(C.Structure):
                 ("n", C.c_int64 * 3), ("pe", C.c_int32 * 3), ("nmodes", C.c_int32),
                 ("c", C.c_double * 3), ("alpha", C.c_double), ("dt", C.c_double), ("seed", C.c_uint64),
                 ("thresholds", C.POINTER(C.c_uint64)), ("amp", C.POINTER(C.c_double)),
-                ("phase", C.POINTER(C.c_double)), ("kappa", C.POINTER(C.c_int32)), ("tsteps", C.c_int32)]
+                ("phase", C.POINTER(C.c_double)), ("kappa", C.POINTER(C.c_int32)), ("tsteps", C.c_int32),
+                ("burgers", C.c_int32)]
 
 
 class at_member_t(C.Structure):
@@ -100,6 +102,7 @@ def load(build_if_missing: bool = True):
     L.at_set_launch.argtypes = [vp, i32, i32]
     L.at_state.argtypes = [vp, C.POINTER(i64), C.POINTER(vp)]
     L.at_error_stats.argtypes = [vp, C.POINTER(at_stats_t)]
+    L.at_error_stats_ref.argtypes = [vp, vp, i32, C.POINTER(at_stats_t)]
     L.at_destroy.argtypes = [vp]
     L.at_last_error.restype = C.c_char_p
     L.at_error_stats_noalloc.argtypes = [C.POINTER(at_config_t), vp, i64, vp, C.POINTER(at_stats_t)]
@@ -190,6 +193,7 @@ class Config:
         s.phase = self.phase.ctypes.data_as(C.POINTER(C.c_double))
         s.kappa = self.kappa.ctypes.data_as(C.POINTER(C.c_int32))
         s.tsteps = int(spec.get("tsteps", 1))
+        s.burgers = int(spec.get("burgers", 0))
         self.s = s
         self.tsteps = max(1, s.tsteps)
         self.dim = dim
@@ -251,6 +255,13 @@ def at_state(h):
 def at_error_stats(h) -> dict:
     st = at_stats_t()
     _check(load().at_error_stats(h, C.byref(st)), "at_error_stats")
+    return st.as_dict()
+
+
+def at_error_stats_ref(h, ref, refine: int) -> dict:
+    """Statistics of U^n - V for a reference field V (CUDA float64 tensor) `refine` times finer on every axis."""
+    st = at_stats_t()
+    _check(load().at_error_stats_ref(h, C.c_void_p(ref.data_ptr()), int(refine), C.byref(st)), "at_error_stats_ref")
     return st.as_dict()
 
 

@@ -494,6 +494,7 @@ static int adjoint_supported(const at_handle *hd) {
   if (hd->sp.ts > 1) return fail(AT_ERR_ARG, "adjoint: only forward Euler (tsteps 0 or 1) is supported");
   if (hd->sp.h > 2) return fail(AT_ERR_ARG, "adjoint: only orders 2 and 4 are supported");
   if (hd->sp.scheme >= AT_AT_SPACE2) return fail(AT_ERR_ARG, "adjoint: the rows expanded in space are not supported");
+  if (hd->sp.burgers) return fail(AT_ERR_ARG, "adjoint: Burgers' equation is not supported (linear equation only)");
   return AT_OK;
 }
 

@@ -42,6 +42,8 @@ int check_config(const at_config_t *c) {
     return fail(AT_ERR_ARG, "scheme must be AT_SYNC, AT_ASYNC_STD, AT_AT, AT_AT_SPACE2 or AT_AT_SPACE1");
   if (c->scheme >= AT_AT_SPACE2 && (c->order != 2 || c->tsteps > 1))
     return fail(AT_ERR_ARG, "the rows expanded in space are second-order schemes with forward Euler (Cases 2, 3)");
+  if (c->burgers != 0 && (c->burgers != 1 || c->dim != 1 || c->c[0] != 0.0 || c->scheme > AT_AT))
+    return fail(AT_ERR_ARG, "burgers: 1D, c = 0 (the advecting speed is u) and scheme AT_SYNC, AT_ASYNC_STD or AT_AT");
   if (c->scheme == AT_AT_SPACE1 && (c->c[0] != 0.0 || c->c[1] != 0.0 || c->c[2] != 0.0))
     return fail(AT_ERR_ARG, "(2,1,2) gives only a second derivative: AT_AT_SPACE1 needs c = 0 (diffusion)");
   if (c->L < 1 || c->L > AT_MAX_L) return fail(AT_ERR_ARG, "L must be in 1..8");
@@ -154,6 +156,7 @@ int at_prepare_params(const at_config_t *cfg, double *ring_dev, uint8_t *log_dev
   p.nb = sides_of(cfg);
   p.dim = cfg->dim; p.h = h; p.T = T; p.R = cfg->L + T; p.L = cfg->L; p.scheme = cfg->scheme;
   p.ts = time_levels(cfg);
+  p.burgers = cfg->burgers;
   p.frhs = p.ts > 1 && ring_dev ? ring_dev + (int64_t)p.R * p.ntot : nullptr;
   // Adams-Bashforth weights of dt f^{n-m} with l = 1, 2, 3 stored levels (Eq. "time_ab2" for two levels; the
   // three-level weights are the standard ones)
@@ -175,6 +178,10 @@ int at_prepare_params(const at_config_t *cfg, double *ring_dev, uint8_t *log_dev
       const double v = cfg->dt * (-cfg->c[a] * c1.cd[j + h] / dx + cfg->alpha * c2.cd[j + h] / (dx * dx));
       const double dv = cfg->dt * c2.cd[j + h] / (dx * dx);
       if (j == 0) { s0 += v; q0 += dv; p.sc[a] = v; } else { p.s[a][j + h] = v; p.q[a][j + h] = dv; }
+      if (a == 0) {
+        p.b1[j + h] = cfg->dt * c1.cd[j + h] / dx;
+        p.b2[j + h] = cfg->dt * cfg->alpha * c2.cd[j + h] / (dx * dx);
+      }
     }
     if (cfg->scheme >= AT_AT_SPACE2 && cfg->pe[a] > 1 && (rc = space_rows(cfg, a, dx, &p)) != AT_OK) return rc;
   }
@@ -297,7 +304,7 @@ extern "C" int at_init(const at_config_t *cfg, double *ring_dev, int64_t ring_le
   p.ab_first = hd->d_step + 1;
   if ((e = cudaMemsetAsync(hd->d_status, 0, sizeof(int32_t), hd->stream)) != cudaSuccess ||
       (e = launch_wave_field(w, 0.0, hd->d_tables, ring_dev, hd->stream)) != cudaSuccess ||
-      (e = ab_start(hd, true)) != cudaSuccess ||
+      (e = ab_start(hd, cfg->burgers == 0)) != cudaSuccess ||
       (e = launch_draw_delays(p, 0, hd->stream)) != cudaSuccess) {
     cudaFree(hd->scratch);
     delete hd;
@@ -362,7 +369,7 @@ extern "C" int at_reset(at_handle_t *hd, const double *u0_dev) {
                         hd->stream);
   else
     e = launch_wave_field(hd->wp, 0.0, hd->d_tables, hd->sp.ring, hd->stream);
-  if (e == cudaSuccess) e = ab_start(hd, u0_dev == nullptr);
+  if (e == cudaSuccess) e = ab_start(hd, u0_dev == nullptr && hd->cfg.burgers == 0);
   if (e == cudaSuccess) e = launch_draw_delays(hd->sp, 0, hd->stream);
   if (e != cudaSuccess) return cuda_fail(e, "at_reset");
   hd->step = 0;
@@ -401,16 +408,34 @@ extern "C" int at_state(at_handle_t *hd, int64_t *step, double **field_dev) {
   return AT_OK;
 }
 
+static int finish_stats(at_handle *hd, at_stats_t *out, const char *where);
+
 extern "C" int at_error_stats(at_handle_t *hd, at_stats_t *out) {
   if (!hd || !out) return fail(AT_ERR_ARG, "at_error_stats: bad argument");
+  if (hd->cfg.burgers) return fail(AT_ERR_ARG, "at_error_stats: Burgers' equation has no analytic solution here "
+                                              "(use at_error_stats_ref with a finer run)");
   const double *u = hd->sp.ring + (hd->step % hd->sp.R) * hd->sp.ntot;
   const double t = (double)hd->step * hd->cfg.dt;
   cudaError_t e = launch_error_stats(hd->wp, hd->sp, u, t, hd->d_tables, hd->d_partials, hd->d_result, hd->stream);
   if (e != cudaSuccess) return cuda_fail(e, "at_error_stats: launch");
+  return finish_stats(hd, out, "at_error_stats");
+}
+
+extern "C" int at_error_stats_ref(at_handle_t *hd, const double *ref_dev, int32_t refine, at_stats_t *out) {
+  if (!hd || !out || !ref_dev || refine < 1) return fail(AT_ERR_ARG, "at_error_stats_ref: bad argument");
+  const double *u = hd->sp.ring + (hd->step % hd->sp.R) * hd->sp.ntot;
+  cudaError_t e = launch_error_stats_ref(hd->wp, hd->sp, u, ref_dev, refine, hd->d_partials, hd->d_result,
+                                         hd->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "at_error_stats_ref: launch");
+  return finish_stats(hd, out, "at_error_stats_ref");
+}
+
+static int finish_stats(at_handle *hd, at_stats_t *out, const char *where) {
+  cudaError_t e;
   double r[AT_STAT_FIELDS];
   if ((e = cudaMemcpyAsync(r, hd->d_result, sizeof(r), cudaMemcpyDeviceToHost, hd->stream)) != cudaSuccess ||
       (e = cudaStreamSynchronize(hd->stream)) != cudaSuccess)
-    return cuda_fail(e, "at_error_stats: copy");
+    return cuda_fail(e, where);
   const double N = (double)hd->sp.ntot;
   out->rms = std::sqrt(r[0] / N);
   out->max_abs = r[1];
@@ -422,7 +447,8 @@ extern "C" int at_error_stats(at_handle_t *hd, at_stats_t *out) {
   out->n_I = (int64_t)r[7];
   out->n_B = (int64_t)r[8];
   out->step = hd->step;
-  if (!std::isfinite(out->rms) || !std::isfinite(out->max_abs)) return fail(AT_ERR_NONFINITE, "at_error_stats: non-finite error");
+  if (!std::isfinite(out->rms) || !std::isfinite(out->max_abs)) return fail(AT_ERR_NONFINITE, "non-finite error");
+  (void)where;
   return AT_OK;
 }
 

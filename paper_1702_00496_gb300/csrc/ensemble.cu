@@ -320,6 +320,7 @@ extern "C" int at_ensemble_sizes(const at_config_t *members, const at_member_t *
     if ((rc = at_num_sides(members + r, &nb))) return rc;
     if (members[r].dim != 1 || members[r].n[0] % 4 || (members[r].pe[0] > 1 && (members[r].n[0] / members[r].pe[0]) % 4))
       return fail(AT_ERR_ARG, "ensemble members must be 1D with N and the PE width multiples of 4");
+    if (members[r].burgers) return fail(AT_ERR_ARG, "ensemble: Burgers' members are not supported (no analytic error)");
     const at_member_t &u = runs[r];
     if (u.nsteps < 0 || u.nsteps > 0xFFFFFFFFll) return fail(AT_ERR_ARG, "ensemble: nsteps must be in 0..2^32-1");
     if (u.group < -1) return fail(AT_ERR_ARG, "ensemble: group must be >= -1");

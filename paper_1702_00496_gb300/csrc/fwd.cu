@@ -79,6 +79,14 @@ __global__ void __launch_bounds__(512) forward_point_kernel(const StepParams p, 
   for (int64_t i = tid; i < p.ntot; i += nthreads) {
     int c[3];
     point_coords(p, DIM, i, c);
+    if (DIM == 1 && p.burgers) {
+      double r[1] = {point_update_burgers<H, LdgNC>(p, keff, un, n, i)};
+      const double u[1] = {un[i]};
+      if (AB) ab_combine<1>(p, n, i, u, r);
+      else r[0] = u[0] + r[0];
+      out[i] = r[0];
+      continue;
+    }
     double r[1] = {(H == 1 && p.scheme >= AT_AT_SPACE2) ? point_update_space<DIM, LdgNC>(p, keff, un, n, i, c)
                                                         : point_update<DIM, H, LdgNC>(p, keff, un, n, i, c)};
     if (AB) {

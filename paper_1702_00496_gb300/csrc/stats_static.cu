@@ -49,6 +49,7 @@ extern "C" int at_error_stats_noalloc(const at_config_t *cfg, const double *u_de
   int rc = at_ring_slots(cfg, &R);  // validates cfg; host only, allocates nothing
   if (rc) return rc;
   if (!u_dev || !out || step < 0) return fail(AT_ERR_ARG, "at_error_stats_noalloc: bad argument");
+  if (cfg->burgers) return fail(AT_ERR_ARG, "at_error_stats_noalloc: Burgers' equation has no analytic solution here");
   if (cfg->dim == 3 && cfg->n[0] + cfg->n[1] + cfg->n[2] > kMaxTables)
     return fail(AT_ERR_ARG, "at_error_stats_noalloc: n[0]+n[1]+n[2] exceeds 24576 (the static scratch limit)");
   int dev = 0;

@@ -272,6 +272,79 @@ __device__ double point_update(const StepParams &p, const uint8_t *__restrict__ 
   return acc;
 }
 
+// Viscous Burgers' equation (1D, Case 6): dt f = -u_i (dt D1 u) + dt alpha D2 u with the same x window and the
+// same extrapolated halo values as the linear step; r receives dt f^n of the four points x0..x0+3, uc their
+// level-n values.  Each derivative is its own FMA chain; u_i enters through the final FMA.
+template <int H, class LD>
+__device__ __forceinline__ void group_eval_burgers(const StepParams &p, const uint8_t *__restrict__ keff,
+                                                   const double *__restrict__ un, int64_t n, int x0, double r[4],
+                                                   double uc[4]) {
+  constexpr int W = XWin<H>::W, NW = XWin<H>::N;
+  const int nx = p.n[0];
+  const int sn = (int)(n % p.R);
+  const int pidx[3] = {x0 / p.S[0], 0, 0};
+  const int pos0 = x0 - pidx[0] * p.S[0];
+  double v[NW];
+  if (x0 >= W && x0 + 4 + W <= nx) {
+#pragma unroll
+    for (int t = 0; t < NW; t += 2) {
+      const double2 a = LD::ld2(un + x0 - W + t);
+      v[t] = a.x; v[t + 1] = a.y;
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < NW; ++t) v[t] = LD::ld(un + wrap_coord(x0 - W + t, nx));
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) uc[q] = v[W + q];
+  if (p.use_pe[0] && (pos0 < H || pos0 + 3 >= p.S[0] - H)) {
+    const int kl = keff[side_of<1>(p, pidx, 0, 0)], kr = keff[side_of<1>(p, pidx, 0, 1)];
+#pragma unroll
+    for (int t = W - H; t <= W + 3 + H; ++t) {
+      const int rel = pos0 - W + t;
+      const int k = rel < 0 ? kl : (rel >= p.S[0] ? kr : 0);
+      if (k > 0) v[t] = halo_value<LD>(p, wrap_coord(x0 - W + t, nx), sn, k);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    double a1 = fma(p.b1[0], v[q + W - H], p.zero);
+    double a2 = fma(p.b2[H], v[q + W], p.zero);
+#pragma unroll
+    for (int j = -H; j <= H; ++j) {
+      if (j == 0) continue;
+      if (j != -H) a1 = fma(p.b1[j + H], v[q + W + j], a1);
+      a2 = fma(p.b2[j + H], v[q + W + j], a2);
+    }
+    r[q] = fma(-v[q + W], a1, a2);
+  }
+}
+
+// One point of the Burgers step (per-point shapes): dt f^n of point i.
+template <int H, class LD>
+__device__ double point_update_burgers(const StepParams &p, const uint8_t *__restrict__ keff,
+                                       const double *__restrict__ un, int64_t n, int64_t i) {
+  const int c = (int)i;
+  const int pidx[3] = {c / p.S[0], 0, 0};
+  const int pos = c - pidx[0] * p.S[0];
+  const bool edge = p.use_pe[0] && (pos < H || pos >= p.S[0] - H);
+  const double ui = LD::ld(un + i);
+  double a1 = p.zero;
+  double a2 = fma(p.b2[H], ui, p.zero);
+#pragma unroll
+  for (int j = -H; j <= H; ++j) {
+    if (j == 0) continue;
+    const int cj = wrap_coord(c + j, p.n[0]);
+    int k = 0;
+    if (edge && pos + j < 0) k = keff[side_of<1>(p, pidx, 0, 0)];
+    if (edge && pos + j >= p.S[0]) k = keff[side_of<1>(p, pidx, 0, 1)];
+    const double v = k > 0 ? halo_value<LD>(p, cj, (int)(n % p.R), k) : LD::ld(un + cj);
+    a1 = j == -H ? fma(p.b1[0], v, p.zero) : fma(p.b1[j + H], v, a1);
+    a2 = fma(p.b2[j + H], v, a2);
+  }
+  return fma(-ui, a1, a2);
+}
+
 // Rows expanded in space (AT_AT_SPACE2 / AT_AT_SPACE1, order 2): a point at the edge of its PE along a split axis
 // (position 0 or S-1) whose side has delay k > 0 takes that axis's edge row -- in-PE taps at level n, buffer taps
 // at level n-k -- instead of the central taps; every other axis and point keeps the central difference.  One
@@ -342,6 +415,19 @@ template <int DIM, int H, class LD, bool AB>
 __device__ __forceinline__ void group_step(const StepParams &p, const uint8_t *__restrict__ keff,
                                            const double *__restrict__ un, double *__restrict__ out, int64_t n,
                                            int x0, int y, int z) {
+  if (DIM == 1 && p.burgers) {
+    double r[4], uc[4];
+    group_eval_burgers<H, LD>(p, keff, un, n, x0, r, uc);
+    if (AB) {
+      ab_combine<4>(p, n, x0, uc, r);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) r[q] = uc[q] + r[q];
+    }
+    reinterpret_cast<double2 *>(out + x0)[0] = make_double2(r[0], r[1]);
+    reinterpret_cast<double2 *>(out + x0)[1] = make_double2(r[2], r[3]);
+    return;
+  }
   if (H == 1 && !AB && p.scheme >= AT_AT_SPACE2 && group_at_space_edge<DIM>(p, x0, y, z)) {
     const int64_t i0 = (DIM == 3 ? ((int64_t)z * p.n[1] + y) * p.n[0] : 0) + x0;
     int c[3] = {x0, y, z};

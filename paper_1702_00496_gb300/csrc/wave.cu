@@ -53,21 +53,29 @@ __global__ void field_3d_kernel(const WaveParams w, const double *tables, double
   }
 }
 
-template <int DIM>
+// REF = false: E = U - u_a with u_a the analytic solution at time t; REF = true: E = U - V with V a reference field
+// `refine` times finer on every axis, sampled at the coarse points (V at (refine x, refine y, refine z)).
+template <int DIM, bool REF>
 __global__ void __launch_bounds__(256) stats_partial_kernel(const WaveParams w, const StepParams p, const double *u,
-                                                            double t, const double *tables, double *partials) {
+                                                            double t, const double *tables, double *partials,
+                                                            const double *ref, int refine) {
   double acc[AT_STAT_FIELDS];
 #pragma unroll
   for (int f = 0; f < AT_STAT_FIELDS; ++f) acc[f] = 0.0;
   const int64_t nx = w.n[0], ny = w.n[1];
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.ntot; i += (int64_t)gridDim.x * blockDim.x) {
     int c[3] = {(int)i, 0, 0};
-    double ua;
-    if (DIM == 1) {
-      ua = axis_sum(w, 0, c[0], t);
-    } else {
+    if (DIM == 3) {
       const int64_t yz = i / nx;
       c[0] = (int)(i - yz * nx); c[2] = (int)(yz / ny); c[1] = (int)(yz - (int64_t)c[2] * ny);
+    }
+    double ua;
+    if (REF) {
+      const int64_t nxf = nx * refine, nyf = ny * refine;
+      ua = ref[((int64_t)c[2] * refine * nyf + (int64_t)c[1] * refine) * nxf + (int64_t)c[0] * refine];
+    } else if (DIM == 1) {
+      ua = axis_sum(w, 0, c[0], t);
+    } else {
       ua = tables[c[0]] * tables[w.n[0] + c[1]] * tables[w.n[0] + w.n[1] + c[2]];
     }
     bool inB = false;
@@ -139,11 +147,21 @@ cudaError_t launch_error_stats(const WaveParams &w0, const StepParams &p, const 
                                double *partials, double *result, cudaStream_t st) {
   const WaveParams w = at_time(w0, t);
   if (w.dim == 1) {
-    stats_partial_kernel<1><<<AT_STAT_BLOCKS, 256, 0, st>>>(w, p, u, t, tables, partials);
+    stats_partial_kernel<1, false><<<AT_STAT_BLOCKS, 256, 0, st>>>(w, p, u, t, tables, partials, nullptr, 1);
   } else {
     axis_table_kernel<<<8, 256, 0, st>>>(w, t, tables);
-    stats_partial_kernel<3><<<AT_STAT_BLOCKS, 256, 0, st>>>(w, p, u, t, tables, partials);
+    stats_partial_kernel<3, false><<<AT_STAT_BLOCKS, 256, 0, st>>>(w, p, u, t, tables, partials, nullptr, 1);
   }
+  stats_final_kernel<<<1, AT_STAT_BLOCKS, 0, st>>>(partials, result);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_error_stats_ref(const WaveParams &w, const StepParams &p, const double *u, const double *ref,
+                                   int refine, double *partials, double *result, cudaStream_t st) {
+  if (w.dim == 1)
+    stats_partial_kernel<1, true><<<AT_STAT_BLOCKS, 256, 0, st>>>(w, p, u, 0.0, nullptr, partials, ref, refine);
+  else
+    stats_partial_kernel<3, true><<<AT_STAT_BLOCKS, 256, 0, st>>>(w, p, u, 0.0, nullptr, partials, ref, refine);
   stats_final_kernel<<<1, AT_STAT_BLOCKS, 0, st>>>(partials, result);
   return cudaGetLastError();
 }

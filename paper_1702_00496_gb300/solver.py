@@ -59,6 +59,11 @@ class Solver:
     def error_stats(self) -> dict:
         return B.at_error_stats(self.h)
 
+    def error_stats_ref(self, ref: torch.Tensor, refine: int) -> dict:
+        """Statistics of U^n - V for a reference field V `refine` times finer on every axis (e.g. a finer run)."""
+        ref = ref.reshape(-1).to(device=self.device, dtype=torch.float64).contiguous()
+        return B.at_error_stats_ref(self.h, ref, refine)
+
     def adjoint_forward(self, nsteps: int, ckpt_every: int = 0) -> None:
         """Run nsteps from step 0 keeping checkpoints every ckpt_every steps (0: ceil(sqrt(nsteps)))."""
         n = B.at_adjoint_workspace(self.h, nsteps, ckpt_every)

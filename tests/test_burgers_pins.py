@@ -54,3 +54,26 @@ def test_burgers_is_rejected_where_it_is_not_defined():
     spec["burgers"] = 1  # one-dimensional only
     with pytest.raises(ValueError):
         oracle.Config(spec)
+
+
+def test_case6_converges_at_fourth_order_against_a_finer_run():
+    """Fig. "at-ord4-nl": Case 6 (Eq. "IC" with kappa = {3,4,5}, A = {2, 0.5, 1.5}) converges at fourth order
+    against a synchronous run four times finer, at every delay mix, and the delays hardly change the error."""
+    nf, ns = 1024, (64, 128, 256)
+    ref = {}
+    errs = {}
+    for probs in ((1.0, 0.0, 0.0), (0.7, 0.2, 0.1), (0.3, 0.5, 0.2)):
+        errs[probs] = []
+        for n in ns:
+            spec = W.paper_case(6, n, 300, probs)
+            steps = W.steps_to(spec, 0.1)
+            if n not in ref:  # the fine run ends at the same time: its dt is (n/nf)^2 of the coarse one
+                ref[n], _, _ = oracle.run(oracle.Config(W.paper_case(6, nf, 300)), steps * (nf // n) ** 2,
+                                          want_log=False, threads=4)
+            u, _, _ = oracle.run(oracle.Config(spec), steps, want_log=False, threads=4)
+            errs[probs].append(np.sqrt(np.mean((u - ref[n][::nf // n]) ** 2)))
+        e = errs[probs]
+        assert abs(np.log(e[2] / e[1]) / np.log(2) + 4.0) < 0.25, e
+    sync = np.array(errs[(1.0, 0.0, 0.0)])
+    for probs in ((0.7, 0.2, 0.1), (0.3, 0.5, 0.2)):
+        assert np.all(np.abs(np.array(errs[probs]) / sync - 1) < 0.01)

@@ -16,6 +16,7 @@ themselves, not stand-ins for a dataset):
   1d_n16m_case3  the paper's Case 3 scaled to N=2^24, 4096 PEs: CD2 + (1,2,2)a/(2,2,2)a, Euler, L=3, 1000 steps
   1d_n16m_case4  the paper's Case 4 scaled to N=2^24, 4096 PEs: CD4 + (1,4,2)/(2,4,2), AB2, L=3, 1000 steps
   1d_n16m_case5  the paper's Case 5 scaled to N=2^24, 4096 PEs: CD6 + (2,6,2), AB3, L=3, 1000 steps
+  1d_n16m_case6  the paper's Case 6 (viscous Burgers) at N=2^24, 4096 PEs: CD4 + (1,4,2)/(2,4,2), AB2, L=3
 """
 from __future__ import annotations
 
@@ -89,7 +90,7 @@ def workload(name: str, scheme: int = AT):
         return wl_3d(256, 4, 4, 3, 500, 3, scheme)
     if name == "adjoint_256":
         return adjoint_spec(256, 4, 2000)
-    if name in ("1d_n16m_case2", "1d_n16m_case3", "1d_n16m_case4", "1d_n16m_case5"):
+    if name in ("1d_n16m_case2", "1d_n16m_case3", "1d_n16m_case4", "1d_n16m_case5", "1d_n16m_case6"):
         spec = paper_case(int(name[-1]), 1 << 24, 2, (1 / 3, 1 / 3, 1 / 3), P=4096)
         if scheme != AT:
             spec["scheme"] = scheme
@@ -102,18 +103,22 @@ def paper_case(case: int, n: int, seed: int, p0_probs=(1.0, 0.0, 0.0), P: int = 
     L = len(p0_probs), alpha = 0.1, phases random per seed.  Case 1: advection-diffusion, forward Euler, CD2 with
     (1,2,2)b/(2,2,2)b, r_alpha = 0.1 (Fig. "at-ord2-procs").  Case 2: diffusion, forward Euler, CD2 with (2,1,2);
     Case 3: advection-diffusion, forward Euler, CD2 with (1,2,2)a/(2,2,2)a; both at r_alpha = 0.1 (not given for
-    Fig. "at-prob-all"; Case 1's value).  Case 4: advection-diffusion, AB2, CD4 with
+    Fig. "at-prob-all"; Case 1's value).  Case 6: the viscous Burgers' equation u_t + u u_x = alpha u_xx, AB2, CD4
+    with (1,4,2)/(2,4,2), r_alpha = 0.05 (Case 4's), the same initial condition.  Case 4: advection-diffusion, AB2,
+    CD4 with
     (1,4,2)/(2,4,2); Case 5: diffusion, AB3, CD6 with (2,6,2).  The paper does not give c or r_alpha for Cases 4
     and 5: c = 1 (Case 4) or 0 (Case 5), r_alpha = 0.05 (Case 4) or 0.01 (Case 5): with the time-extrapolated
     halos, AB2 and AB3 stay stable at every delay mix only at these smaller steps (the oracle diverges at
     r_alpha = 0.1 / 0.02 when p_0 <= 0.3)."""
     order, tsteps, c, r, scheme = {1: (2, 1, 1.0, 0.1, AT), 2: (2, 1, 0.0, 0.1, AT_SPACE1),
                                    3: (2, 1, 1.0, 0.1, AT_SPACE2), 4: (4, 2, 1.0, 0.05, AT),
-                                   5: (6, 3, 0.0, 0.01, AT)}[case]
+                                   5: (6, 3, 0.0, 0.01, AT), 6: (4, 2, 0.0, 0.05, AT)}[case]
     probs = list(p0_probs)
     spec, _ = wl_1d(n, P, order, len(probs), 0, seed, (3, 4, 5), scheme=scheme, c=c, alpha=0.1, r_alpha=r,
                     probs=probs if len(probs) > 1 else None, tsteps=tsteps)
     spec["amp"] = np.array([[2.0, 0.5, 1.5]])
+    if case == 6:
+        spec["burgers"] = 1  # Case 6: the viscous Burgers' equation, AB2, CD4 with (1,4,2)/(2,4,2)
     return spec
 
 
