@@ -133,10 +133,16 @@ def time_levels(spec) -> int:
 
 def flops_per_update(spec) -> int:
     """FP64 flops per interior point: the merged stencil, 1 multiply + 2*h*dim FMAs (2 flops each); with
-    Adams-Bashforth (ts levels) also the ts FMAs that add the weighted right-hand sides to U^n."""
+    Adams-Bashforth (ts levels) also the ts FMAs that add the weighted right-hand sides to U^n.  Burgers' equation
+    keeps its two derivatives apart (below)."""
     h = spec["order"] // 2
-    f = 1 + 2 * (2 * h * spec["dim"])
     ts = time_levels(spec)
+    if spec.get("burgers", 0):
+        # Burgers: dt D1 u (1 multiply + 2h-1 FMAs), dt alpha D2 u (1 multiply + 2h FMAs), -u_i * D1 + D2 (1 FMA),
+        # then U^n + that (1 add) or the ts Adams-Bashforth FMAs
+        f = 1 + 2 * (2 * h - 1) + 1 + 2 * (2 * h) + 2
+        return f + (2 * ts if ts > 1 else 1)
+    f = 1 + 2 * (2 * h * spec["dim"])
     if ts > 1:
         f += 2 * ts
     return f
