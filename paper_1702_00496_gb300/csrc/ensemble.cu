@@ -88,9 +88,9 @@ __device__ void run_member(const StepParams &p, uint8_t *keff_sh, int64_t nsteps
     if (n + 1 < nsteps) atfd::draw_sides(p, n + 1, threadIdx.x, blockDim.x, keff_sh + ((n + 1) & 1) * p.nb);
     const uint8_t *keff = keff_sh + (n & 1) * p.nb;
     for (int k = threadIdx.x; k < groups; k += blockDim.x)
-      if (SPACE)
-        atfd::group_step<1, H, atfd::LdCoherent, AB>(p, keff, un, out, n, (int)(atfd::group_1d_order(p, k) << 2), 0,
-                                                     0);
+      if (SPACE && p.scheme >= AT_AT_SPACE2)
+        atfd::group_step<1, H, atfd::LdCoherent, AB, 2>(p, keff, un, out, n, (int)(atfd::group_1d_order(p, k) << 2),
+                                                        0, 0);
       else
         atfd::group_update<1, H, atfd::LdCoherent, AB>(p, keff, un, out, n, (int)(atfd::group_1d_order(p, k) << 2),
                                                        0, 0);

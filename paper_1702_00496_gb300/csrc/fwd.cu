@@ -30,7 +30,7 @@ using namespace atfd;
 // Grouped kernel: a thread updates four consecutive x points per iteration (grid-stride); every thread
 // also draws the delays of one slice of the PE sides for step n+1 into the other half of the double-buffered
 // delay array, so the next launch finds them ready.
-template <int DIM, int H, bool AB>
+template <int DIM, int H, bool AB, int KIND>
 __global__ void __launch_bounds__(512) forward_group_kernel(const StepParams p, const int64_t n_off,
                                                             const int64_t *n_base) {
   const int64_t n = n_off + (n_base ? *n_base : 0);
@@ -44,13 +44,13 @@ __global__ void __launch_bounds__(512) forward_group_kernel(const StepParams p, 
   for (int64_t k = tid; k < groups; k += nthreads) {
     if (DIM == 1) {
       const int64_t g = group_1d_order(p, k);
-      group_step<1, H, LdgNC, AB>(p, keff, un, out, n, (int)(g << 2), 0, 0);
+      group_step<1, H, LdgNC, AB, KIND>(p, keff, un, out, n, (int)(g << 2), 0, 0);
     } else {
       const int64_t g = p.order ? (int64_t)p.order[k] : k;
       const int64_t r = g / gx;
       const int x0 = (int)(g - r * gx) << 2;
       const int z = (int)(r / p.n[1]), y = (int)(r - (int64_t)z * p.n[1]);
-      group_step<3, H, LdgNC, AB>(p, keff, un, out, n, x0, y, z);
+      group_step<3, H, LdgNC, AB, KIND>(p, keff, un, out, n, x0, y, z);
     }
   }
 }
@@ -67,7 +67,7 @@ __device__ __forceinline__ void point_coords(const StepParams &p, int dim, int64
 }
 
 // Fallback for shapes the grouped kernel does not take (n[0] not a multiple of 4, odd slots).
-template <int DIM, int H, bool AB>
+template <int DIM, int H, bool AB, int KIND>
 __global__ void __launch_bounds__(512) forward_point_kernel(const StepParams p, const int64_t n_off,
                                                             const int64_t *n_base) {
   const int64_t n = n_off + (n_base ? *n_base : 0);
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(512) forward_point_kernel(const StepParams p, 
   for (int64_t i = tid; i < p.ntot; i += nthreads) {
     int c[3];
     point_coords(p, DIM, i, c);
-    if (DIM == 1 && p.burgers) {
+    if (DIM == 1 && KIND == 1) {
       double r[1] = {point_update_burgers<H, LdgNC>(p, keff, un, n, i)};
       const double u[1] = {un[i]};
       if (AB) ab_combine<1>(p, n, i, u, r);
@@ -87,8 +87,8 @@ __global__ void __launch_bounds__(512) forward_point_kernel(const StepParams p, 
       out[i] = r[0];
       continue;
     }
-    double r[1] = {(H == 1 && p.scheme >= AT_AT_SPACE2) ? point_update_space<DIM, LdgNC>(p, keff, un, n, i, c)
-                                                        : point_update<DIM, H, LdgNC>(p, keff, un, n, i, c)};
+    double r[1] = {(KIND == 2 && H == 1) ? point_update_space<DIM, LdgNC>(p, keff, un, n, i, c)
+                                         : point_update<DIM, H, LdgNC>(p, keff, un, n, i, c)};
     if (AB) {
       const double u[1] = {un[i]};
       ab_combine<1>(p, n, i, u, r);
@@ -156,8 +156,20 @@ bool grouped_shape(const StepParams &p, const void *base) {
 template <int DIM, int H, bool AB>
 void launch_typed(const StepParams &p, bool grouped, int blocks, int threads, int64_t n, const int64_t *n_base,
                   cudaStream_t st) {
-  if (grouped) forward_group_kernel<DIM, H, AB><<<blocks, threads, 0, st>>>(p, n, n_base);
-  else forward_point_kernel<DIM, H, AB><<<blocks, threads, 0, st>>>(p, n, n_base);
+  if (DIM == 1 && p.burgers) {
+    if (grouped) forward_group_kernel<1, H, AB, 1><<<blocks, threads, 0, st>>>(p, n, n_base);
+    else forward_point_kernel<1, H, AB, 1><<<blocks, threads, 0, st>>>(p, n, n_base);
+    return;
+  }
+  if constexpr (H == 1 && !AB) {
+    if (p.scheme >= AT_AT_SPACE2) {  // rows expanded in space: order 2, forward Euler only
+      if (grouped) forward_group_kernel<DIM, 1, false, 2><<<blocks, threads, 0, st>>>(p, n, n_base);
+      else forward_point_kernel<DIM, 1, false, 2><<<blocks, threads, 0, st>>>(p, n, n_base);
+      return;
+    }
+  }
+  if (grouped) forward_group_kernel<DIM, H, AB, 0><<<blocks, threads, 0, st>>>(p, n, n_base);
+  else forward_point_kernel<DIM, H, AB, 0><<<blocks, threads, 0, st>>>(p, n, n_base);
 }
 
 template <int DIM, bool AB>

@@ -410,12 +410,14 @@ __device__ __forceinline__ bool group_at_space_edge(const StepParams &p, int x0,
 }
 
 // One group of the forward step for every scheme: groups holding a PE-edge point of a scheme expanded in space
-// go point by point through its edge rows, all others through the grouped central / time-expanded path.
-template <int DIM, int H, class LD, bool AB>
+// go point by point through its edge rows, all others through the grouped central / time-expanded path.  KIND
+// selects the kernel variant -- 0: central and time-expanded rows, 1: Burgers' equation (1D), 2: rows expanded in
+// space -- so each kernel carries only its own path.
+template <int DIM, int H, class LD, bool AB, int KIND = 0>
 __device__ __forceinline__ void group_step(const StepParams &p, const uint8_t *__restrict__ keff,
                                            const double *__restrict__ un, double *__restrict__ out, int64_t n,
                                            int x0, int y, int z) {
-  if (DIM == 1 && p.burgers) {
+  if (DIM == 1 && KIND == 1) {
     double r[4], uc[4];
     group_eval_burgers<H, LD>(p, keff, un, n, x0, r, uc);
     if (AB) {
@@ -428,7 +430,7 @@ __device__ __forceinline__ void group_step(const StepParams &p, const uint8_t *_
     reinterpret_cast<double2 *>(out + x0)[1] = make_double2(r[2], r[3]);
     return;
   }
-  if (H == 1 && !AB && p.scheme >= AT_AT_SPACE2 && group_at_space_edge<DIM>(p, x0, y, z)) {
+  if (KIND == 2 && H == 1 && !AB && group_at_space_edge<DIM>(p, x0, y, z)) {
     const int64_t i0 = (DIM == 3 ? ((int64_t)z * p.n[1] + y) * p.n[0] : 0) + x0;
     int c[3] = {x0, y, z};
     double r[4];
