@@ -34,9 +34,12 @@ PEAK_FP64_FLOPS = 152 * 2 * 2 * 2.07e9  # 152 SMs x 2 FP64 FMA lanes/clk x 2 flo
 # DRAM bytes (read + write) per launch of the step kernel, the mean of two launches of one ncu capture of the current
 # kernel source (profiles/forward_group_kernel_1d_n16m*.md); None where no capture of the current source exists.
 MEASURED_TRAFFIC = {
-    ("1d_n16m", "forward_group_kernel<1,2,false>"): 136.95e6 + 80.32e6,
-    ("1d_n16m_case4", "forward_group_kernel<1,2,true>"): 271.96e6 + 208.95e6,
-    ("1d_n16m_case5", "forward_group_kernel<1,3,true>"): 409.76e6 + 221.67e6,
+    ("1d_n16m", "forward_group_kernel<1,2,false>"): 136.95e6 + 80.50e6,
+    ("1d_n16m_case2", "forward_group_kernel<1,1,false>"): None,
+    ("1d_n16m_case3", "forward_group_kernel<1,1,false>"): 135.27e6 + 80.13e6,
+    ("1d_n16m_case4", "forward_group_kernel<1,2,true>"): 271.91e6 + 209.17e6,
+    ("1d_n16m_case5", "forward_group_kernel<1,3,true>"): 409.85e6 + 221.76e6,
+    ("1d_n16m_case6", "forward_group_kernel<1,2,true>"): 271.83e6 + 209.14e6,
 }
 
 
