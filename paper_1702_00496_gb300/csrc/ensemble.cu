@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "../../include/at.h"
+#include "modes.cuh"
 #include "stencil.cuh"
 
 namespace {
@@ -39,12 +40,16 @@ struct MemberParams {
   int64_t steps;                   // steps this member runs
   int32_t nmodes, group;           // group: index of the member's summary group
   int32_t twin;                    // member whose final field this one is compared with, or -1
+  // the same modes prepared for the rotation recurrence (when ms_ic.rot), exactly as the single-problem path
+  // prepares them, so a member's fields and statistics carry the same bits: t = 0, t_final, t = -dt, -2 dt
+  ModeSet ms_ic, ms_fin, ms_pre[2];
 };
 
 constexpr int kStatFields = AT_STAT_FIELDS;
 
-__device__ double wave_1d(const MemberParams &m, const double *amp, double shift, int i) {
+__device__ double wave_1d(const MemberParams &m, const ModeSet &ms, const double *amp, double shift, int i) {
   const double x = (double)i * m.dx;
+  if (ms.rot) return atfd::mode_sum(ms, m.nmodes, x);
   double s = 0.0;
   for (int q = 0; q < m.nmodes; ++q) s += amp[q] * sin(m.kappa[q] * (x - shift) + m.phase[q]);
   return s;
@@ -61,7 +66,7 @@ __device__ void member_prehistory(MemberParams &m) {
   __syncthreads();
   if (threadIdx.x == 0) m.p.use_pe[0] = 0;
   for (int mm = 1; mm <= ns; ++mm) {
-    for (int i = threadIdx.x; i < N; i += blockDim.x) tmp[i] = wave_1d(m, m.amp_pre[mm - 1], m.shift_pre[mm - 1], i);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tmp[i] = wave_1d(m, m.ms_pre[mm - 1], m.amp_pre[mm - 1], m.shift_pre[mm - 1], i);
     __syncthreads();
     double *out = m.p.frhs + (int64_t)(((-mm) % ns + ns) % ns) * m.p.ntot;
     for (int k = threadIdx.x; k < (N >> 2); k += blockDim.x) {
@@ -122,7 +127,7 @@ __global__ void __launch_bounds__(1024, 1) ensemble_kernel(const MemberParams *_
     }
     __syncthreads();
     const int N = m.p.n[0];
-    for (int i = threadIdx.x; i < N; i += blockDim.x) m.p.ring[i] = wave_1d(m, m.amp, 0.0, i);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) m.p.ring[i] = wave_1d(m, m.ms_ic, m.amp, 0.0, i);
     __syncthreads();
     if (AB && m.p.ts > 1) {
       if (m.p.h == 1) member_prehistory<1>(m);
@@ -142,7 +147,7 @@ __global__ void __launch_bounds__(1024, 1) ensemble_kernel(const MemberParams *_
 #pragma unroll
     for (int f = 0; f < kStatFields; ++f) acc[f] = 0.0;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
-      const double ua = wave_1d(m, m.amp_final, m.shift_final, i);
+      const double ua = wave_1d(m, m.ms_fin, m.amp_final, m.shift_final, i);
       const int pos = i % m.p.S[0];
       const bool inB = m.p.use_pe[0] && (pos < m.p.h || pos >= m.p.S[0] - m.p.h);
       const double e = u[i] - ua;
@@ -381,6 +386,10 @@ extern "C" int at_ensemble_create(const at_config_t *members, const at_member_t 
         m.amp_pre[mm - 1][q] = c.amp[q] * std::exp(c.alpha * m.kappa[q] * m.kappa[q] * (double)mm * c.dt);
     }
     for (int mm = 1; mm <= 2; ++mm) m.shift_pre[mm - 1] = -c.c[0] * (double)mm * c.dt;
+    fill_modes(&m.ms_ic, m.amp, m.phase, m.kappa, c.nmodes, c.alpha, c.c[0], 0.0);
+    fill_modes(&m.ms_fin, m.amp, m.phase, m.kappa, c.nmodes, c.alpha, c.c[0], tf);
+    for (int mm = 1; mm <= 2; ++mm)
+      fill_modes(&m.ms_pre[mm - 1], m.amp, m.phase, m.kappa, c.nmodes, c.alpha, c.c[0], -(double)mm * c.dt);
     m.group = groups[key_of(r)];
     m.steps = nsteps;
     m.twin = runs[r].twin;

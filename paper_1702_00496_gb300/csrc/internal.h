@@ -12,6 +12,7 @@
 #define AT_MAX_H 3
 #define AT_MAX_MODES 16
 #define AT_MAX_ETAPS 8
+#define AT_MAX_KROT 64
 #define AT_STAT_FIELDS 9
 #define AT_STAT_BLOCKS 1024
 
@@ -66,6 +67,17 @@ struct StepParams {
   double b2[2 * AT_MAX_H + 1];    // Burgers: dt alpha cd2_j / dx^2
 };
 
+// The modes of one axis at one time t, prepared on the host for the rotation recurrence: sorted by wavenumber,
+// with A exp(-alpha kappa^2 t) and the phase phi - kappa c t folded into ac = A cos(.), as = A sin(.).  rot = 1 when
+// every wavenumber is an integer in 1..AT_MAX_KROT (else the sines are evaluated one by one).
+struct ModeSet {
+  int32_t rot, kmax;
+  int32_t kr[AT_MAX_MODES];
+  double ac[AT_MAX_MODES], as[AT_MAX_MODES];
+};
+void fill_modes(ModeSet *ms, const double *amp, const double *phase, const double *kappa, int nmodes, double alpha,
+                double c, double t);
+
 // Initial-condition / analytic-solution parameters.
 struct WaveParams {
   int32_t dim, nmodes;
@@ -76,6 +88,7 @@ struct WaveParams {
   double amp[3][AT_MAX_MODES];
   double phase[3][AT_MAX_MODES];
   double kappa[3][AT_MAX_MODES];
+  ModeSet ms[3];  // per axis, filled by the launchers for the time of the launch (fill_modes)
 };
 
 // Validate cfg and fill the step parameters (merged taps, extrapolation weights, delay process) for a problem

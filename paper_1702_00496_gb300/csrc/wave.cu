@@ -8,14 +8,18 @@
 //                      AT_STAT_BLOCKS blocks, per-block partials, then one block reduces them in a fixed
 //                      order, so the result is deterministic.
 #include <cmath>
+#include <utility>
 
 #include "internal.h"
+#include "modes.cuh"
 
 namespace {
 
-// w.amp holds A exp(-alpha kappa^2 t) for the time t of the launch (scaled on the host).
+// Sum over the modes of axis a at grid point i, for the time t of the launch (w.amp holds A exp(-alpha kappa^2 t),
+// scaled on the host): the rotation recurrence for integer wavenumbers, else a sine per mode.
 __device__ __forceinline__ double axis_sum(const WaveParams &w, int a, int i, double t) {
   const double x = (double)i * w.dx[a];
+  if (w.ms[a].rot) return atfd::mode_sum(w.ms[a], w.nmodes, x);
   const double shift = w.c[a] * t;
   double s = 0.0;
   for (int q = 0; q < w.nmodes; ++q) s += w.amp[a][q] * sin(w.kappa[a][q] * (x - shift) + w.phase[a][q]);
@@ -24,6 +28,10 @@ __device__ __forceinline__ double axis_sum(const WaveParams &w, int a, int i, do
 
 WaveParams at_time(const WaveParams &w0, double t) {
   WaveParams w = w0;
+  for (int a = 0; a < 3; ++a) {
+    if (a < w.dim) fill_modes(&w.ms[a], w0.amp[a], w0.phase[a], w0.kappa[a], w.nmodes, w0.alpha, w0.c[a], t);
+    else w.ms[a].rot = 0;
+  }
   for (int a = 0; a < w.dim; ++a)
     for (int q = 0; q < w.nmodes; ++q)
       if (t != 0.0) w.amp[a][q] = w0.amp[a][q] * std::exp(-w0.alpha * w0.kappa[a][q] * w0.kappa[a][q] * t);
@@ -128,6 +136,31 @@ __global__ void __launch_bounds__(AT_STAT_BLOCKS) stats_final_kernel(const doubl
 }
 
 }  // namespace
+
+void fill_modes(ModeSet *ms, const double *amp, const double *phase, const double *kappa, int nmodes, double alpha,
+                double c, double t) {
+  int idx[AT_MAX_MODES];
+  bool ok = nmodes >= 1 && nmodes <= AT_MAX_MODES;
+  for (int q = 0; ok && q < nmodes; ++q) {
+    idx[q] = q;
+    ok = kappa[q] >= 1.0 && kappa[q] <= (double)AT_MAX_KROT && kappa[q] == std::floor(kappa[q]);
+  }
+  ms->rot = ok ? 1 : 0;
+  ms->kmax = 0;
+  if (!ok) return;
+  for (int q = 1; q < nmodes; ++q)  // insertion sort of the modes by wavenumber (stable)
+    for (int r = q; r > 0 && kappa[idx[r - 1]] > kappa[idx[r]]; --r) std::swap(idx[r - 1], idx[r]);
+  for (int q = 0; q < nmodes; ++q) {
+    const int m = idx[q];
+    const double k = kappa[m];
+    const double A = t != 0.0 ? amp[m] * std::exp(-alpha * k * k * t) : amp[m];
+    const double ph = phase[m] - k * c * t;
+    ms->kr[q] = (int32_t)k;
+    ms->ac[q] = A * std::cos(ph);
+    ms->as[q] = A * std::sin(ph);
+    if ((int32_t)k > ms->kmax) ms->kmax = (int32_t)k;
+  }
+}
 
 cudaError_t launch_wave_field(const WaveParams &w0, double t, double *tables, double *out, cudaStream_t st) {
   const WaveParams w = at_time(w0, t);
