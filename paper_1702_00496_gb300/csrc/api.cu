@@ -447,8 +447,11 @@ static int finish_stats(at_handle *hd, at_stats_t *out, const char *where) {
   out->n_I = (int64_t)r[7];
   out->n_B = (int64_t)r[8];
   out->step = hd->step;
-  if (!std::isfinite(out->rms) || !std::isfinite(out->max_abs)) return fail(AT_ERR_NONFINITE, "non-finite error");
-  (void)where;
+  if (!std::isfinite(out->rms) || !std::isfinite(out->max_abs)) {
+    char buf[120];
+    std::snprintf(buf, sizeof(buf), "%s: non-finite error", where);
+    return fail(AT_ERR_NONFINITE, buf);
+  }
   return AT_OK;
 }
 
