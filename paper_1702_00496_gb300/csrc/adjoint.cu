@@ -148,18 +148,21 @@ __device__ __forceinline__ void adjoint_group(const AdjParams &a, const uint8_t 
     pidx[1] = y / f.S[1]; pos[1] = y - pidx[1] * f.S[1];
     pidx[2] = z / f.S[2]; pos[2] = z - pidx[2] * f.S[2];
   }
-  double lv[8];
-  if (x0 >= 2 && x0 + 6 <= nx) {
-    const double2 l0 = LdgNC::ld2(ln + i0 - 2), l1 = LdgNC::ld2(ln + i0), l2 = LdgNC::ld2(ln + i0 + 2),
-                  l3 = LdgNC::ld2(ln + i0 + 4);
-    lv[0] = l0.x; lv[1] = l0.y; lv[2] = l1.x; lv[3] = l1.y; lv[4] = l2.x; lv[5] = l2.y; lv[6] = l3.x; lv[7] = l3.y;
+  constexpr int W = XWin<H>::W, NW = XWin<H>::N;
+  double lv[NW];
+  if (x0 >= W && x0 + 4 + W <= nx) {
+#pragma unroll
+    for (int t = 0; t < NW; t += 2) {
+      const double2 l = LdgNC::ld2(ln + i0 - W + t);
+      lv[t] = l.x; lv[t + 1] = l.y;
+    }
   } else {
 #pragma unroll
-    for (int t = 0; t < 8; ++t) lv[t] = LdgNC::ld(ln + row + wrap_coord(x0 - 2 + t, nx));
+    for (int t = 0; t < NW; ++t) lv[t] = LdgNC::ld(ln + row + wrap_coord(x0 - W + t, nx));
   }
 #pragma unroll
-  for (int q = 0; q < 4; ++q) galpha = fma(lv[q + 2], d[q], galpha);
-  // x: window element t is point i = x0-2+t; rel < 0 lies in the lower PE (reads c on its high side),
+  for (int q = 0; q < 4; ++q) galpha = fma(lv[q + W], d[q], galpha);
+  // x: window element t is point i = x0-W+t; rel < 0 lies in the lower PE (reads c on its high side),
   // rel >= S in the upper PE (reads c on its low side)
   int kxl = 0, kxr = 0;
   if (f.use_pe[0]) {
@@ -172,13 +175,13 @@ __device__ __forceinline__ void adjoint_group(const AdjParams &a, const uint8_t 
   int kX[4] = {kxl, kxr, 0, 0};
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    A[q] = fma(f.s0, lv[q + 2], f.zero);
+    A[q] = fma(f.s0, lv[q + W], f.zero);
     X[0][q] = X[1][q] = X[2][q] = X[3][q] = 0.0;
 #pragma unroll
     for (int j = -H; j <= H; ++j) {
       if (j == 0) continue;
-      const int t = q + 2 - j;
-      const int rel = pos[0] - 2 + t;
+      const int t = q + W - j;
+      const int rel = pos[0] - W + t;
       const double s = f.s[0][j + H];
       if (rel < 0 && kxl > 0) X[0][q] = fma(s, lv[t], X[0][q]);
       else if (rel >= f.S[0] && kxr > 0) X[1][q] = fma(s, lv[t], X[1][q]);
@@ -298,26 +301,26 @@ __global__ void __launch_bounds__(256, AdjBounds<MODE>::min_blocks) adjoint_step
         adjoint_group<DIM, H>(a, keff, n, x0, y, z, galpha);
         continue;
       }
-      double lv[8], uv[8];
-      {
-        const double2 l0 = LdgNC::ld2(ln + i0 - 2), l1 = LdgNC::ld2(ln + i0), l2 = LdgNC::ld2(ln + i0 + 2),
-                      l3 = LdgNC::ld2(ln + i0 + 4);
-        lv[0] = l0.x; lv[1] = l0.y; lv[2] = l1.x; lv[3] = l1.y; lv[4] = l2.x; lv[5] = l2.y; lv[6] = l3.x; lv[7] = l3.y;
+      constexpr int W = XWin<H>::W, NW = XWin<H>::N;
+      double lv[NW], uv[NW];
+#pragma unroll
+      for (int t = 0; t < NW; t += 2) {
+        const double2 l = LdgNC::ld2(ln + i0 - W + t);
+        lv[t] = l.x; lv[t + 1] = l.y;
         if (AL) {
-          const double2 u0 = LdgNC::ld2(un + i0 - 2), u1 = LdgNC::ld2(un + i0), u2 = LdgNC::ld2(un + i0 + 2),
-                        u3 = LdgNC::ld2(un + i0 + 4);
-          uv[0] = u0.x; uv[1] = u0.y; uv[2] = u1.x; uv[3] = u1.y; uv[4] = u2.x; uv[5] = u2.y; uv[6] = u3.x; uv[7] = u3.y;
+          const double2 u = LdgNC::ld2(un + i0 - W + t);
+          uv[t] = u.x; uv[t + 1] = u.y;
         }
       }
       double A[4], D[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        double acc = fma(f.s0, lv[q + 2], f.zero), d = AL ? fma(f.q0, uv[q + 2], f.zero) : 0.0;
+        double acc = fma(f.s0, lv[q + W], f.zero), d = AL ? fma(f.q0, uv[q + W], f.zero) : 0.0;
 #pragma unroll
         for (int j = -H; j <= H; ++j) {
           if (j == 0) continue;
-          acc = fma(f.s[0][j + H], lv[q + 2 - j], acc);
-          if (AL) d = fma(f.q[0][j + H], uv[q + 2 + j], d);
+          acc = fma(f.s[0][j + H], lv[q + W - j], acc);
+          if (AL) d = fma(f.q[0][j + H], uv[q + W + j], d);
         }
         A[q] = acc;
         D[q] = d;
@@ -339,7 +342,7 @@ __global__ void __launch_bounds__(256, AdjBounds<MODE>::min_blocks) adjoint_step
         }
       }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) if (AL) galpha = fma(lv[q + 2], D[q], galpha);
+      for (int q = 0; q < 4; ++q) if (AL) galpha = fma(lv[q + W], D[q], galpha);
       double2 *cur = reinterpret_cast<double2 *>(a.lam + (n % a.Rl) * N + i0);
       if (a.Rl == 2) {
         cur[0] = make_double2(A[0], A[1]);
@@ -412,11 +415,11 @@ bool adjoint_grouped(const AdjParams &a) {
 // Group g (x0 = 4 (g mod nx/4), row g div nx/4) is interior when its cells and all their stencil neighbours lie in
 // its PE and away from the domain ends: the straight path of the interior launch applies.
 bool group_interior(const StepParams &f, int64_t g) {
-  const int h = f.h, nx = (int)f.n[0], gx = nx / 4;
+  const int h = f.h, nx = (int)f.n[0], gx = nx / 4, W = (h + 1) / 2 * 2;  // the x window's half-width
   const int64_t r = g / gx;
   const int x0 = (int)(g - r * gx) * 4;
   const int px = x0 % f.S[0];
-  bool in = x0 >= 2 && x0 + 6 <= nx && (!f.use_pe[0] || (px >= h && px + 3 < f.S[0] - h));
+  bool in = x0 >= W && x0 + 4 + W <= nx && (!f.use_pe[0] || (px >= h && px + 3 < f.S[0] - h));
   if (f.dim == 3) {
     const int z = (int)(r / f.n[1]), y = (int)(r - (int64_t)z * f.n[1]);
     const int py = y % f.S[1], pz = z % f.S[2];
@@ -430,10 +433,12 @@ cudaError_t launch_adjoint_step(const AdjParams &a, int64_t n, int nblk, cudaStr
   const bool grouped = adjoint_grouped(a);
   if (a.f.dim == 1) {
     if (a.f.h == 1) launch_alpha<1, 1>(a, n, nblk, grouped, st);
-    else launch_alpha<1, 2>(a, n, nblk, grouped, st);
+    else if (a.f.h == 2) launch_alpha<1, 2>(a, n, nblk, grouped, st);
+    else launch_alpha<1, 3>(a, n, nblk, grouped, st);
   } else {
     if (a.f.h == 1) launch_alpha<3, 1>(a, n, nblk, grouped, st);
-    else launch_alpha<3, 2>(a, n, nblk, grouped, st);
+    else if (a.f.h == 2) launch_alpha<3, 2>(a, n, nblk, grouped, st);
+    else launch_alpha<3, 3>(a, n, nblk, grouped, st);
   }
   return cudaGetLastError();
 }
@@ -489,10 +494,9 @@ cudaError_t copy_field(double *dst, const double *src, int64_t n, cudaStream_t s
 
 }  // namespace
 
-// The transposed step covers forward Euler with stencils of half-width 1 or 2.
+// The transposed step covers forward Euler with the central and time-expanded rows, orders 2, 4 and 6.
 static int adjoint_supported(const at_handle *hd) {
   if (hd->sp.ts > 1) return fail(AT_ERR_ARG, "adjoint: only forward Euler (tsteps 0 or 1) is supported");
-  if (hd->sp.h > 2) return fail(AT_ERR_ARG, "adjoint: only orders 2 and 4 are supported");
   if (hd->sp.scheme >= AT_AT_SPACE2) return fail(AT_ERR_ARG, "adjoint: the rows expanded in space are not supported");
   if (hd->sp.burgers) return fail(AT_ERR_ARG, "adjoint: Burgers' equation is not supported (linear equation only)");
   return AT_OK;

@@ -35,6 +35,10 @@ CASES = [
     ("1d_point_path", lambda: W.wl_1d(250, 5, 4, 3, 0, 65, (1, 2))[0], 50),
     ("3d_o4", lambda: W.wl_3d([16, 12, 8], [2, 2, 2], 4, 3, 0, 66, c=(0.3, 0.2, 0.1))[0], 20),
     ("3d_o2_unsplit", lambda: W.wl_3d([12, 16, 8], [3, 1, 2], 2, 4, 0, 67, c=(0.2, 0.2, 0.2))[0], 25),
+    ("1d_o6_L3", lambda: W.wl_1d(256, 8, 6, 3, 0, 68, (1, 2, 3), r_alpha=0.02)[0], 60),
+    ("1d_o6_point_path", lambda: W.wl_1d(250, 5, 6, 4, 0, 69, (1, 2), r_alpha=0.02)[0], 50),
+    ("3d_o6", lambda: W.wl_3d([24, 16, 16], [2, 2, 2], 6, 3, 0, 70, c=(0.3, 0.2, 0.1), dt=0.02 * W.dx_of(24) ** 2 / 0.05)[0],
+     20),
 ]
 
 
