@@ -590,9 +590,84 @@ int orc_error_stats(const orc_cfg *g, const double *u, int64_t n, double *out) {
  * the literal transpose of orc_step: every tap c * U^{n-l}_{i+j} of point i at step n sends
  * lambda^{n+1}_i * dt * (-c_a or alpha) * c to lambda^{n-l}_{i+j}, and lambda^{n+1}_i reaches
  * lambda^n_i through the identity part of the Euler step.  dJ/dalpha = sum_n dt <lambda^{n+1}, D2 U>. */
+/* The adjoint of an Adams-Bashforth run started from a caller's field (Euler, then AB2, then AB3; a run from
+ * Eq. "IC" takes its earliest right-hand sides from the analytic solution, which depends on alpha, and is not
+ * covered): U^{n+1} = U^n + dt sum_m beta_m f^{n-m} is transposed literally.  Going back from the last step, step n
+ * adds lambda^{n+1} to lambda^n (identity) and dt beta_m lambda^{n+1} to the adjoint of f^{n-m}; the adjoint of f^n is
+ * then complete and goes back through the taps of f^n to the levels it reads, and dJ/dalpha gains
+ * <adjoint of f^n, sum_a D2_a U>. */
+static int orc_adjoint_ab(const orc_cfg *g, const double *u0, int64_t nsteps, const double *u_target,
+                          double *grad_u0, double *grad_alpha, double *J) {
+  if (!u0) return -1;
+  const int ts = g->tsteps;
+  const int T = orc_time_width(g->order, g->scheme);
+  const int64_t N = ntot(g), nb = orc_num_sides(g);
+  const int64_t nx = g->n[0], ny = g->n[1], nz = g->n[2];
+  double *hist = (double *)malloc(sizeof(double) * (size_t)((nsteps + 1) * N));
+  double *adj = (double *)calloc((size_t)((nsteps + 1) * N), sizeof(double));
+  double *adjf = (double *)calloc((size_t)((nsteps > 0 ? nsteps : 1) * N), sizeof(double));
+  int32_t *keff = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nsteps > 0 ? nsteps * nb : 1));
+  double *ulast = (double *)malloc(sizeof(double) * (size_t)N);
+  if (!hist || !adj || !adjf || !keff || !ulast) {
+    free(hist); free(adj); free(adjf); free(keff); free(ulast);
+    return -2;
+  }
+  if (orc_run(g, u0, nsteps, ulast, NULL, hist)) {
+    free(hist); free(adj); free(adjf); free(keff); free(ulast);
+    return -1;
+  }
+  for (int64_t n = 0; n < nsteps; ++n) draw_delays(g, n, T, NULL, keff + n * nb);
+  double jj = 0.0;
+  for (int64_t i = 0; i < N; ++i) {
+    double r = hist[nsteps * N + i] - u_target[i];
+    jj = jj + 0.5 * r * r;
+    adj[nsteps * N + i] = r;
+  }
+  double ga = 0.0;
+  for (int64_t n = nsteps - 1; n >= 0; --n) {
+    const int32_t *kn = keff + n * nb;
+    double beta[3];
+    const int nl = ab_weights((int)(n + 1 < ts ? n + 1 : ts), beta);
+    for (int64_t i = 0; i < N; ++i) {
+      const double lam = adj[(n + 1) * N + i];
+      adj[n * N + i] = adj[n * N + i] + lam;
+      for (int m = 0; m < nl; ++m) adjf[(n - m) * N + i] = adjf[(n - m) * N + i] + g->dt * beta[m] * lam;
+    }
+    for (int64_t z = 0; z < nz; ++z)
+      for (int64_t y = 0; y < ny; ++y)
+        for (int64_t x = 0; x < nx; ++x) {
+          int64_t i = (z * ny + y) * nx + x;
+          const double af = adjf[n * N + i];
+          for (int a = 0; a < g->dim; ++a) {
+            orc_tap taps[32];
+            for (int deriv = 1; deriv <= 2; ++deriv) {
+              int nt = point_taps(g, kn, x, y, z, a, deriv, taps);
+              double fac = deriv == 1 ? -g->c[a] : g->alpha;
+              double d2 = 0.0;
+              for (int t = 0; t < nt; ++t) {
+                int64_t q[3] = {x, y, z};
+                q[a] = wrap_add(q[a], taps[t].j, g->n[a]);
+                int64_t src = (q[2] * ny + q[1]) * nx + q[0];
+                int64_t level = n - taps[t].l;
+                adj[level * N + src] = adj[level * N + src] + af * fac * taps[t].c;
+                if (deriv == 2) d2 = d2 + taps[t].c * hist[level * N + src];
+              }
+              if (deriv == 2) ga = ga + af * d2;
+            }
+          }
+        }
+  }
+  memcpy(grad_u0, adj, sizeof(double) * (size_t)N);
+  *grad_alpha = ga;
+  *J = jj;
+  free(hist); free(adj); free(adjf); free(keff); free(ulast);
+  return 0;
+}
+
 int orc_adjoint(const orc_cfg *g, const double *u0, int64_t nsteps, const double *u_target, double *grad_u0,
                 double *grad_alpha, double *J) {
-  if (orc_check(g) || nsteps < 0 || g->tsteps > 1 || g->burgers) return -1; /* forward Euler, linear equation */
+  if (orc_check(g) || nsteps < 0 || g->burgers) return -1; /* linear equation */
+  if (g->tsteps > 1) return orc_adjoint_ab(g, u0, nsteps, u_target, grad_u0, grad_alpha, J);
   const int T = orc_time_width(g->order, g->scheme);
   const int64_t N = ntot(g), nb = orc_num_sides(g);
   const int64_t nx = g->n[0], ny = g->n[1], nz = g->n[2];
