@@ -211,8 +211,11 @@ int at_destroy(at_handle_t *hd);
  * lambda^{n+1} back through the merged taps to lambda^n and, for buffer points, through the extrapolation
  * weights w_m(k) of the replayed delay k to lambda^{n-k-m}.  dJ/dalpha = sum_n <lambda^{n+1}, dt D2_AT U^n>.
  * The paper has no adjoint; this is the exact discrete adjoint of the forward step of Sec. 4.1 / Tables
- * "atschemes-left/right" for forward Euler, orders 2, 4 and 6, schemes AT_SYNC, AT_ASYNC_STD and AT_AT, the linear
- * equation (other configurations: AT_ERR_ARG).
+ * "atschemes-left/right" for orders 2, 4 and 6, schemes AT_SYNC, AT_ASYNC_STD and AT_AT, the linear equation,
+ * with forward Euler or Adams-Bashforth (other configurations: AT_ERR_ARG).  An Adams-Bashforth run must start
+ * from a caller's field (at_reset with u0_dev; the analytic pre-history of a run from Eq. "IC" depends on alpha):
+ * otherwise AT_ERR_STATE.  Its step n sends lambda^{n+1} to lambda^n (identity) and the adjoint of dt f^n,
+ * mu^n = sum_m beta_m lambda^{n+1+m} over the later steps that use f^n, back through the transposed taps.
  *
  * at_adjoint_workspace: doubles of device workspace for a run of nsteps with a checkpoint every ckpt_every
  *   steps (0: ceil(sqrt(nsteps))): checkpoints of the R-1 live levels, one segment of recomputed levels, the

@@ -43,6 +43,10 @@ struct AdjParams {
   int64_t list_len;
   int64_t edge_len;    // on the host: the edge groups come first in the list
   int32_t alpha;       // accumulate dJ/dalpha (needs the forward levels); 0: lambda only
+  // Adams-Bashforth (kernels instantiated with AB): the transposed taps act on mu = sum_m beta_m lambda^{s+1} (the
+  // adjoint of dt f^n), and lambda^{n+1} reaches lambda^n through the identity (s0 lacks the 1).
+  const double *mu;
+  int32_t reach;       // levels a step reaches below n: R - 2 (level n - reach is initialised by step n)
 };
 
 // Block sum of v into g_blk[blockIdx.x] (warp shuffles, then warp 0 in warp order).
@@ -60,12 +64,13 @@ __device__ __forceinline__ void block_accumulate(double v, double *g_blk) {
 }
 
 // General path for one output cell c (any position): transpose contributions per lag and the alpha term.
-template <int DIM, int H>
+template <int DIM, int H, bool AB>
 __device__ void adjoint_cell(const AdjParams &a, const uint8_t *__restrict__ keff, int64_t n, int64_t ci,
                              const int c[3], double &galpha) {
   const StepParams &f = a.f;
   const int64_t N = f.ntot;
-  const double *ln = a.lam + ((n + 1) % a.Rl) * N;
+  const double *lnext = a.lam + ((n + 1) % a.Rl) * N;
+  const double *ln = AB ? a.mu : lnext;
   const double *un = f.ring + (n % f.R) * N;
   const int64_t stride[3] = {1, (int64_t)f.n[0], (int64_t)f.n[0] * f.n[1]};
   int pidx[3] = {0, 0, 0}, pos[3] = {0, 0, 0};
@@ -78,7 +83,7 @@ __device__ void adjoint_cell(const AdjParams &a, const uint8_t *__restrict__ kef
 #pragma unroll
   for (int l = 0; l < AT_MAX_LAG; ++l) acc[l] = 0.0;
   const double lc = ln[ci];
-  acc[0] = fma(f.s0, lc, f.zero);
+  acc[0] = fma(f.s0, lc, AB ? lnext[ci] : f.zero);
   double d2 = a.alpha ? fma(f.q0, __ldg(un + ci), f.zero) : 0.0;
 #pragma unroll
   for (int ax = 0; ax < DIM; ++ax) {
@@ -116,7 +121,7 @@ __device__ void adjoint_cell(const AdjParams &a, const uint8_t *__restrict__ kef
     }
   }
   galpha = fma(lc, d2, galpha);
-  const int maxlag = a.Rl - 2;
+  const int maxlag = a.reach;
   for (int l = 0; l <= maxlag; ++l) {
     const int64_t level = n - l;
     if (level < 0) break;
@@ -130,7 +135,7 @@ __device__ void adjoint_cell(const AdjParams &a, const uint8_t *__restrict__ kef
 // wraps around the domain).  Neighbour points i = c - j in another PE read c as a buffer point; their
 // contributions are summed per PE side (one side per axis, two along x) and sent to the levels n-k-m of that
 // side's delay k with weights w_m(k).  The fresh level n-R+2 is zeroed before any contribution lands in it.
-template <int DIM, int H>
+template <int DIM, int H, bool AB>
 __device__ __forceinline__ void adjoint_group(const AdjParams &a, const uint8_t *__restrict__ keff, int64_t n, int x0,
                                               int y, int z, double &galpha) {
   const StepParams &f = a.f;
@@ -138,7 +143,8 @@ __device__ __forceinline__ void adjoint_group(const AdjParams &a, const uint8_t 
   const int nx = f.n[0];
   const int64_t row = DIM == 3 ? ((int64_t)z * f.n[1] + y) * nx : 0;
   const int64_t i0 = row + x0;
-  const double *ln = a.lam + ((n + 1) % a.Rl) * N;
+  const double *lnext = a.lam + ((n + 1) % a.Rl) * N;
+  const double *ln = AB ? a.mu : lnext;
   double d[4] = {0.0, 0.0, 0.0, 0.0};
   double uc[4];
   if (a.alpha) group_eval<DIM, H, LdgNC, true>(f, keff, f.ring + (n % f.R) * N, n, x0, y, z, d, uc);
@@ -173,9 +179,14 @@ __device__ __forceinline__ void adjoint_group(const AdjParams &a, const uint8_t 
   }
   double A[4], X[4][4];  // X[0]: lower x PE, X[1]: upper x PE, X[2]: y neighbour PE, X[3]: z neighbour PE
   int kX[4] = {kxl, kxr, 0, 0};
+  double id[4] = {f.zero, f.zero, f.zero, f.zero};
+  if (AB) {
+    const double2 e0 = LdgNC::ld2(lnext + i0), e1 = LdgNC::ld2(lnext + i0 + 2);
+    id[0] = e0.x; id[1] = e0.y; id[2] = e1.x; id[3] = e1.y;
+  }
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    A[q] = fma(f.s0, lv[q + W], f.zero);
+    A[q] = fma(f.s0, lv[q + W], id[q]);
     X[0][q] = X[1][q] = X[2][q] = X[3][q] = 0.0;
 #pragma unroll
     for (int j = -H; j <= H; ++j) {
@@ -221,16 +232,16 @@ __device__ __forceinline__ void adjoint_group(const AdjParams &a, const uint8_t 
       }
     }
   }
-  const int64_t fresh = n - a.Rl + 2;
+  const int64_t fresh = n - a.reach;
   const int snl = (int)(n % a.Rl);
   double2 *cur = reinterpret_cast<double2 *>(a.lam + snl * N + i0);
-  if (a.Rl == 2) {
+  if (a.reach == 0) {
     cur[0] = make_double2(A[0], A[1]);
     cur[1] = make_double2(A[2], A[3]);
     return;
   }
   if (fresh >= 0) {
-    double2 *fr = reinterpret_cast<double2 *>(a.lam + slot_back(snl, a.Rl - 2, a.Rl) * N + i0);
+    double2 *fr = reinterpret_cast<double2 *>(a.lam + slot_back(snl, a.reach, a.Rl) * N + i0);
     fr[0] = make_double2(0.0, 0.0);
     fr[1] = make_double2(0.0, 0.0);
   }
@@ -265,7 +276,7 @@ template <int MODE>
 struct AdjBounds {
   static constexpr int min_blocks = MODE == 1 ? AT_ADJ_MIN_BLOCKS : 2;
 };
-template <int DIM, int H, int MODE, bool AL>
+template <int DIM, int H, int MODE, bool AL, bool AB>
 __global__ void __launch_bounds__(256, AdjBounds<MODE>::min_blocks) adjoint_step_kernel(const AdjParams a,
                                                                                       const int64_t n) {
   constexpr bool G = MODE != 0;
@@ -283,10 +294,11 @@ __global__ void __launch_bounds__(256, AdjBounds<MODE>::min_blocks) adjoint_step
         const int64_t yz = i / nx;
         c[0] = (int)(i - yz * nx); c[2] = (int)(yz / ny); c[1] = (int)(yz - (int64_t)c[2] * ny);
       }
-      adjoint_cell<DIM, H>(a, keff, n, i, c, galpha);
+      adjoint_cell<DIM, H, AB>(a, keff, n, i, c, galpha);
     }
   } else {
-    const double *ln = a.lam + ((n + 1) % a.Rl) * N;
+    const double *lnext = a.lam + ((n + 1) % a.Rl) * N;
+    const double *ln = AB ? a.mu : lnext;
     const double *un = f.ring + (n % f.R) * N;
     const int nx = f.n[0], ny = f.n[1];
     const int gx = nx >> 2;
@@ -298,7 +310,7 @@ __global__ void __launch_bounds__(256, AdjBounds<MODE>::min_blocks) adjoint_step
       const int z = DIM == 3 ? (int)(r / ny) : 0, y = DIM == 3 ? (int)(r - (int64_t)z * ny) : 0;
       const int64_t i0 = r * nx + x0;
       if (MODE == 2) {
-        adjoint_group<DIM, H>(a, keff, n, x0, y, z, galpha);
+        adjoint_group<DIM, H, AB>(a, keff, n, x0, y, z, galpha);
         continue;
       }
       constexpr int W = XWin<H>::W, NW = XWin<H>::N;
@@ -312,10 +324,14 @@ __global__ void __launch_bounds__(256, AdjBounds<MODE>::min_blocks) adjoint_step
           uv[t] = u.x; uv[t + 1] = u.y;
         }
       }
-      double A[4], D[4];
+      double A[4], D[4], id[4] = {f.zero, f.zero, f.zero, f.zero};
+      if (AB) {
+        const double2 e0 = LdgNC::ld2(lnext + i0), e1 = LdgNC::ld2(lnext + i0 + 2);
+        id[0] = e0.x; id[1] = e0.y; id[2] = e1.x; id[3] = e1.y;
+      }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        double acc = fma(f.s0, lv[q + W], f.zero), d = AL ? fma(f.q0, uv[q + W], f.zero) : 0.0;
+        double acc = fma(f.s0, lv[q + W], id[q]), d = AL ? fma(f.q0, uv[q + W], f.zero) : 0.0;
 #pragma unroll
         for (int j = -H; j <= H; ++j) {
           if (j == 0) continue;
@@ -344,14 +360,14 @@ __global__ void __launch_bounds__(256, AdjBounds<MODE>::min_blocks) adjoint_step
 #pragma unroll
       for (int q = 0; q < 4; ++q) if (AL) galpha = fma(lv[q + W], D[q], galpha);
       double2 *cur = reinterpret_cast<double2 *>(a.lam + (n % a.Rl) * N + i0);
-      if (a.Rl == 2) {
+      if (a.reach == 0) {
         cur[0] = make_double2(A[0], A[1]);
         cur[1] = make_double2(A[2], A[3]);
       } else {
         const double2 p0 = cur[0], p1 = cur[1];
         cur[0] = make_double2(p0.x + A[0], p0.y + A[1]);
         cur[1] = make_double2(p1.x + A[2], p1.y + A[3]);
-        const int64_t fresh = n - a.Rl + 2;
+        const int64_t fresh = n - a.reach;
         if (fresh >= 0) {
           double2 *fr = reinterpret_cast<double2 *>(a.lam + (fresh % a.Rl) * N + i0);
           fr[0] = make_double2(0.0, 0.0);
@@ -361,6 +377,21 @@ __global__ void __launch_bounds__(256, AdjBounds<MODE>::min_blocks) adjoint_step
     }
   }
   if (AL) block_accumulate(galpha, a.g_blk);
+}
+
+// Adams-Bashforth: mu = sum of up to three weighted adjoint levels (the adjoint of dt f^n, see the driver).
+struct MuTerms {
+  const double *src[3];
+  double w[3];
+  int32_t count;
+};
+
+__global__ void ab_mu_kernel(double *__restrict__ mu, const MuTerms t, int64_t N) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    double v = t.w[0] * t.src[0][i];
+    for (int k = 1; k < t.count; ++k) v = fma(t.w[k], t.src[k][i], v);
+    mu[i] = v;
+  }
 }
 
 __global__ void sum_blocks_kernel(const double *g_blk, int nblk, double *out) {
@@ -386,7 +417,7 @@ int adj_blocks() {
   return sms * 8;
 }
 
-template <int DIM, int H, bool AL>
+template <int DIM, int H, bool AL, bool AB>
 void launch_modes(const AdjParams &a, int64_t n, int nblk, bool grouped, cudaStream_t st) {
   if (grouped) {
     AdjParams e = a, i = a;
@@ -394,17 +425,22 @@ void launch_modes(const AdjParams &a, int64_t n, int nblk, bool grouped, cudaStr
     e.list_len = a.edge_len;
     i.list = a.list + a.edge_len;
     i.list_len = a.list_len - a.edge_len;
-    adjoint_step_kernel<DIM, H, 2, AL><<<nblk, kAdjThreads, 0, st>>>(e, n);
-    adjoint_step_kernel<DIM, H, 1, AL><<<nblk, kAdjThreads, 0, st>>>(i, n);
+    adjoint_step_kernel<DIM, H, 2, AL, AB><<<nblk, kAdjThreads, 0, st>>>(e, n);
+    adjoint_step_kernel<DIM, H, 1, AL, AB><<<nblk, kAdjThreads, 0, st>>>(i, n);
   } else {
-    adjoint_step_kernel<DIM, H, 0, AL><<<nblk, kAdjThreads, 0, st>>>(a, n);
+    adjoint_step_kernel<DIM, H, 0, AL, AB><<<nblk, kAdjThreads, 0, st>>>(a, n);
   }
 }
 
 template <int DIM, int H>
 void launch_alpha(const AdjParams &a, int64_t n, int nblk, bool grouped, cudaStream_t st) {
-  if (a.alpha) launch_modes<DIM, H, true>(a, n, nblk, grouped, st);
-  else launch_modes<DIM, H, false>(a, n, nblk, grouped, st);
+  if (a.mu) {
+    if (a.alpha) launch_modes<DIM, H, true, true>(a, n, nblk, grouped, st);
+    else launch_modes<DIM, H, false, true>(a, n, nblk, grouped, st);
+  } else {
+    if (a.alpha) launch_modes<DIM, H, true, false>(a, n, nblk, grouped, st);
+    else launch_modes<DIM, H, false, false>(a, n, nblk, grouped, st);
+  }
 }
 
 bool adjoint_grouped(const AdjParams &a) {
@@ -443,6 +479,25 @@ cudaError_t launch_adjoint_step(const AdjParams &a, int64_t n, int nblk, cudaStr
   return cudaGetLastError();
 }
 
+// mu for backward step n of an Adams-Bashforth run started from a caller's field (step s uses l(s) = min(s+1, ts)
+// levels): the adjoint of dt f^n is sum over the steps s = n .. n+ts-1 (s < Ns) that use f^n, with m = s - n < l(s),
+// of beta^{(l(s))}_m lambda^{s+1}.
+cudaError_t launch_ab_mu(const AdjParams &a, const StepParams &p, int64_t n, int64_t Ns, cudaStream_t st) {
+  MuTerms t;
+  t.count = 0;
+  for (int64_t s = n; s < n + p.ts && s < Ns; ++s) {
+    const int64_t m = s - n;
+    const int l = (int)(s + 1 < p.ts ? s + 1 : p.ts);
+    if (m >= l) continue;
+    t.src[t.count] = a.lam + ((s + 1) % a.Rl) * p.ntot;
+    t.w[t.count] = p.beta[l - 1][m];
+    ++t.count;
+  }
+  const int64_t b = (p.ntot + 255) / 256;
+  ab_mu_kernel<<<(int)(b < 152 * 16 ? b : 152 * 16), 256, 0, st>>>(const_cast<double *>(a.mu), t, p.ntot);
+  return cudaGetLastError();
+}
+
 int fail(int code, const char *msg) {
   at_internal_set_error(msg);
   return code;
@@ -466,7 +521,7 @@ namespace {
 //   g_blk        nblk                   per-block d J / d alpha accumulators, then the sum
 //   delays       2 x 2 x nb bytes       effective delays of the recompute and of the backward sweep
 struct AdjLayout {
-  int64_t s, nck, seg_depth, ck, seg, lam, gblk, keff, list, total;
+  int64_t s, nck, seg_depth, ck_fields, lam_slots, ck, seg, segf, lam, mu, gblk, keff, list, total;
 };
 
 int64_t up32(int64_t v) { return (v + 31) / 32 * 32; }
@@ -477,11 +532,16 @@ AdjLayout layout(const at_handle *hd, int64_t nsteps, int64_t every) {
   L.s = every > 0 ? every : (int64_t)std::ceil(std::sqrt((double)(nsteps > 0 ? nsteps : 1)));
   if (L.s < 1) L.s = 1;
   L.nck = nsteps > 0 ? (nsteps + L.s - 1) / L.s : 0;
+  const int64_t nf = hd->sp.ts - 1;  // Adams-Bashforth: stored right-hand sides, part of the forward state
   L.seg_depth = L.s + R - 1;
+  L.ck_fields = R - 1 + nf;
+  L.lam_slots = R + nf;             // the adjoint levels n+1+m that mu still needs stay alive
   L.ck = 0;
-  L.seg = L.ck + up32(L.nck * (R - 1) * N);
-  L.lam = L.seg + up32(L.seg_depth * N);
-  L.gblk = L.lam + up32(R * N);
+  L.seg = L.ck + up32(L.nck * L.ck_fields * N);
+  L.segf = L.seg + up32(L.seg_depth * N);
+  L.lam = L.segf + up32(nf * N);
+  L.mu = L.lam + up32(L.lam_slots * N);
+  L.gblk = L.mu + up32(nf > 0 ? N : 0);
   L.keff = L.gblk + up32(adj_blocks() + 1);
   L.list = L.keff + up32((4 * hd->sp.nb + 7) / 8);
   L.total = L.list + up32((hd->sp.ntot / 4 + 1) / 2);
@@ -494,9 +554,12 @@ cudaError_t copy_field(double *dst, const double *src, int64_t n, cudaStream_t s
 
 }  // namespace
 
-// The transposed step covers forward Euler with the central and time-expanded rows, orders 2, 4 and 6.
+// The transposed step covers the central and time-expanded rows, orders 2, 4 and 6, forward Euler and
+// Adams-Bashforth runs started from a caller's field.
 static int adjoint_supported(const at_handle *hd) {
-  if (hd->sp.ts > 1) return fail(AT_ERR_ARG, "adjoint: only forward Euler (tsteps 0 or 1) is supported");
+  if (hd->sp.ts > 1 && hd->ab_analytic)
+    return fail(AT_ERR_STATE, "adjoint: an Adams-Bashforth run must start from a caller's field (at_reset with "
+                              "u0_dev): the analytic pre-history depends on alpha");
   if (hd->sp.scheme >= AT_AT_SPACE2) return fail(AT_ERR_ARG, "adjoint: the rows expanded in space are not supported");
   if (hd->sp.burgers) return fail(AT_ERR_ARG, "adjoint: Burgers' equation is not supported (linear equation only)");
   return AT_OK;
@@ -523,8 +586,13 @@ extern "C" int at_adjoint_forward(at_handle_t *hd, int64_t nsteps, int64_t ckpt_
     const int64_t n0 = c * L.s;
     for (int64_t lev = n0 - R + 2; lev <= n0; ++lev) {
       if (lev < 0) continue;
-      cudaError_t e = copy_field(work_dev + L.ck + (c * (R - 1) + (lev - (n0 - R + 2))) * N,
+      cudaError_t e = copy_field(work_dev + L.ck + (c * L.ck_fields + (lev - (n0 - R + 2))) * N,
                                  hd->sp.ring + (lev % R) * N, N, hd->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "at_adjoint_forward: checkpoint");
+    }
+    for (int64_t m = 0; m + 1 < hd->sp.ts; ++m) {  // the stored right-hand sides, slot by slot
+      cudaError_t e = copy_field(work_dev + L.ck + (c * L.ck_fields + R - 1 + m) * N, hd->sp.frhs + m * N, N,
+                                 hd->stream);
       if (e != cudaSuccess) return cuda_fail(e, "at_adjoint_forward: checkpoint");
     }
     const int64_t todo = (n0 + L.s <= nsteps) ? L.s : nsteps - n0;
@@ -555,13 +623,17 @@ extern "C" int at_adjoint_backward(at_handle_t *hd, const double *lambda_dev, do
   StepParams seg = hd->sp;
   seg.ring = w + L.seg;
   seg.R = (int32_t)L.seg_depth;
+  seg.frhs = hd->sp.ts > 1 ? w + L.segf : nullptr;
   seg.log = nullptr;
   seg.log_steps = 0;
   seg.keff = reinterpret_cast<uint8_t *>(w + L.keff);
   AdjParams a;
   a.f = seg;
   a.lam = w + L.lam;
-  a.Rl = (int32_t)R;
+  a.Rl = (int32_t)L.lam_slots;
+  a.reach = (int32_t)(R - 2);
+  a.mu = hd->sp.ts > 1 ? w + L.mu : nullptr;
+  const int64_t Rl = a.Rl;
   a.akeff = reinterpret_cast<uint8_t *>(w + L.keff) + 2 * hd->sp.nb;
   a.g_blk = w + L.gblk;
   a.alpha = want_alpha ? 1 : 0;
@@ -583,9 +655,9 @@ extern "C" int at_adjoint_backward(at_handle_t *hd, const double *lambda_dev, do
     if (e != cudaSuccess) return cuda_fail(e, "at_adjoint_backward: group lists");
   }
   // lambda^Ns = the caller's seed; the R-2 older levels start at zero; alpha accumulators at zero
-  e = copy_field(a.lam + (Ns % R) * N, lambda_dev, N, st);
+  e = copy_field(a.lam + (Ns % Rl) * N, lambda_dev, N, st);
   for (int64_t m = 1; m <= R - 2 && e == cudaSuccess; ++m)
-    if (Ns - m >= 0) e = cudaMemsetAsync(a.lam + ((Ns - m) % R) * N, 0, sizeof(double) * (size_t)N, st);
+    if (Ns - m >= 0) e = cudaMemsetAsync(a.lam + ((Ns - m) % Rl) * N, 0, sizeof(double) * (size_t)N, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.g_blk, 0, sizeof(double) * (size_t)(nblk + 1), st);
   if (e == cudaSuccess && Ns > 0) {
     StepParams first = seg;
@@ -596,12 +668,17 @@ extern "C" int at_adjoint_backward(at_handle_t *hd, const double *lambda_dev, do
     const int64_t n0 = c * L.s, n1 = (n0 + L.s < Ns) ? n0 + L.s : Ns;
     for (int64_t lev = n0 - R + 2; want_alpha && lev <= n0 && e == cudaSuccess; ++lev) {
       if (lev < 0) continue;
-      e = copy_field(seg.ring + (lev % seg.R) * N, w + L.ck + (c * (R - 1) + (lev - (n0 - R + 2))) * N, N, st);
+      e = copy_field(seg.ring + (lev % seg.R) * N, w + L.ck + (c * L.ck_fields + (lev - (n0 - R + 2))) * N, N, st);
     }
+    for (int64_t m = 0; want_alpha && m + 1 < hd->sp.ts && e == cudaSuccess; ++m)
+      e = copy_field(seg.frhs + m * N, w + L.ck + (c * L.ck_fields + R - 1 + m) * N, N, st);
     // the forward levels only serve the alpha term: without it the sweep needs no recompute
     if (want_alpha && e == cudaSuccess) e = launch_draw_delays(seg, n0, st);
     for (int64_t n = n0; want_alpha && n + 1 < n1 && e == cudaSuccess; ++n) e = launch_forward_step(seg, n, nullptr, st);
-    for (int64_t n = n1 - 1; n >= n0 && e == cudaSuccess; --n) e = launch_adjoint_step(a, n, nblk, st);
+    for (int64_t n = n1 - 1; n >= n0 && e == cudaSuccess; --n) {
+      if (a.mu) e = launch_ab_mu(a, hd->sp, n, Ns, st);
+      if (e == cudaSuccess) e = launch_adjoint_step(a, n, nblk, st);
+    }
   }
   if (e == cudaSuccess) e = copy_field(grad_u0_dev, a.lam, N, st);  // level 0 lives in slot 0
   if (want_alpha && e == cudaSuccess) {

@@ -310,6 +310,7 @@ extern "C" int at_init(const at_config_t *cfg, double *ring_dev, int64_t ring_le
     delete hd;
     return cuda_fail(e, "at_init: initial condition");
   }
+  hd->ab_analytic = p.ts > 1 && cfg->burgers == 0;
   *out = hd;
   return AT_OK;
 }
@@ -369,7 +370,8 @@ extern "C" int at_reset(at_handle_t *hd, const double *u0_dev) {
                         hd->stream);
   else
     e = launch_wave_field(hd->wp, 0.0, hd->d_tables, hd->sp.ring, hd->stream);
-  if (e == cudaSuccess) e = ab_start(hd, u0_dev == nullptr && hd->cfg.burgers == 0);
+  hd->ab_analytic = hd->sp.ts > 1 && u0_dev == nullptr && hd->cfg.burgers == 0;
+  if (e == cudaSuccess) e = ab_start(hd, hd->ab_analytic);
   if (e == cudaSuccess) e = launch_draw_delays(hd->sp, 0, hd->stream);
   if (e != cudaSuccess) return cuda_fail(e, "at_reset");
   hd->step = 0;

@@ -135,6 +135,7 @@ struct at_handle {
   int64_t adj_every = 0;         // checkpoint interval
   double *adj_work = nullptr;    // caller's workspace
   int64_t adj_work_len = 0;
+  bool ab_analytic = false;      // Adams-Bashforth run started from Eq. "IC" with the analytic pre-history
 };
 
 // Steps per captured graph: long runs replay one graph of kGraphSteps kernel nodes plus a counter update.

@@ -144,3 +144,65 @@ def test_u0_only_sweep_gives_the_same_u0_gradient():
         assert (ga is None) == (not want_alpha)
         s.close()
     assert torch.equal(grads[0], grads[1])
+
+
+# ------------------------------------------------------------ Adams-Bashforth runs (from a caller's field)
+AB_CASES = [
+    ("1d_o4_ab2", lambda: W.wl_1d(256, 8, 4, 3, 0, 81, (1, 2, 3), r_alpha=0.02, tsteps=2)[0], 80),
+    ("1d_o6_ab3", lambda: W.wl_1d(256, 8, 6, 4, 0, 82, (1, 2, 3), r_alpha=0.01, tsteps=3)[0], 60),
+    ("1d_o2_ab3_point", lambda: W.wl_1d(250, 5, 2, 3, 0, 83, (1, 2), r_alpha=0.02, tsteps=3)[0], 70),
+    ("1d_o4_std_ab2", lambda: W.wl_1d(256, 8, 4, 3, 0, 84, (1, 2), r_alpha=0.02, tsteps=2, scheme=W.ASYNC_STD)[0], 60),
+    ("1d_o2_sync_ab2", lambda: W.wl_1d(128, 4, 2, 1, 0, 85, (1, 2), r_alpha=0.02, tsteps=2, scheme=W.SYNC)[0], 40),
+    ("3d_o4_ab2", lambda: W.wl_3d([16, 12, 8], [2, 2, 2], 4, 3, 0, 86, c=(0.3, 0.2, 0.1), tsteps=2)[0], 20),
+]
+
+
+@pytest.mark.parametrize("name,make,nsteps", AB_CASES, ids=[c[0] for c in AB_CASES])
+def test_multistep_adjoint_matches_cpu_adjoint(name, make, nsteps):
+    spec = make()
+    cfg = oracle.Config(spec)
+    rng = np.random.default_rng(4)
+    u0 = oracle.initial(cfg) + 0.01 * rng.standard_normal(cfg.shape)
+    target = 0.5 * u0 + 0.1 * rng.standard_normal(cfg.shape)
+    J, g, ga, _ = _gpu_grad(spec, nsteps, target, u0=u0)
+    Jo, go, gao = oracle.adjoint(cfg, nsteps, target, u0=u0)
+    assert J == pytest.approx(Jo, rel=1e-11)
+    assert np.linalg.norm(g - go) / np.linalg.norm(go) <= 1e-12
+    assert ga == pytest.approx(gao, rel=1e-10)
+
+
+def test_multistep_adjoint_checkpoints_and_start():
+    """The checkpoint interval does not change the bits; a run from Eq. "IC" (analytic pre-history, which depends
+    on alpha) is refused with AT_ERR_STATE."""
+    from paper_1702_00496_gb300 import Solver, binding as B
+    spec, _ = W.wl_1d(512, 8, 6, 4, 0, 87, (1, 2, 3), r_alpha=0.01, tsteps=3)
+    cfg = oracle.Config(spec)
+    u0 = oracle.initial(cfg) + 0.01
+    target = np.zeros(512)
+    ref = None
+    for every in (0, 1, 7, 97):
+        J, g, ga, _ = _gpu_grad(spec, 97, target, every, u0=u0)
+        if ref is None:
+            ref = (J, g, ga)
+        assert J == ref[0] and ga == ref[2] and np.array_equal(g, ref[1]), every
+    s = Solver(spec)
+    with pytest.raises(B.ATError) as e:
+        s.adjoint_forward(10)
+    assert e.value.code == B.AT_ERR_STATE
+    s.close()
+
+
+def test_multistep_autograd_function():
+    from paper_1702_00496_gb300 import at_forward
+    spec, _ = W.wl_1d(256, 8, 4, 3, 0, 88, (1, 2, 3), r_alpha=0.02, tsteps=2)
+    cfg = oracle.Config(spec)
+    u0n = oracle.initial(cfg) + 0.02
+    u0 = torch.as_tensor(u0n, device="cuda").requires_grad_(True)
+    alpha = torch.tensor(spec["alpha"], dtype=torch.float64, device="cuda", requires_grad=True)
+    u = at_forward(u0, alpha, spec, 50)
+    loss = 0.5 * (u ** 2).sum()
+    loss.backward()
+    Jo, go, gao = oracle.adjoint(cfg, 50, np.zeros(cfg.shape), u0=u0n)
+    assert float(loss.detach()) == pytest.approx(Jo, rel=1e-11)
+    assert np.linalg.norm(u0.grad.cpu().numpy() - go) / np.linalg.norm(go) <= 1e-12
+    assert float(alpha.grad) == pytest.approx(gao, rel=1e-10)
