@@ -25,7 +25,8 @@
  *     f = -U_i^n D1 U + alpha D2 U with the same AT D1 and D2, U_i^n the point's own (current) value.
  *   - error: E = U - u_a (Sec. 5.1, Eq. "ana_sol", with the travelling phase read as
  *     sin(kappa (x - c t) + phi)); averages over I, I_I and I_B (Sec. 4).
- *   - adjoint: the literal transpose of the forward step over the stored history.
+ *   - adjoint: the literal transpose of the forward step over the stored history (Burgers' equation: the
+ *     D1 taps carry -U_i^n and U_i^n itself receives -D1 U, the derivative of the nonlinear term).
  *
  * Readings where the paper is silent (each one is listed in the design doc):
  *   - a PE side uses one delay for all its buffer points (uniform delay, Sec. 5.1); the two sides
@@ -598,7 +599,7 @@ int orc_error_stats(const orc_cfg *g, const double *u, int64_t n, double *out) {
  * <adjoint of f^n, sum_a D2_a U>. */
 static int orc_adjoint_ab(const orc_cfg *g, const double *u0, int64_t nsteps, const double *u_target,
                           double *grad_u0, double *grad_alpha, double *J) {
-  if (!u0) return -1;
+  if (!u0 && !g->burgers) return -1; /* Burgers' runs always start with Euler (no analytic pre-history) */
   const int ts = g->tsteps;
   const int T = orc_time_width(g->order, g->scheme);
   const int64_t N = ntot(g), nb = orc_num_sides(g);
@@ -642,17 +643,18 @@ static int orc_adjoint_ab(const orc_cfg *g, const double *u0, int64_t nsteps, co
             orc_tap taps[32];
             for (int deriv = 1; deriv <= 2; ++deriv) {
               int nt = point_taps(g, kn, x, y, z, a, deriv, taps);
-              double fac = deriv == 1 ? -g->c[a] : g->alpha;
-              double d2 = 0.0;
+              double fac = deriv == 1 ? (g->burgers ? -hist[n * N + i] : -g->c[a]) : g->alpha;
+              double dd = 0.0;
               for (int t = 0; t < nt; ++t) {
                 int64_t q[3] = {x, y, z};
                 q[a] = wrap_add(q[a], taps[t].j, g->n[a]);
                 int64_t src = (q[2] * ny + q[1]) * nx + q[0];
                 int64_t level = n - taps[t].l;
                 adj[level * N + src] = adj[level * N + src] + af * fac * taps[t].c;
-                if (deriv == 2) d2 = d2 + taps[t].c * hist[level * N + src];
+                dd = dd + taps[t].c * hist[level * N + src];
               }
-              if (deriv == 2) ga = ga + af * d2;
+              if (deriv == 2) ga = ga + af * dd;
+              if (deriv == 1 && g->burgers) adj[n * N + i] = adj[n * N + i] - af * dd;
             }
           }
         }
@@ -666,7 +668,7 @@ static int orc_adjoint_ab(const orc_cfg *g, const double *u0, int64_t nsteps, co
 
 int orc_adjoint(const orc_cfg *g, const double *u0, int64_t nsteps, const double *u_target, double *grad_u0,
                 double *grad_alpha, double *J) {
-  if (orc_check(g) || nsteps < 0 || g->burgers) return -1; /* linear equation */
+  if (orc_check(g) || nsteps < 0) return -1;
   if (g->tsteps > 1) return orc_adjoint_ab(g, u0, nsteps, u_target, grad_u0, grad_alpha, J);
   const int T = orc_time_width(g->order, g->scheme);
   const int64_t N = ntot(g), nb = orc_num_sides(g);
@@ -698,17 +700,19 @@ int orc_adjoint(const orc_cfg *g, const double *u0, int64_t nsteps, const double
             orc_tap taps[32];
             for (int deriv = 1; deriv <= 2; ++deriv) {
               int nt = point_taps(g, kn, x, y, z, a, deriv, taps);
-              double fac = deriv == 1 ? -g->c[a] : g->alpha;
-              double d2 = 0.0;
+              /* Burgers: f = -U_i^n D1 U + alpha D2 U; the D1 taps carry -U_i^n, and U_i^n itself gets -D1 U */
+              double fac = deriv == 1 ? (g->burgers ? -hist[n * N + i] : -g->c[a]) : g->alpha;
+              double dd = 0.0;
               for (int t = 0; t < nt; ++t) {
                 int64_t q[3] = {x, y, z};
                 q[a] = wrap_add(q[a], taps[t].j, g->n[a]);
                 int64_t src = (q[2] * ny + q[1]) * nx + q[0];
                 int64_t level = n - taps[t].l;
                 adj[level * N + src] = adj[level * N + src] + lam * g->dt * fac * taps[t].c;
-                if (deriv == 2) d2 = d2 + taps[t].c * hist[level * N + src];
+                dd = dd + taps[t].c * hist[level * N + src];
               }
-              if (deriv == 2) ga = ga + lam * g->dt * d2;
+              if (deriv == 2) ga = ga + lam * g->dt * dd;
+              if (deriv == 1 && g->burgers) adj[n * N + i] = adj[n * N + i] - lam * g->dt * dd;
             }
           }
         }

@@ -77,3 +77,36 @@ def test_case6_converges_at_fourth_order_against_a_finer_run():
     sync = np.array(errs[(1.0, 0.0, 0.0)])
     for probs in ((0.7, 0.2, 0.1), (0.3, 0.5, 0.2)):
         assert np.all(np.abs(np.array(errs[probs]) / sync - 1) < 0.01)
+
+
+@pytest.mark.parametrize("order,tsteps,scheme", [(4, 2, W.AT), (2, 1, W.AT), (4, 1, W.ASYNC_STD), (6, 3, W.AT)])
+def test_burgers_adjoint_matches_central_differences(order, tsteps, scheme):
+    """The literal transpose of the Burgers step: the D1 taps carry -U_i^n and U_i^n receives -D1 U.  J is no longer
+    quadratic in u0, so both directions use Richardson-extrapolated central differences."""
+    spec, _ = W.wl_1d(128, 8, order, 3, 0, 71, (3, 4, 5), scheme=scheme, c=0.0, r_alpha=0.02 if order < 6 else 0.01,
+                      tsteps=tsteps)
+    spec["burgers"] = 1
+    cfg = oracle.Config(spec)
+    rng = np.random.default_rng(3)
+    u0 = oracle.initial(cfg)
+    tgt = 0.5 * u0 + 0.1 * rng.standard_normal(cfg.shape)
+    nsteps = 40
+    J, g, ga = oracle.adjoint(cfg, nsteps, tgt)
+
+    def Jf(u, alpha=spec["alpha"]):
+        sp = dict(spec)
+        sp["alpha"] = alpha
+        uu, _, _ = oracle.run(oracle.Config(sp), nsteps, want_log=False, u0=u)
+        return 0.5 * float(np.sum((uu - tgt) ** 2))
+
+    assert J == pytest.approx(Jf(u0), rel=1e-14)
+
+    def rich(f, h):
+        d1 = (f(h) - f(-h)) / (2 * h)
+        d2 = (f(h / 2) - f(-h / 2)) / h
+        return (4 * d2 - d1) / 3
+
+    v = rng.standard_normal(cfg.shape)
+    assert float(np.sum(g * v)) == pytest.approx(rich(lambda e: Jf(u0 + e * v), 1e-3), rel=1e-8)
+    a0 = spec["alpha"]
+    assert ga == pytest.approx(rich(lambda e: Jf(u0, a0 + e), 1e-3 * a0), rel=1e-7)
