@@ -131,6 +131,70 @@ __device__ void adjoint_cell(const AdjParams &a, const uint8_t *__restrict__ kef
   }
 }
 
+// Burgers' equation (1D), one output cell c: the step is U^{n+1}_i = U^n_i + phi_i with phi_i = -U^n_i a1_i + a2_i,
+// a1 = dt D1_AT U, a2 = dt alpha D2_AT U (taps b1, b2).  Its transpose, with mu the adjoint of phi (Euler:
+// lambda^{n+1}), sends mu_i (b2_j - b1_j U^n_i) from each point i = c - j that reads c through tap j to c's level
+// (n, or n-k-m with w_m(k) when c is a buffer point of i), and mu_c (b2_0 - a1_c) plus the identity lambda^{n+1}_c to
+// level n.  The alpha term is mu_c dt D2_AT U at c, as for the linear step.  The forward levels are always needed.
+template <int H, bool AB>
+__device__ void adjoint_cell_burgers(const AdjParams &a, const uint8_t *__restrict__ keff, int64_t n, int64_t ci,
+                                     double &galpha) {
+  const StepParams &f = a.f;
+  const int64_t N = f.ntot;
+  const double *lnext = a.lam + ((n + 1) % a.Rl) * N;
+  const double *ln = AB ? a.mu : lnext;
+  const double *un = f.ring + (n % f.R) * N;
+  const int c = (int)ci;
+  const int pidx[3] = {c / f.S[0], 0, 0};
+  const int pos = c - pidx[0] * f.S[0];
+  const int sn = (int)(n % f.R);
+  const bool edge = f.use_pe[0] && (pos < H || pos >= f.S[0] - H);
+  double acc[AT_MAX_LAG];
+#pragma unroll
+  for (int l = 0; l < AT_MAX_LAG; ++l) acc[l] = 0.0;
+  const double mc = ln[ci], uc = LdgNC::ld(un + ci);
+  double a1 = f.zero, d2 = a.alpha ? fma(f.q0, uc, f.zero) : 0.0;
+#pragma unroll
+  for (int j = -H; j <= H; ++j) {
+    if (j == 0) continue;
+    // transpose: point i = c - j reads c through its tap j
+    const int ia = wrap_coord(c - j, f.n[0]);
+    const double li = ln[ia], ui = LdgNC::ld(un + ia);
+    const double src = fma(f.b2[j + H], li, -(f.b1[j + H] * li) * ui);
+    int k = 0;
+    if (edge) {
+      const int pi = ia / f.S[0];
+      if (pi != pidx[0]) {
+        const int pid[3] = {pi, 0, 0};
+        k = keff[side_of<1>(f, pid, 0, j > 0 ? 1 : 0)];
+      }
+    }
+    if (k == 0) {
+      acc[0] += src;
+    } else {
+      for (int m = 0; m < f.T; ++m) acc[k + m] = fma(f.w[k][m], src, acc[k + m]);
+    }
+    // c's own tap j (its first derivative for the direct term, its second for alpha)
+    const int cj = wrap_coord(c + j, f.n[0]);
+    int kc = 0;
+    if (edge && pos + j < 0) kc = keff[side_of<1>(f, pidx, 0, 0)];
+    if (edge && pos + j >= f.S[0]) kc = keff[side_of<1>(f, pidx, 0, 1)];
+    const double v = kc > 0 ? halo_value<LdgNC>(f, cj, sn, kc) : LdgNC::ld(un + cj);
+    a1 = fma(f.b1[j + H], v, a1);
+    if (a.alpha) d2 = fma(f.q[0][j + H], v, d2);
+  }
+  acc[0] += fma(mc, f.b2[H] - a1, lnext[ci]);
+  galpha = fma(mc, d2, galpha);
+  const int maxlag = a.reach;
+  for (int l = 0; l <= maxlag; ++l) {
+    const int64_t level = n - l;
+    if (level < 0) break;
+    double *slot = a.lam + (level % a.Rl) * N + ci;
+    if (l == maxlag) *slot = acc[l];
+    else if (l == 0 || acc[l] != 0.0) *slot = *slot + acc[l];
+  }
+}
+
 // Edge group: the four cells x0..x0+3 of row (y, z) when some of them lie within h of a PE edge (or the stencil
 // wraps around the domain).  Neighbour points i = c - j in another PE read c as a buffer point; their
 // contributions are summed per PE side (one side per axis, two along x) and sent to the levels n-k-m of that
@@ -276,7 +340,7 @@ template <int MODE>
 struct AdjBounds {
   static constexpr int min_blocks = MODE == 1 ? AT_ADJ_MIN_BLOCKS : 2;
 };
-template <int DIM, int H, int MODE, bool AL, bool AB>
+template <int DIM, int H, int MODE, bool AL, bool AB, bool BG = false>
 __global__ void __launch_bounds__(256, AdjBounds<MODE>::min_blocks) adjoint_step_kernel(const AdjParams a,
                                                                                       const int64_t n) {
   constexpr bool G = MODE != 0;
@@ -294,7 +358,8 @@ __global__ void __launch_bounds__(256, AdjBounds<MODE>::min_blocks) adjoint_step
         const int64_t yz = i / nx;
         c[0] = (int)(i - yz * nx); c[2] = (int)(yz / ny); c[1] = (int)(yz - (int64_t)c[2] * ny);
       }
-      adjoint_cell<DIM, H, AB>(a, keff, n, i, c, galpha);
+      if constexpr (BG && DIM == 1) adjoint_cell_burgers<H, AB>(a, keff, n, i, galpha);
+      else adjoint_cell<DIM, H, AB>(a, keff, n, i, c, galpha);
     }
   } else {
     const double *lnext = a.lam + ((n + 1) % a.Rl) * N;
@@ -419,6 +484,12 @@ int adj_blocks() {
 
 template <int DIM, int H, bool AL, bool AB>
 void launch_modes(const AdjParams &a, int64_t n, int nblk, bool grouped, cudaStream_t st) {
+  if constexpr (DIM == 1) {
+    if (a.f.burgers) {  // per-cell path
+      adjoint_step_kernel<1, H, 0, AL, AB, true><<<nblk, kAdjThreads, 0, st>>>(a, n);
+      return;
+    }
+  }
   if (grouped) {
     AdjParams e = a, i = a;
     e.list = a.list;
@@ -555,13 +626,12 @@ cudaError_t copy_field(double *dst, const double *src, int64_t n, cudaStream_t s
 }  // namespace
 
 // The transposed step covers the central and time-expanded rows, orders 2, 4 and 6, forward Euler and
-// Adams-Bashforth runs started from a caller's field.
+// Adams-Bashforth runs started from a caller's field, the linear equation and Burgers' equation.
 static int adjoint_supported(const at_handle *hd) {
   if (hd->sp.ts > 1 && hd->ab_analytic)
     return fail(AT_ERR_STATE, "adjoint: an Adams-Bashforth run must start from a caller's field (at_reset with "
                               "u0_dev): the analytic pre-history depends on alpha");
   if (hd->sp.scheme >= AT_AT_SPACE2) return fail(AT_ERR_ARG, "adjoint: the rows expanded in space are not supported");
-  if (hd->sp.burgers) return fail(AT_ERR_ARG, "adjoint: Burgers' equation is not supported (linear equation only)");
   return AT_OK;
 }
 
@@ -637,6 +707,8 @@ extern "C" int at_adjoint_backward(at_handle_t *hd, const double *lambda_dev, do
   a.akeff = reinterpret_cast<uint8_t *>(w + L.keff) + 2 * hd->sp.nb;
   a.g_blk = w + L.gblk;
   a.alpha = want_alpha ? 1 : 0;
+  // the linear transposed step needs the forward levels only for the alpha term; Burgers' always does
+  const bool need_fwd = want_alpha || hd->sp.burgers;
   a.list = reinterpret_cast<int32_t *>(w + L.list);
   a.list_len = 0;
   a.edge_len = 0;
@@ -666,15 +738,15 @@ extern "C" int at_adjoint_backward(at_handle_t *hd, const double *lambda_dev, do
   }
   for (int64_t c = L.nck - 1; c >= 0 && e == cudaSuccess; --c) {
     const int64_t n0 = c * L.s, n1 = (n0 + L.s < Ns) ? n0 + L.s : Ns;
-    for (int64_t lev = n0 - R + 2; want_alpha && lev <= n0 && e == cudaSuccess; ++lev) {
+    for (int64_t lev = n0 - R + 2; need_fwd && lev <= n0 && e == cudaSuccess; ++lev) {
       if (lev < 0) continue;
       e = copy_field(seg.ring + (lev % seg.R) * N, w + L.ck + (c * L.ck_fields + (lev - (n0 - R + 2))) * N, N, st);
     }
-    for (int64_t m = 0; want_alpha && m + 1 < hd->sp.ts && e == cudaSuccess; ++m)
+    for (int64_t m = 0; need_fwd && m + 1 < hd->sp.ts && e == cudaSuccess; ++m)
       e = copy_field(seg.frhs + m * N, w + L.ck + (c * L.ck_fields + R - 1 + m) * N, N, st);
-    // the forward levels only serve the alpha term: without it the sweep needs no recompute
-    if (want_alpha && e == cudaSuccess) e = launch_draw_delays(seg, n0, st);
-    for (int64_t n = n0; want_alpha && n + 1 < n1 && e == cudaSuccess; ++n) e = launch_forward_step(seg, n, nullptr, st);
+    // the forward levels serve the alpha term (and Burgers' transposed step): without them no recompute
+    if (need_fwd && e == cudaSuccess) e = launch_draw_delays(seg, n0, st);
+    for (int64_t n = n0; need_fwd && n + 1 < n1 && e == cudaSuccess; ++n) e = launch_forward_step(seg, n, nullptr, st);
     for (int64_t n = n1 - 1; n >= n0 && e == cudaSuccess; --n) {
       if (a.mu) e = launch_ab_mu(a, hd->sp, n, Ns, st);
       if (e == cudaSuccess) e = launch_adjoint_step(a, n, nblk, st);

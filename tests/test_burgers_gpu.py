@@ -127,8 +127,38 @@ def test_burgers_rejections():
     s = Solver(spec)
     with pytest.raises(B.ATError):
         s.error_stats()  # no analytic solution
-    with pytest.raises(B.ATError):
-        B.at_adjoint_workspace(s.h, 10, 0)
     s.close()
     with pytest.raises(B.ATError):
         Ensemble([spec], 10)
+
+
+BURGERS_ADJ = [(4, 2, W.AT, 256, 8), (2, 1, W.AT, 256, 8), (4, 1, W.ASYNC_STD, 256, 8), (6, 3, W.AT, 256, 8),
+               (4, 2, W.AT, 250, 5)]
+
+
+@pytest.mark.parametrize("order,tsteps,scheme,n,P", BURGERS_ADJ)
+def test_burgers_adjoint_matches_cpu_adjoint(order, tsteps, scheme, n, P):
+    """The transposed Burgers step (state-dependent: the D1 taps carry -U_i^n, U_i^n receives -D1 U) against the
+    oracle's literal transpose; the u0-only sweep (which still recomputes the forward levels) gives the same bits."""
+    from paper_1702_00496_gb300 import Solver
+    spec = _burgers(n, P, order, 3, 150 + order + tsteps, tsteps, scheme, r_alpha=0.01 if order == 6 else 0.02)
+    cfg = oracle.Config(spec)
+    rng = np.random.default_rng(6)
+    target = 0.5 * oracle.initial(cfg) + 0.1 * rng.standard_normal(cfg.shape)
+    nsteps = 60
+    grads = []
+    for want_alpha in (True, False):
+        s = Solver(spec)
+        s.adjoint_forward(nsteps, 7)
+        u = s.field().clone()
+        lam = u - torch.as_tensor(target, device="cuda")
+        J = 0.5 * float((lam * lam).sum())
+        g, ga = s.adjoint_backward(lam.clone(), want_alpha)
+        grads.append(g.clone())
+        s.close()
+        if want_alpha:
+            Jo, go, gao = oracle.adjoint(cfg, nsteps, target)
+            assert J == pytest.approx(Jo, rel=1e-11)
+            assert np.linalg.norm(g.cpu().numpy() - go) / np.linalg.norm(go) <= 1e-12
+            assert ga == pytest.approx(gao, rel=1e-10)
+    assert torch.equal(grads[0], grads[1])
