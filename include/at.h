@@ -211,10 +211,11 @@ int at_destroy(at_handle_t *hd);
  * lambda^{n+1} back through the merged taps to lambda^n and, for buffer points, through the extrapolation
  * weights w_m(k) of the replayed delay k to lambda^{n-k-m}.  dJ/dalpha = sum_n <lambda^{n+1}, dt D2_AT U^n>.
  * The paper has no adjoint; this is the exact discrete adjoint of the forward step of Sec. 4.1 / Tables
- * "atschemes-left/right" for orders 2, 4 and 6, schemes AT_SYNC, AT_ASYNC_STD and AT_AT, the linear equation
+ * "atschemes-left/right" for orders 2, 4 and 6, every scheme, the linear equation
  * and Burgers' equation (whose transpose is state-dependent: the first-derivative taps carry -U_i^n and U_i^n
  * itself receives -D1 U, so the backward sweep always recomputes the forward levels), with forward Euler or
- * Adams-Bashforth (other configurations, the rows expanded in space: AT_ERR_ARG).  An Adams-Bashforth run must start
+ * Adams-Bashforth, and for the rows expanded in space (AT_AT_SPACE2 / AT_AT_SPACE1: each edge row's taps send
+ * lambda to level n or n-k).  An Adams-Bashforth run must start
  * from a caller's field (at_reset with u0_dev; the analytic pre-history of a run from Eq. "IC" depends on alpha):
  * otherwise AT_ERR_STATE.  Its step n sends lambda^{n+1} to lambda^n (identity) and the adjoint of dt f^n,
  * mu^n = sum_m beta_m lambda^{n+1+m} over the later steps that use f^n, back through the transposed taps.

@@ -195,6 +195,96 @@ __device__ void adjoint_cell_burgers(const AdjParams &a, const uint8_t *__restri
   }
 }
 
+// Rows expanded in space (order 2, forward Euler), one output cell c.  A point i whose axis-a position is a PE
+// edge and whose side there has delay k > 0 takes that axis's edge row: each row tap t with i + j_t = c sends
+// ec_t lambda_i to level n (in-PE tap) or n - k (buffer tap).  Every other point reads c through the central taps
+// at level n.  c's own centre coefficient leaves out the axes on which c itself takes a row (the row's j = 0 tap
+// stands for it).  The alpha term uses the second-derivative part of the same rows (eq) or of the central taps.
+template <int DIM>
+__device__ void adjoint_cell_space(const AdjParams &a, const uint8_t *__restrict__ keff, int64_t n, int64_t ci,
+                                   const int c[3], double &galpha) {
+  const StepParams &f = a.f;
+  const int64_t N = f.ntot;
+  const double *ln = a.lam + ((n + 1) % a.Rl) * N;
+  const double *un = f.ring + (n % f.R) * N;
+  const int sn = (int)(n % f.R);
+  const int64_t stride[3] = {1, (int64_t)f.n[0], (int64_t)f.n[0] * f.n[1]};
+  int pidx[3] = {0, 0, 0}, krow[3] = {0, 0, 0}, srow[3] = {0, 0, 0};
+#pragma unroll
+  for (int ax = 0; ax < DIM; ++ax) pidx[ax] = c[ax] / f.S[ax];
+  double c0 = f.ts > 1 ? 0.0 : 1.0;
+#pragma unroll
+  for (int ax = 0; ax < DIM; ++ax) {
+    const int pos = c[ax] - pidx[ax] * f.S[ax];
+    if (f.use_pe[ax] && (pos == 0 || pos == f.S[ax] - 1)) {
+      srow[ax] = pos == 0 ? 0 : 1;
+      krow[ax] = keff[side_of<DIM>(f, pidx, ax, srow[ax])];
+    }
+    if (krow[ax] == 0) c0 += f.sc[ax];
+  }
+  double acc[AT_MAX_LAG];
+#pragma unroll
+  for (int l = 0; l < AT_MAX_LAG; ++l) acc[l] = 0.0;
+  const double lc = ln[ci];
+  acc[0] = fma(c0, lc, f.zero);
+  double d2 = 0.0;
+#pragma unroll
+  for (int ax = 0; ax < DIM; ++ax) {
+    const int jmax = f.use_pe[ax] ? 3 : 1;
+    for (int j = -jmax; j <= jmax; ++j) {
+      // point i = c - j along axis ax
+      const int ia = wrap_coord(c[ax] - j, f.n[ax]);
+      const int64_t i = ci + (int64_t)(ia - c[ax]) * stride[ax];
+      int ki = 0, si = 0;
+      if (f.use_pe[ax]) {
+        const int pi = ia / f.S[ax], posi = ia - pi * f.S[ax];
+        if (posi == 0 || posi == f.S[ax] - 1) {
+          int pid[3] = {pidx[0], pidx[1], pidx[2]};
+          pid[ax] = pi;
+          si = posi == 0 ? 0 : 1;
+          ki = keff[side_of<DIM>(f, pid, ax, si)];
+        }
+      }
+      if (ki > 0) {
+        const double li = ln[i];
+        for (int t = 0; t < f.ecount[ax][si]; ++t)
+          if (f.ej[ax][si][t] == j) {
+            const int l = f.ebuf[ax][si][t] ? ki : 0;
+            acc[l] = fma(f.ec[ax][si][t], li, acc[l]);
+          }
+      } else if (j == 1 || j == -1) {
+        acc[0] = fma(f.s[ax][j + 1], ln[i], acc[0]);
+      }
+    }
+    if (!a.alpha) continue;
+    // c's own second derivative along ax at step n
+    if (krow[ax] > 0) {
+      const int s = srow[ax];
+      for (int t = 0; t < f.ecount[ax][s]; ++t) {
+        const int cj = wrap_coord(c[ax] + f.ej[ax][s][t], f.n[ax]);
+        const int64_t cell = ci + (int64_t)(cj - c[ax]) * stride[ax];
+        const double *lvl = f.ebuf[ax][s][t] ? f.ring + slot_back(sn, krow[ax], f.R) * N : un;
+        d2 = fma(f.eq[ax][s][t], LdgNC::ld(lvl + cell), d2);
+      }
+    } else {
+      d2 = fma(f.qc[ax], LdgNC::ld(un + ci), d2);
+      for (int j = -1; j <= 1; j += 2) {
+        const int cj = wrap_coord(c[ax] + j, f.n[ax]);
+        d2 = fma(f.q[ax][j + 1], LdgNC::ld(un + ci + (int64_t)(cj - c[ax]) * stride[ax]), d2);
+      }
+    }
+  }
+  galpha = fma(lc, d2, galpha);
+  const int maxlag = a.reach;
+  for (int l = 0; l <= maxlag; ++l) {
+    const int64_t level = n - l;
+    if (level < 0) break;
+    double *slot = a.lam + (level % a.Rl) * N + ci;
+    if (l == maxlag) *slot = acc[l];
+    else if (l == 0 || acc[l] != 0.0) *slot = *slot + acc[l];
+  }
+}
+
 // Edge group: the four cells x0..x0+3 of row (y, z) when some of them lie within h of a PE edge (or the stencil
 // wraps around the domain).  Neighbour points i = c - j in another PE read c as a buffer point; their
 // contributions are summed per PE side (one side per axis, two along x) and sent to the levels n-k-m of that
@@ -340,7 +430,7 @@ template <int MODE>
 struct AdjBounds {
   static constexpr int min_blocks = MODE == 1 ? AT_ADJ_MIN_BLOCKS : 2;
 };
-template <int DIM, int H, int MODE, bool AL, bool AB, bool BG = false>
+template <int DIM, int H, int MODE, bool AL, bool AB, bool BG = false, bool SP = false>
 __global__ void __launch_bounds__(256, AdjBounds<MODE>::min_blocks) adjoint_step_kernel(const AdjParams a,
                                                                                       const int64_t n) {
   constexpr bool G = MODE != 0;
@@ -359,6 +449,7 @@ __global__ void __launch_bounds__(256, AdjBounds<MODE>::min_blocks) adjoint_step
         c[0] = (int)(i - yz * nx); c[2] = (int)(yz / ny); c[1] = (int)(yz - (int64_t)c[2] * ny);
       }
       if constexpr (BG && DIM == 1) adjoint_cell_burgers<H, AB>(a, keff, n, i, galpha);
+      else if constexpr (SP) adjoint_cell_space<DIM>(a, keff, n, i, c, galpha);
       else adjoint_cell<DIM, H, AB>(a, keff, n, i, c, galpha);
     }
   } else {
@@ -487,6 +578,12 @@ void launch_modes(const AdjParams &a, int64_t n, int nblk, bool grouped, cudaStr
   if constexpr (DIM == 1) {
     if (a.f.burgers) {  // per-cell path
       adjoint_step_kernel<1, H, 0, AL, AB, true><<<nblk, kAdjThreads, 0, st>>>(a, n);
+      return;
+    }
+  }
+  if constexpr (H == 1 && !AB) {
+    if (a.f.scheme >= AT_AT_SPACE2) {  // rows expanded in space: per-cell path
+      adjoint_step_kernel<DIM, 1, 0, AL, false, false, true><<<nblk, kAdjThreads, 0, st>>>(a, n);
       return;
     }
   }
@@ -625,13 +722,12 @@ cudaError_t copy_field(double *dst, const double *src, int64_t n, cudaStream_t s
 
 }  // namespace
 
-// The transposed step covers the central and time-expanded rows, orders 2, 4 and 6, forward Euler and
-// Adams-Bashforth runs started from a caller's field, the linear equation and Burgers' equation.
+// The transposed step covers every scheme (central, time-expanded and space-expanded rows), orders 2, 4 and 6,
+// forward Euler and Adams-Bashforth runs started from a caller's field, the linear and Burgers' equations.
 static int adjoint_supported(const at_handle *hd) {
   if (hd->sp.ts > 1 && hd->ab_analytic)
     return fail(AT_ERR_STATE, "adjoint: an Adams-Bashforth run must start from a caller's field (at_reset with "
                               "u0_dev): the analytic pre-history depends on alpha");
-  if (hd->sp.scheme >= AT_AT_SPACE2) return fail(AT_ERR_ARG, "adjoint: the rows expanded in space are not supported");
   return AT_OK;
 }
 

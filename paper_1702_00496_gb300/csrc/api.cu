@@ -129,8 +129,10 @@ static int space_rows(const at_config_t *cfg, int a, double dx, StepParams *p) {
           p->ej[a][side][slot] = (int8_t)j0[t];
           p->ebuf[a][side][slot] = (int8_t)l0[t];
           p->ec[a][side][slot] = 0.0;
+          p->eq[a][side][slot] = 0.0;
         }
         p->ec[a][side][slot] += cfg->dt * scale * c0[t];
+        if (deriv == 2) p->eq[a][side][slot] += cfg->dt * c0[t] / (dx * dx);
       }
     }
     p->ecount[a][side] = n;
@@ -177,7 +179,7 @@ int at_prepare_params(const at_config_t *cfg, double *ring_dev, uint8_t *log_dev
     for (int j = -h; j <= h; ++j) {
       const double v = cfg->dt * (-cfg->c[a] * c1.cd[j + h] / dx + cfg->alpha * c2.cd[j + h] / (dx * dx));
       const double dv = cfg->dt * c2.cd[j + h] / (dx * dx);
-      if (j == 0) { s0 += v; q0 += dv; p.sc[a] = v; } else { p.s[a][j + h] = v; p.q[a][j + h] = dv; }
+      if (j == 0) { s0 += v; q0 += dv; p.sc[a] = v; p.qc[a] = dv; } else { p.s[a][j + h] = v; p.q[a][j + h] = dv; }
       if (a == 0) {
         p.b1[j + h] = cfg->dt * c1.cd[j + h] / dx;
         p.b2[j + h] = cfg->dt * cfg->alpha * c2.cd[j + h] / (dx * dx);

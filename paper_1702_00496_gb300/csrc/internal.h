@@ -65,6 +65,10 @@ struct StepParams {
   int32_t burgers;                // 1: viscous Burgers' equation, f = -u D1 u + alpha D2 u (1D)
   double b1[2 * AT_MAX_H + 1];    // Burgers: dt cd1_j / dx (index j+h; the first derivative's taps)
   double b2[2 * AT_MAX_H + 1];    // Burgers: dt alpha cd2_j / dx^2
+  // For the adjoint's alpha term: the per-axis centre dt cd2_0 / dx_a^2 (q0 is their sum) and the second-derivative
+  // part dt c2 / dx_a^2 of each merged edge-row tap of the rows expanded in space.
+  double qc[3];
+  double eq[3][2][AT_MAX_ETAPS];
 };
 
 // The modes of one axis at one time t, prepared on the host for the rotation recurrence: sorted by wavenumber,

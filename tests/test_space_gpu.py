@@ -120,3 +120,33 @@ def test_cases_2_and_3_on_the_gpu(case):
     ratio = np.array([(g[L]["mean"] - g[100 + L]["mean"]) / g[100 + L]["mean"] / ((L - 1) / 2.0) for L in Ls])
     assert np.all(ratio > 0) and np.ptp(ratio) <= 0.15 * ratio.max(), ratio
     ens.close()
+
+
+SPACE_ADJ = [
+    ("1d_case3", lambda: W.wl_1d(256, 8, 2, 4, 0, 160, (1, 2, 3), scheme=W.AT_SPACE2, c=1.0)[0], 80),
+    ("1d_case2", lambda: W.wl_1d(256, 8, 2, 3, 0, 161, (1, 2, 3), scheme=W.AT_SPACE1, c=0.0)[0], 80),
+    ("1d_min_width", lambda: W.wl_1d(64, 32, 2, 3, 0, 162, (1, 3), scheme=W.AT_SPACE2, c=1.0)[0], 60),
+    ("3d_space2", lambda: W.wl_3d([16, 12, 8], [2, 3, 2], 2, 3, 0, 163, scheme=W.AT_SPACE2, c=(0.3, 0.2, 0.1))[0], 20),
+    ("3d_space1", lambda: W.wl_3d([16, 12, 8], [2, 3, 2], 2, 3, 0, 164, scheme=W.AT_SPACE1, c=(0.0, 0.0, 0.0))[0], 20),
+]
+
+
+@pytest.mark.parametrize("name,make,nsteps", SPACE_ADJ, ids=[c[0] for c in SPACE_ADJ])
+def test_adjoint_of_space_expanded_rows(name, make, nsteps):
+    """The transposed step through the edge rows (in-PE taps to level n, buffer taps to n - k) against the
+    oracle's literal transpose."""
+    from paper_1702_00496_gb300 import Solver
+    spec = make()
+    cfg = oracle.Config(spec)
+    rng = np.random.default_rng(8)
+    target = 0.5 * oracle.initial(cfg) + 0.1 * rng.standard_normal(cfg.shape)
+    s = Solver(spec)
+    s.adjoint_forward(nsteps, 9)
+    lam = s.field() - torch.as_tensor(target, device="cuda")
+    J = 0.5 * float((lam * lam).sum())
+    g, ga = s.adjoint_backward(lam.clone())
+    s.close()
+    Jo, go, gao = oracle.adjoint(cfg, nsteps, target)
+    assert J == pytest.approx(Jo, rel=1e-11)
+    assert np.linalg.norm(g.cpu().numpy() - go) / np.linalg.norm(go) <= 1e-12
+    assert ga == pytest.approx(gao, rel=1e-10)

@@ -98,3 +98,28 @@ def test_cases_2_and_3_asynchronous_error_is_linear_in_the_mean_delay(case):
     res = _sweep(*W.moment_members(case, Ls, range(300, 312)))
     ratio = np.array([(res[L][0] - res[L][1]) / res[L][1] / ((L - 1) / 2.0) for L in Ls])
     assert np.all(ratio > 0) and np.ptp(ratio) <= 0.15 * ratio.max(), ratio
+
+
+@pytest.mark.parametrize("scheme,c", [(W.AT_SPACE2, 1.0), (W.AT_SPACE1, 0.0)])
+def test_adjoint_of_the_space_expanded_rows_matches_central_differences(scheme, c):
+    spec, _ = W.wl_1d(64, 8, 2, 3, 0, 44, (1, 2, 3), scheme=scheme, c=c)
+    cfg = oracle.Config(spec)
+    rng = np.random.default_rng(9)
+    u0 = oracle.initial(cfg)
+    tgt = 0.5 * u0 + 0.1 * rng.standard_normal(cfg.shape)
+    nsteps = 50
+
+    def J(u, alpha=spec["alpha"]):
+        sp = dict(spec)
+        sp["alpha"] = alpha
+        uu, _, _ = oracle.run(oracle.Config(sp), nsteps, want_log=False, u0=u)
+        return 0.5 * float(np.sum((uu - tgt) ** 2))
+
+    Jo, g, ga = oracle.adjoint(cfg, nsteps, tgt)
+    assert Jo == pytest.approx(J(u0), rel=1e-14)
+    v = rng.standard_normal(cfg.shape)
+    assert float(np.sum(g * v)) == pytest.approx((J(u0 + 1e-3 * v) - J(u0 - 1e-3 * v)) / 2e-3, rel=1e-8)
+    a0, h = spec["alpha"], 1e-3 * spec["alpha"]
+    d1 = (J(u0, a0 + h) - J(u0, a0 - h)) / (2 * h)
+    d2 = (J(u0, a0 + h / 2) - J(u0, a0 - h / 2)) / h
+    assert ga == pytest.approx((4 * d2 - d1) / 3, rel=1e-6)
