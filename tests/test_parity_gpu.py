@@ -180,3 +180,17 @@ def test_launch_shapes_do_not_change_results():
             if ref is None:
                 ref = u
             assert torch.equal(u, ref), (threads, bps)
+
+
+# ------------------------------------------------------------ maximum sizes of the delay process
+@pytest.mark.parametrize("order,r_alpha", [(2, 0.05), (4, 0.02), (6, 0.005)])
+def test_largest_delay_range(order, r_alpha):
+    """L = 8, the largest delay range: delays 0..7, the deepest halo reach (ring of L + T = 8 + 4 levels at order 6)."""
+    spec, _ = W.wl_1d(4096, 16, order, 8, 0, 501, range(1, 6), r_alpha=r_alpha)
+    _compare(spec, 100)
+
+
+def test_largest_delay_range_3d_with_binned_delays():
+    spec, _ = W.wl_3d([16, 16, 12], [2, 2, 3], 4, 8, 0, 502, c=(0.2, 0.2, 0.2), dt=0.02 * W.dx_of(16) ** 2 / 0.05)
+    spec["thresholds"] = W.thresholds_from_probs([0.05, 0.05, 0.1, 0.1, 0.2, 0.2, 0.15, 0.15])
+    _compare(spec, 30)
