@@ -224,8 +224,10 @@ int at_destroy(at_handle_t *hd);
  *   steps (0: ceil(sqrt(nsteps))): checkpoints of the R-1 live levels, one segment of recomputed levels, the
  *   R-slot adjoint ring and small accumulators.
  * at_adjoint_forward: from step 0 (after at_init or at_reset), run nsteps forward steps exactly as at_step and
- *   keep the checkpoints in work_dev (caller-owned, 16-byte aligned).  Errors: AT_ERR_ARG, AT_ERR_STATE (not at
- *   step 0), AT_ERR_CUDA.
+ *   keep the checkpoints in work_dev (caller-owned, 16-byte aligned, untouched until at_adjoint_backward).  When
+ *   one segment covers the run (ckpt_every >= nsteps; workspace about nsteps + R fields), the steps run inside the
+ *   workspace, which then holds every level, and the backward sweep recomputes nothing.  Any later at_step or
+ *   at_reset discards the recorded pass.  Errors: AT_ERR_ARG, AT_ERR_STATE (not at step 0), AT_ERR_CUDA.
  * at_adjoint_backward: given lambda_dev = dJ/dU^nsteps (device, ntot doubles), write dJ/dU^0 to grad_u0_dev
  *   (device, ntot doubles) and dJ/dalpha to *grad_alpha_host.  Replays one checkpoint segment at a time:
  *   restores it, recomputes its levels with the forward kernel, runs its adjoint steps in reverse.  With

@@ -748,7 +748,31 @@ extern "C" int at_adjoint_forward(at_handle_t *hd, int64_t nsteps, int64_t ckpt_
   if (reinterpret_cast<uintptr_t>(work_dev) % 16) return fail(AT_ERR_ARG, "at_adjoint_forward: workspace not 16-byte aligned");
   const int64_t N = hd->sp.ntot, R = hd->sp.R;
   hd->adj_nsteps = -1;
-  for (int64_t c = 0; c < L.nck; ++c) {
+  hd->adj_resident = false;
+  if (L.nck == 1 && nsteps > 0) {
+    // One segment covers the whole run: step it inside the segment buffer, which then holds every level the
+    // backward sweep needs, so the sweep recomputes nothing.  The handle's ring gets the last live levels.
+    cudaStream_t st = hd->stream;
+    StepParams seg = hd->sp;
+    seg.ring = work_dev + L.seg;
+    seg.R = (int32_t)L.seg_depth;
+    seg.frhs = hd->sp.ts > 1 ? work_dev + L.segf : nullptr;
+    seg.keff = reinterpret_cast<uint8_t *>(work_dev + L.keff);
+    cudaError_t e = copy_field(seg.ring, hd->sp.ring, N, st);  // level 0
+    for (int64_t m = 0; m + 1 < hd->sp.ts && e == cudaSuccess; ++m)
+      e = copy_field(seg.frhs + m * N, hd->sp.frhs + m * N, N, st);
+    if (e == cudaSuccess) e = launch_draw_delays(seg, 0, st);
+    for (int64_t n = 0; n < nsteps && e == cudaSuccess; ++n) e = launch_forward_step(seg, n, nullptr, st);
+    for (int64_t lev = nsteps - R + 2; lev <= nsteps && e == cudaSuccess; ++lev)
+      if (lev >= 0) e = copy_field(hd->sp.ring + (lev % R) * N, seg.ring + (lev % seg.R) * N, N, st);
+    for (int64_t m = 0; m + 1 < hd->sp.ts && e == cudaSuccess; ++m)
+      e = copy_field(hd->sp.frhs + m * N, seg.frhs + m * N, N, st);
+    if (e == cudaSuccess) e = launch_draw_delays(hd->sp, nsteps, st);  // as at_step leaves them
+    if (e != cudaSuccess) return cuda_fail(e, "at_adjoint_forward");
+    hd->step = nsteps;
+    hd->adj_resident = true;
+  }
+  for (int64_t c = 0; !hd->adj_resident && c < L.nck; ++c) {
     const int64_t n0 = c * L.s;
     for (int64_t lev = n0 - R + 2; lev <= n0; ++lev) {
       if (lev < 0) continue;
@@ -804,7 +828,7 @@ extern "C" int at_adjoint_backward(at_handle_t *hd, const double *lambda_dev, do
   a.g_blk = w + L.gblk;
   a.alpha = want_alpha ? 1 : 0;
   // the linear transposed step needs the forward levels only for the alpha term; Burgers' always does
-  const bool need_fwd = want_alpha || hd->sp.burgers;
+  const bool need_fwd = (want_alpha || hd->sp.burgers) && !hd->adj_resident;  // resident: levels are in place
   a.list = reinterpret_cast<int32_t *>(w + L.list);
   a.list_len = 0;
   a.edge_len = 0;

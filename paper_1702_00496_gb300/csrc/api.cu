@@ -340,6 +340,7 @@ static int build_graph(at_handle *hd) {
 
 extern "C" int at_step(at_handle_t *hd, int64_t nsteps) {
   if (!hd || nsteps < 0) return fail(AT_ERR_ARG, "at_step: bad argument");
+  hd->adj_nsteps = -1;  // stepping on invalidates a recorded adjoint forward pass
   if (hd->sp.log && hd->step + nsteps > hd->log_steps) return fail(AT_ERR_STATE, "at_step: delay log is full");
   if (hd->step + nsteps > 0xFFFFFFFFll) return fail(AT_ERR_STATE, "at_step: step counter exceeds 32 bits");
   cudaError_t e;
@@ -377,6 +378,7 @@ extern "C" int at_reset(at_handle_t *hd, const double *u0_dev) {
   if (e == cudaSuccess) e = launch_draw_delays(hd->sp, 0, hd->stream);
   if (e != cudaSuccess) return cuda_fail(e, "at_reset");
   hd->step = 0;
+  hd->adj_nsteps = -1;  // a recorded adjoint forward pass no longer matches the handle
   return AT_OK;
 }
 

@@ -140,6 +140,7 @@ struct at_handle {
   double *adj_work = nullptr;    // caller's workspace
   int64_t adj_work_len = 0;
   bool ab_analytic = false;      // Adams-Bashforth run started from Eq. "IC" with the analytic pre-history
+  bool adj_resident = false;     // the forward pass kept every level in the workspace (one segment)
 };
 
 // Steps per captured graph: long runs replay one graph of kGraphSteps kernel nodes plus a counter update.
