@@ -151,6 +151,15 @@ def flops_per_update(spec) -> int:
     return f
 
 
+def fp64_ops_per_update(spec) -> int:
+    """FP64 instructions per interior point, what the FP64 pipe executes: the flops above are FMAs but the leading
+    multiplies (issued as FMAs onto zero) and Burgers' final add."""
+    h, ts = spec["order"] // 2, time_levels(spec)
+    if spec.get("burgers", 0):
+        return 4 * h + 2 + (ts if ts > 1 else 1)
+    return (flops_per_update(spec) + 1) // 2
+
+
 def bytes_per_update(spec) -> int:
     """Algorithmic HBM bytes per point and step: read U^n, write U^{n+1}; with Adams-Bashforth also read the ts-1
     stored right-hand sides and write dt f^n (halo reads of delayed levels are not counted)."""
@@ -498,6 +507,7 @@ def main():
                 "algorithmic_bytes_per_launch": bytes_launch,
                 "kernel": kname, "launch_ms": kern_ms,
                 "peak_source": "152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
+                "fp64_lanes_per_clk_sm": fp64_ops_per_update(spec) * ntot / (kern_ms / 1e3) / 152 / 2.07e9,
                 "hbm_gbs": bytes_launch / (kern_ms / 1e3) / 1e9,
                 "hbm_frac_of_measured": (bytes_launch / (kern_ms / 1e3) / 1e9 / hbm) if hbm else None}
 
