@@ -39,9 +39,9 @@ struct AdjParams {
   int32_t Rl;          // = L + T of the problem
   uint8_t *akeff;      // effective delays of the forward steps the backward sweep replays (two buffers)
   double *g_blk;       // per-block accumulators of d J / d alpha
-  const int32_t *list; // group indices of this launch (interior groups for MODE 1, edge groups for MODE 2)
-  int64_t list_len;
-  int64_t edge_len;    // on the host: the edge groups come first in the list
+  // grouped launches: positions list_off .. list_off + list_len - 1 of the step kernel's group order (interior
+  // groups first, then edge groups: f.order in 3D, group_1d_order in 1D); n_interior splits the two
+  int64_t list_off, list_len, n_interior;
   int32_t alpha;       // accumulate dJ/dalpha (needs the forward levels); 0: lambda only
   // Adams-Bashforth (kernels instantiated with AB): the transposed taps act on mu = sum_m beta_m lambda^{s+1} (the
   // adjoint of dt f^n), and lambda^{n+1} reaches lambda^n through the identity (s0 lacks the 1).
@@ -426,9 +426,12 @@ __device__ __forceinline__ void adjoint_group(const AdjParams &a, const uint8_t 
 #ifndef AT_ADJ_MIN_BLOCKS
 #define AT_ADJ_MIN_BLOCKS 3
 #endif
+#ifndef AT_ADJ_EDGE_MIN_BLOCKS
+#define AT_ADJ_EDGE_MIN_BLOCKS 2
+#endif
 template <int MODE>
 struct AdjBounds {
-  static constexpr int min_blocks = MODE == 1 ? AT_ADJ_MIN_BLOCKS : 2;
+  static constexpr int min_blocks = MODE == 1 ? AT_ADJ_MIN_BLOCKS : AT_ADJ_EDGE_MIN_BLOCKS;
 };
 template <int DIM, int H, int MODE, bool AL, bool AB, bool BG = false, bool SP = false>
 __global__ void __launch_bounds__(256, AdjBounds<MODE>::min_blocks) adjoint_step_kernel(const AdjParams a,
@@ -460,7 +463,7 @@ __global__ void __launch_bounds__(256, AdjBounds<MODE>::min_blocks) adjoint_step
     const int gx = nx >> 2;
     // the host partitions the groups into interior and edge lists, so a warp's lanes take the same path
     for (int64_t e = tid; e < a.list_len; e += nthreads) {
-      const int64_t g = a.list[e];
+      const int64_t g = DIM == 1 ? group_1d_order(f, a.list_off + e) : (int64_t)f.order[a.list_off + e];
       const int64_t r = g / gx;
       const int x0 = (int)(g - r * gx) << 2;
       const int z = DIM == 3 ? (int)(r / ny) : 0, y = DIM == 3 ? (int)(r - (int64_t)z * ny) : 0;
@@ -589,10 +592,10 @@ void launch_modes(const AdjParams &a, int64_t n, int nblk, bool grouped, cudaStr
   }
   if (grouped) {
     AdjParams e = a, i = a;
-    e.list = a.list;
-    e.list_len = a.edge_len;
-    i.list = a.list + a.edge_len;
-    i.list_len = a.list_len - a.edge_len;
+    e.list_off = a.n_interior;
+    e.list_len = a.list_len - a.n_interior;
+    i.list_off = 0;
+    i.list_len = a.n_interior;
     adjoint_step_kernel<DIM, H, 2, AL, AB><<<nblk, kAdjThreads, 0, st>>>(e, n);
     adjoint_step_kernel<DIM, H, 1, AL, AB><<<nblk, kAdjThreads, 0, st>>>(i, n);
   } else {
@@ -612,27 +615,15 @@ void launch_alpha(const AdjParams &a, int64_t n, int nblk, bool grouped, cudaStr
 }
 
 bool adjoint_grouped(const AdjParams &a) {
-  return a.f.n[0] % 4 == 0 && (!a.f.use_pe[0] || a.f.S[0] % 4 == 0) &&
+  return a.f.n[0] % 4 == 0 && (!a.f.use_pe[0] || a.f.S[0] % 4 == 0) && (a.f.dim == 1 || a.f.order != nullptr) &&
          (reinterpret_cast<uintptr_t>(a.lam) % 16) == 0 && (reinterpret_cast<uintptr_t>(a.f.ring) % 16) == 0;
 }
 
-// Group g (x0 = 4 (g mod nx/4), row g div nx/4) is interior when its cells and all their stencil neighbours lie in
-// its PE and away from the domain ends: the straight path of the interior launch applies.
-bool group_interior(const StepParams &f, int64_t g) {
-  const int h = f.h, nx = (int)f.n[0], gx = nx / 4, W = (h + 1) / 2 * 2;  // the x window's half-width
-  const int64_t r = g / gx;
-  const int x0 = (int)(g - r * gx) * 4;
-  const int px = x0 % f.S[0];
-  bool in = x0 >= W && x0 + 4 + W <= nx && (!f.use_pe[0] || (px >= h && px + 3 < f.S[0] - h));
-  if (f.dim == 3) {
-    const int z = (int)(r / f.n[1]), y = (int)(r - (int64_t)z * f.n[1]);
-    const int py = y % f.S[1], pz = z % f.S[2];
-    in = in && y >= h && y + h < f.n[1] && (!f.use_pe[1] || (py >= h && py < f.S[1] - h)) && z >= h &&
-         z + h < f.n[2] && (!f.use_pe[2] || (pz >= h && pz < f.S[2] - h));
-  }
-  return in;
-}
-
+// The interior launch's straight path needs a group whose cells and stencil neighbours (the x window of W = h
+// rounded up to even cells on each side) lie in its PE and away from the domain ends.  The step kernel's order
+// lists exactly those groups first (3D: built at at_init; 1D: group_1d_order, every group of a PE but its first
+// and last): with x0 a multiple of 4 and h <= 3, x0 >= h implies x0 >= W and x0 + 3 + h < n implies
+// x0 + 3 + W < n, so the two definitions agree.
 cudaError_t launch_adjoint_step(const AdjParams &a, int64_t n, int nblk, cudaStream_t st) {
   const bool grouped = adjoint_grouped(a);
   if (a.f.dim == 1) {
@@ -683,13 +674,16 @@ int cuda_fail(cudaError_t e, const char *where) {
 namespace {
 
 // Workspace layout (doubles, each part rounded up to 32 doubles):
-//   checkpoints  nck x (R-1) x ntot     levels n0-R+2 .. n0 of every checkpoint n0 = 0, s, 2s, ...
-//   segment      (s + R - 1) x ntot     levels of the segment being replayed (level m in slot m mod depth)
-//   lambda       R x ntot               adjoint ring
-//   g_blk        nblk                   per-block d J / d alpha accumulators, then the sum
-//   delays       2 x 2 x nb bytes       effective delays of the recompute and of the backward sweep
+//   checkpoints  nck x (R-1+ts-1) x ntot  levels n0-R+2 .. n0 and the ts-1 stored right-hand sides of every
+//                                         checkpoint n0 = 0, s, 2s, ...
+//   segment      (s + R - 1) x ntot       levels of the segment being replayed (level m in slot m mod depth)
+//   segment rhs  (ts - 1) x ntot          its stored right-hand sides (Adams-Bashforth)
+//   lambda       (R + ts - 1) x ntot      adjoint ring
+//   mu           ntot                     Adams-Bashforth: the adjoint of dt f^n
+//   g_blk        nblk                     per-block d J / d alpha accumulators, then the sum
+//   delays       2 x 2 x nb bytes         effective delays of the recompute and of the backward sweep
 struct AdjLayout {
-  int64_t s, nck, seg_depth, ck_fields, lam_slots, ck, seg, segf, lam, mu, gblk, keff, list, total;
+  int64_t s, nck, seg_depth, ck_fields, lam_slots, ck, seg, segf, lam, mu, gblk, keff, total;
 };
 
 int64_t up32(int64_t v) { return (v + 31) / 32 * 32; }
@@ -711,8 +705,7 @@ AdjLayout layout(const at_handle *hd, int64_t nsteps, int64_t every) {
   L.mu = L.lam + up32(L.lam_slots * N);
   L.gblk = L.mu + up32(nf > 0 ? N : 0);
   L.keff = L.gblk + up32(adj_blocks() + 1);
-  L.list = L.keff + up32((4 * hd->sp.nb + 7) / 8);
-  L.total = L.list + up32((hd->sp.ntot / 4 + 1) / 2);
+  L.total = L.keff + up32((4 * hd->sp.nb + 7) / 8);
   return L;
 }
 
@@ -829,22 +822,18 @@ extern "C" int at_adjoint_backward(at_handle_t *hd, const double *lambda_dev, do
   a.alpha = want_alpha ? 1 : 0;
   // the linear transposed step needs the forward levels only for the alpha term; Burgers' always does
   const bool need_fwd = (want_alpha || hd->sp.burgers) && !hd->adj_resident;  // resident: levels are in place
-  a.list = reinterpret_cast<int32_t *>(w + L.list);
+  // grouped shapes: the interior launch takes the head of the step kernel's group order, the edge launch the rest
+  a.list_off = 0;
   a.list_len = 0;
-  a.edge_len = 0;
-  if (adjoint_grouped(a)) {  // edge groups first, then interior groups
-    const int64_t groups = N / 4;
-    std::vector<int32_t> list;
-    list.reserve((size_t)groups);
-    for (int64_t g = 0; g < groups; ++g)
-      if (!group_interior(seg, g)) list.push_back((int32_t)g);
-    a.edge_len = (int64_t)list.size();
-    for (int64_t g = 0; g < groups; ++g)
-      if (group_interior(seg, g)) list.push_back((int32_t)g);
-    a.list_len = (int64_t)list.size();
-    e = cudaMemcpyAsync(w + L.list, list.data(), sizeof(int32_t) * list.size(), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(e, "at_adjoint_backward: group lists");
+  a.n_interior = 0;
+  if (adjoint_grouped(a)) {
+    a.list_len = N / 4;
+    if (hd->sp.dim == 3) {
+      a.n_interior = hd->n_interior;
+    } else {  // group_1d_order: the groups between the first and the last of each PE, PE by PE
+      const int64_t gS = (hd->sp.use_pe[0] ? hd->sp.S[0] : hd->sp.n[0]) / 4;
+      a.n_interior = gS < 3 ? 0 : (hd->sp.n[0] / 4 / gS) * (gS - 2);
+    }
   }
   // lambda^Ns = the caller's seed; the R-2 older levels start at zero; alpha accumulators at zero
   e = copy_field(a.lam + (Ns % Rl) * N, lambda_dev, N, st);

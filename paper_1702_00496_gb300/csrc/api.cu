@@ -262,6 +262,7 @@ extern "C" int at_init(const at_config_t *cfg, double *ring_dev, int64_t ring_le
   const size_t keff_bytes = (size_t)(2 * p.nb + 255) / 256 * 256;
   // 3D grouped shapes: visit interior groups first, then edge groups, so a warp's lanes share one path
   std::vector<int32_t> order;
+  int64_t n_interior = 0;
   if (cfg->dim == 3 && cfg->n[0] % 4 == 0 && (p.use_pe[0] == 0 || p.S[0] % 4 == 0)) {
     const int64_t gx = cfg->n[0] / 4, groups = ntot / 4;
     const int h = cfg->order / 2;
@@ -279,6 +280,7 @@ extern "C" int at_init(const at_config_t *cfg, double *ring_dev, int64_t ring_le
     order.reserve((size_t)groups);
     for (int64_t g = 0; g < groups; ++g)
       if (interior(g)) order.push_back((int32_t)g);
+    n_interior = (int64_t)order.size();
     for (int64_t g = 0; g < groups; ++g)
       if (!interior(g)) order.push_back((int32_t)g);
   }
@@ -292,6 +294,7 @@ extern "C" int at_init(const at_config_t *cfg, double *ring_dev, int64_t ring_le
   hd->d_step = (int64_t *)(base + 256);
   p.keff = (uint8_t *)(base + 512);
   p.order = order.empty() ? nullptr : (const int32_t *)(base + 512 + keff_bytes);
+  hd->n_interior = n_interior;
   hd->d_partials = (double *)(base + 512 + keff_bytes + order_bytes);
   if (!order.empty() &&
       (e = cudaMemcpy((void *)p.order, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice)) !=

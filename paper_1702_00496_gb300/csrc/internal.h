@@ -141,6 +141,7 @@ struct at_handle {
   int64_t adj_work_len = 0;
   bool ab_analytic = false;      // Adams-Bashforth run started from Eq. "IC" with the analytic pre-history
   bool adj_resident = false;     // the forward pass kept every level in the workspace (one segment)
+  int64_t n_interior = 0;        // 3D grouped shapes: interior groups at the head of sp.order
 };
 
 // Steps per captured graph: long runs replay one graph of kGraphSteps kernel nodes plus a counter update.
