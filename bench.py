@@ -326,7 +326,7 @@ def run_adjoint(args, rank: int, world: int, local: int):
     s = Solver(spec, device=f"cuda:{local}", stream=stream)
     target = torch.zeros(ntot, dtype=torch.float64, device=f"cuda:{local}")
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
-    fwd, adj, adj_u0 = [], [], []
+    fwd, adj, adj_u0, bwd = [], [], [], []
     for it in range(args.warmup + args.steps):
         s.reset()
         a, b = ev(), ev()
@@ -334,9 +334,10 @@ def run_adjoint(args, rank: int, world: int, local: int):
         s.step(T)
         b.record(stream)
         s.reset()
-        c, d = ev(), ev()
+        c, m, d = ev(), ev(), ev()
         c.record(stream)
         s.adjoint_forward(T, args.adjoint_every)
+        m.record(stream)
         lam = s.field().reshape(-1) - target
         g, ga = s.adjoint_backward(lam)
         d.record(stream)
@@ -350,6 +351,7 @@ def run_adjoint(args, rank: int, world: int, local: int):
         if it >= args.warmup:
             fwd.append(a.elapsed_time(b))
             adj.append(c.elapsed_time(d))
+            bwd.append(m.elapsed_time(d))
             adj_u0.append(e.elapsed_time(f))
     s.close()
     f_ms, a_ms = statistics.median(fwd), statistics.median(adj)
@@ -361,10 +363,13 @@ def run_adjoint(args, rank: int, world: int, local: int):
                            "checkpoint_every": args.adjoint_every or "sqrt(T)",
                            "levels_resident": args.adjoint_every >= T},
                 "forward_ms": f_ms, "adjoint_ms": a_ms, "adjoint_forward_ratio": a_ms / f_ms,
+                "backward_ms": statistics.median(bwd),
+                "backward_step_forward_step_ratio": statistics.median(bwd) / f_ms,
                 "adjoint_u0_only_ms": statistics.median(adj_u0),
                 "adjoint_u0_only_forward_ratio": statistics.median(adj_u0) / f_ms,
                 "note": "adjoint_ms = forward pass with checkpoints + backward sweep (restore, recompute, transposed "
-                        "steps) for dJ/du0 and dJ/dalpha; the u0-only sweep needs no recompute; with every level "
+                        "steps) for dJ/du0 and dJ/dalpha; backward_ms = the sweep alone, T backward steps against "
+                        "forward_ms's T forward steps; the u0-only sweep needs no recompute; with every level "
                         "resident (--adjoint-every >= T) the forward pass keeps all levels and nothing is recomputed",
                 "grad_alpha": ga}
         print(json.dumps(line), flush=True)

@@ -285,10 +285,92 @@ __device__ void adjoint_cell_space(const AdjParams &a, const uint8_t *__restrict
   }
 }
 
+// x taps of the four cells of an edge group: tap j of cell q reads window element t = q + W - j (point i = c - j).
+// XT bit 0: the group starts its PE, so the elements t < W lie in the lower x neighbour PE (they read c across
+// that PE's upper side) and go to X0; bit 1: the group ends its PE, elements t >= W + 4 lie in the upper one (X1).
+// Everything else goes to A.  The buckets are fixed at compile time, so no FMA is issued for a bucket not taken.
+template <int H, int XT>
+__device__ __forceinline__ void adj_x_taps(const StepParams &f, const double *lv, double A[4], double X0[4],
+                                           double X1[4]) {
+  constexpr int W = XWin<H>::W;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+#pragma unroll
+    for (int j = -H; j <= H; ++j) {
+      if (j == 0) continue;
+      const int t = q + W - j;
+      const double s = f.s[0][j + H];
+      if ((XT & 1) && t < W) X0[q] = fma(s, lv[t], X0[q]);
+      else if ((XT & 2) && t >= W + 4) X1[q] = fma(s, lv[t], X1[q]);
+      else A[q] = fma(s, lv[t], A[q]);
+    }
+  }
+}
+
+// y or z taps of an edge group (3D): points i = c - j along the axis (rows of four cells at stride st).  SIDE 1: the
+// row sits at pos = H - CNT, so the taps j > pos (j > H - CNT) reach the lower neighbour PE; SIDE 2: the row sits at
+// pos = S - 1 - H + CNT, so the taps j <= pos - S (j < CNT - H) reach the upper one; SIDE 0: every tap stays in the
+// PE.  Taps that cross go to X, the others to A.
+template <int H, int SIDE, int CNT>
+__device__ __forceinline__ void adj_axis_taps(const StepParams &f, int ax, const double *__restrict__ ln, int64_t i0,
+                                              int c, int na, int64_t st, double A[4], double X[4]) {
+#pragma unroll
+  for (int j = -H; j <= H; ++j) {
+    if (j == 0) continue;
+    const int ia = wrap_coord(c - j, na);
+    const int64_t base = i0 + (int64_t)(ia - c) * st;
+    const double2 e = LdgNC::ld2(ln + base), g = LdgNC::ld2(ln + base + 2);
+    const double lr[4] = {e.x, e.y, g.x, g.y};
+    const double s = f.s[ax][j + H];
+    const bool cross = (SIDE == 1 && j > H - CNT) || (SIDE == 2 && j < CNT - H);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (cross) X[q] = fma(s, lr[q], X[q]);
+      else A[q] = fma(s, lr[q], A[q]);
+    }
+  }
+}
+
+// Case index of an axis position: 0 away from the PE faces, CNT (1..H) for a row CNT cells inside the lower face
+// region (pos = H - CNT), H + CNT for CNT cells inside the upper one (pos = S - 1 - H + CNT).
+__device__ __forceinline__ int axis_case(const StepParams &f, int ax, int pos, int H) {
+  if (!f.use_pe[ax]) return 0;
+  if (pos < H) return H - pos;
+  if (pos > f.S[ax] - 1 - H) return H + pos - (f.S[ax] - 1 - H);
+  return 0;
+}
+
+// Side index of the neighbour PE across this PE's lower (or upper) face along axis ax: its upper (lower) side.
+template <int DIM>
+__device__ __forceinline__ int64_t neighbour_side(const StepParams &f, const int pidx[3], int ax, bool lower) {
+  int pid[3] = {pidx[0], pidx[1], pidx[2]};
+  pid[ax] = lower ? (pidx[ax] + f.pe[ax] - 1) % f.pe[ax] : (pidx[ax] + 1) % f.pe[ax];
+  return side_of<DIM>(f, pid, ax, lower ? 1 : 0);
+}
+
+template <int H>
+__device__ __forceinline__ void adj_axis_dispatch(const StepParams &f, int ax, int cs, const double *__restrict__ ln,
+                                                  int64_t i0, int c, int na, int64_t st, double A[4], double X[4]) {
+  switch (cs) {
+    case 1: adj_axis_taps<H, 1, 1>(f, ax, ln, i0, c, na, st, A, X); break;
+    case 2: if constexpr (H >= 2) adj_axis_taps<H, 1, 2>(f, ax, ln, i0, c, na, st, A, X);
+            else adj_axis_taps<H, 2, 1>(f, ax, ln, i0, c, na, st, A, X);
+            break;
+    case 3: if constexpr (H >= 3) adj_axis_taps<H, 1, 3>(f, ax, ln, i0, c, na, st, A, X);
+            else adj_axis_taps<H, 2, 3 - H>(f, ax, ln, i0, c, na, st, A, X);
+            break;
+    case 4: adj_axis_taps<H, 2, (4 - H > 0 ? 4 - H : 1)>(f, ax, ln, i0, c, na, st, A, X); break;
+    case 5: adj_axis_taps<H, 2, (5 - H > 0 ? 5 - H : 1)>(f, ax, ln, i0, c, na, st, A, X); break;
+    case 6: adj_axis_taps<H, 2, (6 - H > 0 ? 6 - H : 1)>(f, ax, ln, i0, c, na, st, A, X); break;
+    default: adj_axis_taps<H, 0, 0>(f, ax, ln, i0, c, na, st, A, X); break;
+  }
+}
+
 // Edge group: the four cells x0..x0+3 of row (y, z) when some of them lie within h of a PE edge (or the stencil
 // wraps around the domain).  Neighbour points i = c - j in another PE read c as a buffer point; their
 // contributions are summed per PE side (one side per axis, two along x) and sent to the levels n-k-m of that
-// side's delay k with weights w_m(k).  The fresh level n-R+2 is zeroed before any contribution lands in it.
+// side's delay k with weights w_m(k) (k = 0: level n itself).  The fresh level n-R+2 is zeroed before any
+// contribution lands in it.
 template <int DIM, int H, bool AB>
 __device__ __forceinline__ void adjoint_group(const AdjParams &a, const uint8_t *__restrict__ keff, int64_t n, int x0,
                                               int y, int z, double &galpha) {
@@ -322,17 +404,14 @@ __device__ __forceinline__ void adjoint_group(const AdjParams &a, const uint8_t 
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) galpha = fma(lv[q + W], d[q], galpha);
-  // x: window element t is point i = x0-W+t; rel < 0 lies in the lower PE (reads c on its high side),
-  // rel >= S in the upper PE (reads c on its low side)
-  int kxl = 0, kxr = 0;
-  if (f.use_pe[0]) {
-    int pl[3] = {(pidx[0] + f.pe[0] - 1) % f.pe[0], pidx[1], pidx[2]};
-    int pr[3] = {(pidx[0] + 1) % f.pe[0], pidx[1], pidx[2]};
-    kxl = keff[side_of<DIM>(f, pl, 0, 1)];
-    kxr = keff[side_of<DIM>(f, pr, 0, 0)];
-  }
-  double A[4], X[4][4];  // X[0]: lower x PE, X[1]: upper x PE, X[2]: y neighbour PE, X[3]: z neighbour PE
-  int kX[4] = {kxl, kxr, 0, 0};
+  // x: x0 is a multiple of 4 and h <= 3 < 4, so only a group at the start of its PE (pos 0) reaches the lower
+  // PE and only one at its end (pos S-4) the upper; with S = 4 both
+  int xt = 0;
+  if (f.use_pe[0]) xt = (pos[0] == 0 ? 1 : 0) | (pos[0] + 4 == f.S[0] ? 2 : 0);
+  // X[0]: lower x PE, X[1]: upper x PE, X[2]: y neighbour PE, X[3]: z neighbour PE; kX[b] its side's delay, -1 for
+  // a bucket this group does not feed
+  double A[4], X[4][4];
+  int kX[4] = {-1, -1, -1, -1};
   double id[4] = {f.zero, f.zero, f.zero, f.zero};
   if (AB) {
     const double2 e0 = LdgNC::ld2(lnext + i0), e1 = LdgNC::ld2(lnext + i0 + 2);
@@ -342,49 +421,28 @@ __device__ __forceinline__ void adjoint_group(const AdjParams &a, const uint8_t 
   for (int q = 0; q < 4; ++q) {
     A[q] = fma(f.s0, lv[q + W], id[q]);
     X[0][q] = X[1][q] = X[2][q] = X[3][q] = 0.0;
-#pragma unroll
-    for (int j = -H; j <= H; ++j) {
-      if (j == 0) continue;
-      const int t = q + W - j;
-      const int rel = pos[0] - W + t;
-      const double s = f.s[0][j + H];
-      if (rel < 0 && kxl > 0) X[0][q] = fma(s, lv[t], X[0][q]);
-      else if (rel >= f.S[0] && kxr > 0) X[1][q] = fma(s, lv[t], X[1][q]);
-      else A[q] = fma(s, lv[t], A[q]);
-    }
   }
-  if (DIM == 3) {
+  if (xt & 1) kX[0] = keff[neighbour_side<DIM>(f, pidx, 0, true)];
+  if (xt & 2) kX[1] = keff[neighbour_side<DIM>(f, pidx, 0, false)];
+  switch (xt) {
+    case 1: adj_x_taps<H, 1>(f, lv, A, X[0], X[1]); break;
+    case 2: adj_x_taps<H, 2>(f, lv, A, X[0], X[1]); break;
+    case 3: adj_x_taps<H, 3>(f, lv, A, X[0], X[1]); break;
+    default: adj_x_taps<H, 0>(f, lv, A, X[0], X[1]); break;
+  }
+  if (DIM == 3) {  // y then z, written out so the buckets stay in registers
+    const int cy = axis_case(f, 1, pos[1], H), cz = axis_case(f, 2, pos[2], H);
+    if (cy > 0) kX[2] = keff[neighbour_side<DIM>(f, pidx, 1, cy <= H)];
+    if (cz > 0) kX[3] = keff[neighbour_side<DIM>(f, pidx, 2, cz <= H)];
+    adj_axis_dispatch<H>(f, 1, cy, ln, i0, y, f.n[1], (int64_t)nx, A, X[2]);
+    adj_axis_dispatch<H>(f, 2, cz, ln, i0, z, f.n[2], (int64_t)nx * f.n[1], A, X[3]);
+  }
+  // delay 0: the crossing taps read level n itself
 #pragma unroll
-    for (int ax = 1; ax < 3; ++ax) {
-      const int c = ax == 1 ? y : z, na = f.n[ax];
-      const int64_t st = ax == 1 ? (int64_t)nx : (int64_t)nx * f.n[1];
+  for (int b = 0; b < 4; ++b) {
+    if (kX[b] != 0) continue;
 #pragma unroll
-      for (int j = -H; j <= H; ++j) {
-        if (j == 0) continue;
-        const int ia = wrap_coord(c - j, na);
-        const int64_t base = i0 + (int64_t)(ia - c) * st;
-        int k = 0;
-        if (f.use_pe[ax]) {
-          const int pi = ia / f.S[ax];
-          if (pi != pidx[ax]) {
-            int pid[3] = {pidx[0], pidx[1], pidx[2]};
-            pid[ax] = pi;
-            k = keff[side_of<DIM>(f, pid, ax, j > 0 ? 1 : 0)];
-          }
-        }
-        const double2 e = LdgNC::ld2(ln + base), g = LdgNC::ld2(ln + base + 2);
-        const double lr[4] = {e.x, e.y, g.x, g.y};
-        const double s = f.s[ax][j + H];
-        if (k > 0) {
-          kX[ax + 1] = k;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) X[ax + 1][q] = fma(s, lr[q], X[ax + 1][q]);
-        } else {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) A[q] = fma(s, lr[q], A[q]);
-        }
-      }
-    }
+    for (int q = 0; q < 4; ++q) A[q] += X[b][q];
   }
   const int64_t fresh = n - a.reach;
   const int snl = (int)(n % a.Rl);
@@ -407,7 +465,7 @@ __device__ __forceinline__ void adjoint_group(const AdjParams &a, const uint8_t 
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
     const int k = kX[b];
-    if (k == 0) continue;
+    if (k <= 0) continue;
     for (int m = 0; m < f.T; ++m) {
       const double wk = f.w[k][m];
       double2 *o = reinterpret_cast<double2 *>(a.lam + slot_back(snl, k + m, a.Rl) * N + i0);

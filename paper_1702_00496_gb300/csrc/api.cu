@@ -277,12 +277,35 @@ extern "C" int at_init(const at_config_t *cfg, double *ring_dev, int64_t ring_le
       }
       return true;
     };
+    // edge groups sorted by how they meet the PE faces (counting sort, g ascending within a kind): the x faces
+    // the group touches, and per y and z axis the cell count into the lower / upper face region, so a warp's
+    // lanes mostly take the same branches
+    const int nc = 2 * h + 1;
+    auto axis_kind = [&](int a, int c) {
+      if (!p.use_pe[a]) return 0;
+      const int pos = c % p.S[a];
+      if (pos < h) return h - pos;
+      if (pos > p.S[a] - 1 - h) return h + pos - (p.S[a] - 1 - h);
+      return 0;
+    };
+    auto kind = [&](int64_t g) {
+      const int64_t r = g / gx;
+      const int x0 = (int)(g - r * gx) * 4, z = (int)(r / cfg->n[1]), y = (int)(r - (int64_t)z * cfg->n[1]);
+      int xt = 0;
+      if (p.use_pe[0]) xt = (x0 % p.S[0] == 0 ? 1 : 0) | (x0 % p.S[0] + 4 == p.S[0] ? 2 : 0);
+      return (xt * nc + axis_kind(1, y)) * nc + axis_kind(2, z);
+    };
     order.reserve((size_t)groups);
-    for (int64_t g = 0; g < groups; ++g)
+    std::vector<int64_t> start((size_t)(4 * nc * nc + 1), 0);
+    for (int64_t g = 0; g < groups; ++g) {
       if (interior(g)) order.push_back((int32_t)g);
+      else ++start[(size_t)kind(g) + 1];
+    }
     n_interior = (int64_t)order.size();
+    for (size_t k = 1; k < start.size(); ++k) start[k] += start[k - 1];
+    order.resize((size_t)groups);
     for (int64_t g = 0; g < groups; ++g)
-      if (!interior(g)) order.push_back((int32_t)g);
+      if (!interior(g)) order[(size_t)(n_interior + start[(size_t)kind(g)]++)] = (int32_t)g;
   }
   const size_t order_bytes = (order.size() * sizeof(int32_t) + 255) / 256 * 256;
   const size_t bytes = 512 + keff_bytes + order_bytes +

@@ -39,6 +39,9 @@ CASES = [
     ("1d_o6_point_path", lambda: W.wl_1d(250, 5, 6, 4, 0, 69, (1, 2), r_alpha=0.02)[0], 50),
     ("3d_o6", lambda: W.wl_3d([24, 16, 16], [2, 2, 2], 6, 3, 0, 70, c=(0.3, 0.2, 0.1), dt=0.02 * W.dx_of(24) ** 2 / 0.05)[0],
      20),
+    # PEs of 4 = 2h cells: each group starts and ends its PE, so its x taps reach both neighbour PEs
+    ("1d_o4_pe_width_4", lambda: W.wl_1d(64, 16, 4, 3, 0, 75, (1, 2, 3))[0], 60),
+    ("3d_o4_pe_width_4", lambda: W.wl_3d([8, 8, 12], [2, 2, 3], 4, 3, 0, 76, c=(0.3, 0.2, 0.1))[0], 20),
 ]
 
 
