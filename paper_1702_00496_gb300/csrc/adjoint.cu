@@ -485,14 +485,16 @@ __device__ __forceinline__ void adjoint_group(const AdjParams &a, const uint8_t 
 #define AT_ADJ_MIN_BLOCKS 3
 #endif
 #ifndef AT_ADJ_EDGE_MIN_BLOCKS
-#define AT_ADJ_EDGE_MIN_BLOCKS 2
+#define AT_ADJ_EDGE_MIN_BLOCKS 4
 #endif
-template <int MODE>
+// Blocks per SM the register allocation must allow: the edge launch of order 4 runs four (256^3, order 4: 3 %
+// faster than two, in spite of a few spilled registers); order 6 spills too much there, order 2 was not measured.
+template <int MODE, int H>
 struct AdjBounds {
-  static constexpr int min_blocks = MODE == 1 ? AT_ADJ_MIN_BLOCKS : AT_ADJ_EDGE_MIN_BLOCKS;
+  static constexpr int min_blocks = MODE == 1 ? AT_ADJ_MIN_BLOCKS : (MODE == 2 && H == 2 ? AT_ADJ_EDGE_MIN_BLOCKS : 2);
 };
 template <int DIM, int H, int MODE, bool AL, bool AB, bool BG = false, bool SP = false>
-__global__ void __launch_bounds__(256, AdjBounds<MODE>::min_blocks) adjoint_step_kernel(const AdjParams a,
+__global__ void __launch_bounds__(256, AdjBounds<MODE, H>::min_blocks) adjoint_step_kernel(const AdjParams a,
                                                                                       const int64_t n) {
   constexpr bool G = MODE != 0;
   const StepParams &f = a.f;
