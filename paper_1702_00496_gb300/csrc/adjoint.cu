@@ -39,9 +39,9 @@ struct AdjParams {
   int32_t Rl;          // = L + T of the problem
   uint8_t *akeff;      // effective delays of the forward steps the backward sweep replays (two buffers)
   double *g_blk;       // per-block accumulators of d J / d alpha
-  // grouped launches: positions list_off .. list_off + list_len - 1 of the step kernel's group order (interior
-  // groups first, then edge groups: f.order in 3D, group_1d_order in 1D); n_interior splits the two
-  int64_t list_off, list_len, n_interior;
+  // grouped shapes: the step kernel's group order (interior groups first, then edge groups: f.order in 3D,
+  // group_1d_order in 1D), list_len groups of which the first n_interior are interior
+  int64_t list_len, n_interior;
   int32_t alpha;       // accumulate dJ/dalpha (needs the forward levels); 0: lambda only
   // Adams-Bashforth (kernels instantiated with AB): the transposed taps act on mu = sum_m beta_m lambda^{s+1} (the
   // adjoint of dt f^n), and lambda^{n+1} reaches lambda^n through the identity (s0 lacks the 1).
@@ -476,31 +476,25 @@ __device__ __forceinline__ void adjoint_group(const AdjParams &a, const uint8_t 
   }
 }
 
-// Backward step n.  G: cells come in groups of four x points (n[0] % 4 == 0, 16-byte aligned slots); a group
-// whose cells and neighbours all lie inside one PE and away from the domain ends takes the straight path.
-// MODE 0: every cell by the general path (shapes without groups of four).  MODE 1: interior groups only.
-// MODE 2: edge groups only, plus the draw of the delays of step n-1.  The two grouped launches of a step touch
-// disjoint cells and add their alpha partials into the same per-block slots in launch order.
+// Backward step n, one launch, which also draws the delays of step n-1.  MODE 0: every cell by the general path
+// (shapes without groups of four).  MODE 1: cells in groups of four x points (n[0] % 4 == 0, 16-byte aligned
+// slots); a group whose cells and neighbours all lie inside one PE and away from the domain ends takes the
+// straight path, the others the edge path (adjoint_group).
 #ifndef AT_ADJ_MIN_BLOCKS
 #define AT_ADJ_MIN_BLOCKS 3
 #endif
-#ifndef AT_ADJ_EDGE_MIN_BLOCKS
-#define AT_ADJ_EDGE_MIN_BLOCKS 4
-#endif
-// Blocks per SM the register allocation must allow: the edge launch of order 4 runs four (256^3, order 4: 3 %
-// faster than two, in spite of a few spilled registers); order 6 spills too much there, order 2 was not measured.
-template <int MODE, int H>
+template <int MODE>
 struct AdjBounds {
-  static constexpr int min_blocks = MODE == 1 ? AT_ADJ_MIN_BLOCKS : (MODE == 2 && H == 2 ? AT_ADJ_EDGE_MIN_BLOCKS : 2);
+  static constexpr int min_blocks = MODE == 1 ? AT_ADJ_MIN_BLOCKS : 2;
 };
 template <int DIM, int H, int MODE, bool AL, bool AB, bool BG = false, bool SP = false>
-__global__ void __launch_bounds__(256, AdjBounds<MODE, H>::min_blocks) adjoint_step_kernel(const AdjParams a,
+__global__ void __launch_bounds__(256, AdjBounds<MODE>::min_blocks) adjoint_step_kernel(const AdjParams a,
                                                                                       const int64_t n) {
   constexpr bool G = MODE != 0;
   const StepParams &f = a.f;
   const int64_t N = f.ntot;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nthreads = (int64_t)gridDim.x * blockDim.x;
-  if (n >= 1 && MODE != 1) draw_sides(f, n - 1, tid, nthreads, a.akeff + ((n - 1) & 1) * f.nb);
+  if (n >= 1) draw_sides(f, n - 1, tid, nthreads, a.akeff + ((n - 1) & 1) * f.nb);
   const uint8_t *keff = a.akeff + (n & 1) * f.nb;
   double galpha = 0.0;
   if (!G) {
@@ -521,14 +515,22 @@ __global__ void __launch_bounds__(256, AdjBounds<MODE, H>::min_blocks) adjoint_s
     const double *un = f.ring + (n % f.R) * N;
     const int nx = f.n[0], ny = f.n[1];
     const int gx = nx >> 2;
-    // the host partitions the groups into interior and edge lists, so a warp's lanes take the same path
-    for (int64_t e = tid; e < a.list_len; e += nthreads) {
-      const int64_t g = DIM == 1 ? group_1d_order(f, a.list_off + e) : (int64_t)f.order[a.list_off + e];
+    // interior and edge groups in chunks of 32 (one warp, one path): chunk c of C = Ci + Ce is an edge chunk when
+    // floor((c+1) Ce / C) > floor(c Ce / C), so edge warps, which wait on memory, spread evenly among interior
+    // warps, which keep the FP64 pipe busy
+    const int64_t n_edge = a.list_len - a.n_interior;
+    const int64_t Ci = (a.n_interior + 31) >> 5, Ce = (n_edge + 31) >> 5, C = Ci + Ce;
+    for (int64_t e = tid; e < (C << 5); e += nthreads) {
+      const int64_t c = e >> 5, lane = e & 31, ce0 = c * Ce / C;
+      const bool edge = (c + 1) * Ce / C > ce0;
+      const int64_t k = edge ? a.n_interior + (ce0 << 5) + lane : ((c - ce0) << 5) + lane;
+      if (k >= (edge ? a.list_len : a.n_interior)) continue;
+      const int64_t g = DIM == 1 ? group_1d_order(f, k) : (int64_t)f.order[k];
       const int64_t r = g / gx;
       const int x0 = (int)(g - r * gx) << 2;
       const int z = DIM == 3 ? (int)(r / ny) : 0, y = DIM == 3 ? (int)(r - (int64_t)z * ny) : 0;
       const int64_t i0 = r * nx + x0;
-      if (MODE == 2) {
+      if (edge) {
         adjoint_group<DIM, H, AB>(a, keff, n, x0, y, z, galpha);
         continue;
       }
@@ -651,13 +653,7 @@ void launch_modes(const AdjParams &a, int64_t n, int nblk, bool grouped, cudaStr
     }
   }
   if (grouped) {
-    AdjParams e = a, i = a;
-    e.list_off = a.n_interior;
-    e.list_len = a.list_len - a.n_interior;
-    i.list_off = 0;
-    i.list_len = a.n_interior;
-    adjoint_step_kernel<DIM, H, 2, AL, AB><<<nblk, kAdjThreads, 0, st>>>(e, n);
-    adjoint_step_kernel<DIM, H, 1, AL, AB><<<nblk, kAdjThreads, 0, st>>>(i, n);
+    adjoint_step_kernel<DIM, H, 1, AL, AB><<<nblk, kAdjThreads, 0, st>>>(a, n);
   } else {
     adjoint_step_kernel<DIM, H, 0, AL, AB><<<nblk, kAdjThreads, 0, st>>>(a, n);
   }
@@ -679,7 +675,7 @@ bool adjoint_grouped(const AdjParams &a) {
          (reinterpret_cast<uintptr_t>(a.lam) % 16) == 0 && (reinterpret_cast<uintptr_t>(a.f.ring) % 16) == 0;
 }
 
-// The interior launch's straight path needs a group whose cells and stencil neighbours (the x window of W = h
+// The straight (interior) path of the grouped kernel needs a group whose cells and stencil neighbours (the x window of W = h
 // rounded up to even cells on each side) lie in its PE and away from the domain ends.  The step kernel's order
 // lists exactly those groups first (3D: built at at_init; 1D: group_1d_order, every group of a PE but its first
 // and last): with x0 a multiple of 4 and h <= 3, x0 >= h implies x0 >= W and x0 + 3 + h < n implies
@@ -882,8 +878,7 @@ extern "C" int at_adjoint_backward(at_handle_t *hd, const double *lambda_dev, do
   a.alpha = want_alpha ? 1 : 0;
   // the linear transposed step needs the forward levels only for the alpha term; Burgers' always does
   const bool need_fwd = (want_alpha || hd->sp.burgers) && !hd->adj_resident;  // resident: levels are in place
-  // grouped shapes: the interior launch takes the head of the step kernel's group order, the edge launch the rest
-  a.list_off = 0;
+  // grouped shapes: the step kernel's group order, interior groups at its head
   a.list_len = 0;
   a.n_interior = 0;
   if (adjoint_grouped(a)) {
