@@ -327,7 +327,10 @@ def run_adjoint(args, rank: int, world: int, local: int):
     target = torch.zeros(ntot, dtype=torch.float64, device=f"cuda:{local}")
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     fwd, adj, adj_u0, bwd = [], [], [], []
+    sampler = ClockSampler(local)
     for it in range(args.warmup + args.steps):
+        if it == args.warmup:
+            sampler.start()
         s.reset()
         a, b = ev(), ev()
         a.record(stream)
@@ -353,6 +356,7 @@ def run_adjoint(args, rank: int, world: int, local: int):
             adj.append(c.elapsed_time(d))
             bwd.append(m.elapsed_time(d))
             adj_u0.append(e.elapsed_time(f))
+    clocks = sampler.stop()
     s.close()
     f_ms, a_ms = statistics.median(fwd), statistics.median(adj)
     if rank == 0:
@@ -371,7 +375,7 @@ def run_adjoint(args, rank: int, world: int, local: int):
                         "steps) for dJ/du0 and dJ/dalpha; backward_ms = the sweep alone, T backward steps against "
                         "forward_ms's T forward steps; the u0-only sweep needs no recompute; with every level "
                         "resident (--adjoint-every >= T) the forward pass keeps all levels and nothing is recomputed",
-                "grad_alpha": ga}
+                "grad_alpha": ga, "clocks": clocks}
         print(json.dumps(line), flush=True)
 
 
