@@ -795,6 +795,9 @@ extern "C" int at_adjoint_forward(at_handle_t *hd, int64_t nsteps, int64_t ckpt_
   const AdjLayout L = layout(hd, nsteps, ckpt_every);
   if (work_len < L.total) return fail(AT_ERR_ARG, "at_adjoint_forward: workspace too small");
   if (reinterpret_cast<uintptr_t>(work_dev) % 16) return fail(AT_ERR_ARG, "at_adjoint_forward: workspace not 16-byte aligned");
+  // at_step's limits, checked before any step so a refused pass leaves the handle at step 0
+  if (hd->sp.log && nsteps > hd->log_steps) return fail(AT_ERR_STATE, "at_adjoint_forward: delay log is full");
+  if (nsteps > 0xFFFFFFFFll) return fail(AT_ERR_STATE, "at_adjoint_forward: step counter exceeds 32 bits");
   const int64_t N = hd->sp.ntot, R = hd->sp.R;
   hd->adj_nsteps = -1;
   hd->adj_resident = false;

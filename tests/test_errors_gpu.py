@@ -44,6 +44,22 @@ def test_adjoint_calls_out_of_order_are_refused():
     s.close()
 
 
+def test_adjoint_forward_past_the_delay_log_is_refused():
+    """Both forward-pass forms (checkpoints, and one segment holding every level) keep at_step's log limit."""
+    from paper_1702_00496_gb300 import Solver
+    from paper_1702_00496_gb300.binding import ATError, AT_ERR_STATE
+    spec, _ = W.wl_1d(256, 8, 4, 3, 0, 95, (1, 2))
+    for every in (0, 12):
+        s = Solver(spec, log_steps=10)
+        with pytest.raises(ATError) as e:
+            s.adjoint_forward(12, every)
+        assert e.value.code == AT_ERR_STATE and s.n == 0
+        s.adjoint_forward(10, every)
+        assert s.n == 10
+        s.sync()
+        s.close()
+
+
 def test_diverging_run_reports_non_finite_statistics():
     from paper_1702_00496_gb300 import Solver
     from paper_1702_00496_gb300.binding import ATError, AT_ERR_NONFINITE
