@@ -249,6 +249,7 @@ extern "C" int at_init(const at_config_t *cfg, double *ring_dev, int64_t ring_le
   for (int a = 0; a < 3; ++a) {
     w.n[a] = (int32_t)cfg->n[a];
     w.dx[a] = kTwoPi / (double)cfg->n[a];
+    w.xpi[a] = 2.0 / (double)cfg->n[a];
     w.c[a] = cfg->c[a];
     if (a >= cfg->dim) continue;
     for (int q = 0; q < cfg->nmodes; ++q) {

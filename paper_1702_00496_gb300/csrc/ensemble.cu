@@ -36,7 +36,7 @@ struct MemberParams {
   double shift_pre[2];             // and its phase shift c t = -c m dt
   double phase[AT_MAX_MODES];
   double kappa[AT_MAX_MODES];
-  double dx, shift_final;          // grid spacing, c * t_final
+  double dx, xpi, shift_final;     // grid spacing, 2 / n (point i at x = pi i xpi), c * t_final
   int64_t steps;                   // steps this member runs
   int32_t nmodes, group;           // group: index of the member's summary group
   int32_t twin;                    // member whose final field this one is compared with, or -1
@@ -48,8 +48,8 @@ struct MemberParams {
 constexpr int kStatFields = AT_STAT_FIELDS;
 
 __device__ double wave_1d(const MemberParams &m, const ModeSet &ms, const double *amp, double shift, int i) {
+  if (ms.rot) return atfd::mode_sum(ms, m.nmodes, (double)i * m.xpi);
   const double x = (double)i * m.dx;
-  if (ms.rot) return atfd::mode_sum(ms, m.nmodes, x);
   double s = 0.0;
   for (int q = 0; q < m.nmodes; ++q) s += amp[q] * sin(m.kappa[q] * (x - shift) + m.phase[q]);
   return s;
@@ -375,6 +375,7 @@ extern "C" int at_ensemble_create(const at_config_t *members, const at_member_t 
     if (rc) { delete e; return rc; }
     m.nmodes = c.nmodes;
     m.dx = kTwoPi / (double)c.n[0];
+    m.xpi = 2.0 / (double)c.n[0];
     const double tf = (double)nsteps * c.dt;
     m.shift_final = c.c[0] * tf;
     for (int q = 0; q < c.nmodes; ++q) {

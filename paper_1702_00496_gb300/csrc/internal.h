@@ -93,6 +93,7 @@ struct WaveParams {
   double phase[3][AT_MAX_MODES];
   double kappa[3][AT_MAX_MODES];
   ModeSet ms[3];  // per axis, filled by the launchers for the time of the launch (fill_modes)
+  double xpi[3];  // 2 / n: grid point i sits at x = pi (i xpi)
 };
 
 // Validate cfg and fill the step parameters (merged taps, extrapolation weights, delay process) for a problem

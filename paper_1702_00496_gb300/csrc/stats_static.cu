@@ -84,6 +84,7 @@ extern "C" int at_error_stats_noalloc(const at_config_t *cfg, const double *u_de
     p.use_pe[a] = (a < cfg->dim && cfg->pe[a] > 1) ? 1 : 0;
     w.n[a] = (int32_t)cfg->n[a];
     w.dx[a] = kTwoPi / (double)cfg->n[a];
+    w.xpi[a] = 2.0 / (double)cfg->n[a];
     w.c[a] = cfg->c[a];
     if (a >= cfg->dim) continue;
     for (int q = 0; q < cfg->nmodes; ++q) {

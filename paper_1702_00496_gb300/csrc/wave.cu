@@ -16,10 +16,10 @@
 namespace {
 
 // Sum over the modes of axis a at grid point i, for the time t of the launch (w.amp holds A exp(-alpha kappa^2 t),
-// scaled on the host): the rotation recurrence for integer wavenumbers, else a sine per mode.
+// scaled on the host): the three-term recurrences for integer wavenumbers, else a sine per mode.
 __device__ __forceinline__ double axis_sum(const WaveParams &w, int a, int i, double t) {
+  if (w.ms[a].rot) return atfd::mode_sum(w.ms[a], w.nmodes, (double)i * w.xpi[a]);
   const double x = (double)i * w.dx[a];
-  if (w.ms[a].rot) return atfd::mode_sum(w.ms[a], w.nmodes, x);
   const double shift = w.c[a] * t;
   double s = 0.0;
   for (int q = 0; q < w.nmodes; ++q) s += w.amp[a][q] * sin(w.kappa[a][q] * (x - shift) + w.phase[a][q]);
