@@ -40,7 +40,7 @@ struct MemberParams {
   int64_t steps;                   // steps this member runs
   int32_t nmodes, group;           // group: index of the member's summary group
   int32_t twin;                    // member whose final field this one is compared with, or -1
-  // the same modes prepared for the rotation recurrence (when ms_ic.rot), exactly as the single-problem path
+  // the same modes prepared for the recurrences over k (when ms_ic.rot), exactly as the single-problem path
   // prepares them, so a member's fields and statistics carry the same bits: t = 0, t_final, t = -dt, -2 dt
   ModeSet ms_ic, ms_fin, ms_pre[2];
 };

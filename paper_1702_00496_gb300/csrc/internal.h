@@ -71,7 +71,7 @@ struct StepParams {
   double eq[3][2][AT_MAX_ETAPS];
 };
 
-// The modes of one axis at one time t, prepared on the host for the rotation recurrence: sorted by wavenumber,
+// The modes of one axis at one time t, prepared on the host for the recurrences over k: sorted by wavenumber,
 // with A exp(-alpha kappa^2 t) and the phase phi - kappa c t folded into ac = A cos(.), as = A sin(.).  rot = 1 when
 // every wavenumber is an integer in 1..AT_MAX_KROT (else the sines are evaluated one by one).
 struct ModeSet {
