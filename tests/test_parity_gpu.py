@@ -84,6 +84,18 @@ def test_single_delay_level_equals_synchronous_run():
     assert np.array_equal(u_at, u_sync)
 
 
+@pytest.mark.parametrize("modes", [range(1, 17), range(9, 25)], ids=["k_to_16", "k_9_to_24"])
+def test_initial_condition_at_high_wavenumbers(modes):
+    """The mode sums over k by the three-term recurrences (largest k at most 16) and by the rotation (above), against
+    the oracle's libm sines: an error made at wavenumber j reaches k at most (k - j)-fold, under 16^2/2 ulp of the
+    amplitude sum for the first, a few ulp per rotation for the second."""
+    spec, _ = W.wl_1d(1000, 10, 4, 3, 0, 9, modes)
+    u, _, _ = _gpu_run(spec, 0, log=False)
+    ref = oracle.initial(oracle.Config(spec))
+    bound = 128 * np.finfo(float).eps * np.abs(spec["amp"]).sum()
+    assert np.abs(u - ref).max() <= bound
+
+
 def test_zero_steps_is_the_initial_condition():
     spec, _ = W.wl_1d(1000, 10, 4, 3, 0, 8, range(1, 5))
     u, _, st = _gpu_run(spec, 0, log=False)
