@@ -390,6 +390,44 @@ def test_error_stats_definitions():
     assert (st["n_I"], st["n_B"]) == (48, 16)
 
 
+@pytest.mark.parametrize("dim", [1, 3])
+def test_error_stats_closed_forms(dim):
+    """Sec. 4's averages on fields whose answers are closed forms: the analytic solution plus a constant delta
+    (every average |delta|, the mean delta), plus delta on I_B only (rms_I = 0, rms = |delta| sqrt(|I_B|/|I|)),
+    and the sizes of I_I and I_B from the PE geometry: prod over split axes of P (S - 2h) interior points."""
+    if dim == 1:
+        spec, _ = W.wl_1d(96, 6, 4, 3, 0, 33, (1, 2))
+    else:
+        spec, _ = W.wl_3d([24, 16, 16], [2, 2, 2], 4, 3, 0, 34)
+    cfg = oracle.Config(spec)
+    h = spec["order"] // 2
+    n_int = 1
+    for n, P in zip(spec["n"], spec["pe"]):
+        n_int *= P * (n // P - 2 * h) if P > 1 else n
+    N = int(np.prod(spec["n"]))
+    t = 5 * spec["dt"]
+    ua = oracle.analytic(cfg, t)
+    delta = -3.0e-3
+    st = oracle.error_stats(cfg, ua + delta, 5)
+    assert (st["n_I"], st["n_B"]) == (n_int, N - n_int)
+    for key in ("rms", "max_abs", "mean_abs", "rms_I", "rms_B"):
+        assert st[key] == pytest.approx(abs(delta), rel=1e-12), key
+    assert st["mean"] == pytest.approx(delta, rel=1e-12)
+    assert st["ua_rms"] == pytest.approx(np.sqrt(np.mean(ua ** 2)), rel=1e-14)
+    # delta on the boundary points only: find them as the points a forced delay can reach (within h of a face)
+    edge = np.zeros(cfg.shape, dtype=bool)
+    for a, (n, P) in enumerate(zip(spec["n"], spec["pe"])):
+        if P < 2:
+            continue
+        pos = np.arange(n) % (n // P)
+        e1 = (pos < h) | (pos >= n // P - h)
+        edge |= e1.reshape([-1 if b == a else 1 for b in range(dim)][::-1])
+    st = oracle.error_stats(cfg, ua + delta * edge, 5)
+    assert st["rms_I"] <= 1e-15 and st["max_abs"] == pytest.approx(abs(delta), rel=1e-12)
+    assert st["rms_B"] == pytest.approx(abs(delta), rel=1e-12)
+    assert st["rms"] == pytest.approx(abs(delta) * np.sqrt((N - n_int) / N), rel=1e-12)
+
+
 # ----------------------------------------------------------------------------- adjoint
 def _J(cfg, nsteps, tgt, u0):
     u, _, _ = oracle.run(cfg, nsteps, want_log=False, u0=u0)
