@@ -149,6 +149,25 @@ def test_example1_closed_form_and_degenerate_cases():
             assert rc == B.AT_ERR_SINGULAR and rank == 3
 
 
+def test_artificial_delay_on_both_sides():
+    """Sec. 3.2 with the single system: imposing the buffer point's delay k on the opposite point as well (an
+    artificial delay at an interior point) leaves the central difference itself second-order accurate for
+    dt ~ dx^2 (Eq. "deriv22": the (0,1) row and every even power of dx drop out), while the delay on one side alone
+    is inconsistent; and no such both-sides central stencil reaches fourth order, since the u^(1,1) dx dt row then
+    asks the same sum to be 1 and 0."""
+    for k in (1, 2, 3):
+        rc, frac, _, rank = P.at_solve_stencil(1, 2, 2, [-1, 1], [k, k])
+        assert rc == B.AT_OK and rank == 2
+        assert [Fraction(n, d) for n, d in frac] == [Fraction(-1, 2), Fraction(1, 2)]
+        rc, _, _, rank = P.at_solve_stencil(1, 2, 2, [-1, 1], [0, k])
+        assert rc == B.AT_ERR_INCONSISTENT and rank == 2
+        rc, _, _, _ = P.at_solve_stencil(1, 4, 2, [-2, -1, 1, 2], [k, k, k, k])
+        assert rc == B.AT_ERR_INCONSISTENT
+    rc, frac, _, _ = P.at_solve_stencil(1, 4, 2, [-2, -1, 1, 2], [0, 0, 0, 0])
+    assert rc == B.AT_OK
+    assert [Fraction(n, d) for n, d in frac] == [Fraction(1, 12), Fraction(-2, 3), Fraction(2, 3), Fraction(-1, 12)]
+
+
 def test_coeffs_argument_errors():
     for args in [(3, 2, 3), (1, 3, 3), (1, 8, 3), (1, 2, 0), (1, 2, 9)]:
         with pytest.raises(B.ATError) as e:
