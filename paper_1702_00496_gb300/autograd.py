@@ -10,7 +10,8 @@ class ATForward(torch.autograd.Function):
     """U^nsteps = AT forward run of `nsteps` steps of the problem `spec` from u0, with diffusivity alpha.
 
     backward() returns dJ/du0 and dJ/dalpha through the same delays (replayed from the counter-based generator),
-    using checkpoints every ckpt_every steps (0: ceil(sqrt(nsteps))).
+    using checkpoints every ckpt_every steps (0: ceil(sqrt(nsteps)); ckpt_every >= nsteps keeps every level in the
+    workspace, about nsteps fields, and recomputes nothing).
     """
 
     @staticmethod

@@ -65,7 +65,8 @@ class Solver:
         return B.at_error_stats_ref(self.h, ref, refine)
 
     def adjoint_forward(self, nsteps: int, ckpt_every: int = 0) -> None:
-        """Run nsteps from step 0 keeping checkpoints every ckpt_every steps (0: ceil(sqrt(nsteps)))."""
+        """Run nsteps from step 0 keeping checkpoints every ckpt_every steps (0: ceil(sqrt(nsteps)); ckpt_every >=
+        nsteps: every level stays in the workspace and the backward sweep recomputes nothing)."""
         n = B.at_adjoint_workspace(self.h, nsteps, ckpt_every)
         if getattr(self, "work", None) is None or self.work.numel() < n:
             self.work = None
