@@ -227,12 +227,14 @@ int at_destroy(at_handle_t *hd);
  *   keep the checkpoints in work_dev (caller-owned, 16-byte aligned, untouched until at_adjoint_backward).  When
  *   one segment covers the run (ckpt_every >= nsteps; workspace about nsteps + R fields), the steps run inside the
  *   workspace, which then holds every level, and the backward sweep recomputes nothing.  Any later at_step or
- *   at_reset discards the recorded pass.  Errors: AT_ERR_ARG, AT_ERR_STATE (not at step 0), AT_ERR_CUDA.
+ *   at_reset discards the recorded pass.  Errors: AT_ERR_ARG, AT_ERR_STATE (not at step 0, or nsteps beyond the
+ *   delay log or the 32-bit step counter, checked before any step), AT_ERR_CUDA.
  * at_adjoint_backward: given lambda_dev = dJ/dU^nsteps (device, ntot doubles), write dJ/dU^0 to grad_u0_dev
  *   (device, ntot doubles) and dJ/dalpha to *grad_alpha_host.  Replays one checkpoint segment at a time:
- *   restores it, recomputes its levels with the forward kernel, runs its adjoint steps in reverse.  With
- *   grad_alpha_host NULL only dJ/dU^0 is formed; the transposed steps need no forward level then, so the sweep
- *   skips the restore and the recompute.  Blocks.
+ *   restores it, recomputes its levels with the forward kernel, runs its adjoint steps in reverse (one launch
+ *   per step); with every level in the workspace it only runs the adjoint steps.  With grad_alpha_host NULL
+ *   only dJ/dU^0 is formed; the linear transposed steps need no forward level then, so the sweep skips the
+ *   restore and the recompute.  dJ/dalpha is summed per block in a fixed assignment: deterministic.  Blocks.
  *   Requires at_adjoint_forward to have been the last stepping call.  Errors: AT_ERR_ARG, AT_ERR_STATE,
  *   AT_ERR_CUDA, AT_ERR_NONFINITE. */
 int at_adjoint_workspace(at_handle_t *hd, int64_t nsteps, int64_t ckpt_every, int64_t *work_len);
