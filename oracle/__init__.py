@@ -10,7 +10,12 @@ Every function follows the paper passage named in ``oracle.c``.  Parity status o
   - stencil taps: pinned (Taylor moment conditions of Eq. "cond", k=0 reduction, truncation terms).
   - synchronous run: pinned (exact discrete Fourier solution; convergence to Eq. "ana_sol").
   - asynchronous run: pinned statistically (order gates of Sec. 5.2) and by truncation terms.
-  - adjoint: pinned (central finite differences, exact for the quadratic misfit).
+  - adjoint: pinned (central finite differences, exact for the quadratic misfit; Richardson differences in alpha;
+    Adams-Bashforth and Burgers' equation too).
+  - error statistics: pinned (closed forms: constant offsets, boundary-only offsets, |I_I| from the PE geometry).
+  - Adams-Bashforth runs: pinned (exact Fourier recurrence of the synchronous run; slopes -4 / -6 of Cases 4, 5).
+  - rows expanded in space: pinned (exact Eq. "cond" rows, printed leading terms, slope -2 of Cases 2, 3).
+  - Burgers' equation: pinned (Cole-Hopf solutions; slope -4 of Case 6 against a finer run).
 """
 from __future__ import annotations
 
