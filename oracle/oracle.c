@@ -28,7 +28,7 @@
  *   - adjoint: the literal transpose of the forward step over the stored history (Burgers' equation: the
  *     D1 taps carry -U_i^n and U_i^n itself receives -D1 U, the derivative of the nonlinear term).
  *
- * Readings where the paper is silent (each one is listed in the design doc):
+ * Readings where the paper is silent:
  *   - a PE side uses one delay for all its buffer points (uniform delay, Sec. 5.1); the two sides
  *     of a shared face are different messages and draw independently;
  *   - levels before 0 do not exist: a drawn delay k>0 is clamped to min(k, max(0, n-(T-1)));
