@@ -92,6 +92,7 @@ def lib():
                                   C.POINTER(C.c_double)]
         L.orc_set_threads.argtypes = [C.c_int]
         L.orc_delay_log.argtypes = [C.POINTER(OrcCfg), C.c_int64, C.c_void_p]
+        L.orc_run_samples.argtypes = [C.POINTER(OrcCfg), C.c_int64, C.c_int64, C.c_void_p, C.c_void_p]
         _lib = L
     return _lib
 
@@ -209,6 +210,17 @@ def run(cfg: Config, nsteps: int, want_log: bool = True, want_history: bool = Fa
         raise RuntimeError(f"orc_run failed ({rc})")
     return (u.reshape(cfg.shape), log,
             None if hist is None else hist.reshape((nsteps + 1,) + cfg.shape))
+
+
+def run_samples(cfg: Config, nsteps: int, positions) -> np.ndarray:
+    """U^{nsteps} of a 1D forward-Euler run from Eq. "IC" at the given cells, each stepped only inside its domain of
+    dependence (the same values as run(), bit for bit, at full sizes where a whole run would take too long)."""
+    pos = np.ascontiguousarray(positions, dtype=np.int64)
+    out = np.empty(pos.size, dtype=np.float64)
+    rc = lib().orc_run_samples(C.byref(cfg.s), int(nsteps), int(pos.size), pos.ctypes.data, out.ctypes.data)
+    if rc != 0:
+        raise RuntimeError(f"orc_run_samples failed ({rc})")
+    return out
 
 
 def delay_log(cfg: Config, nsteps: int) -> np.ndarray:

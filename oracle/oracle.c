@@ -417,28 +417,32 @@ static double eval_taps(const orc_cfg *g, const double *const *lev, int64_t x, i
   return s;
 }
 
-/* Right-hand side f^n = sum_axes ( -c_a D1_a U + alpha D2_a U ) at every point, with the AT stencils at PE
- * edges; lev[m] = U^{n-m} (m = 0.. as deep as the delays need), keff = effective delay of every PE side. */
+/* Right-hand side f^n = sum_axes ( -c_a D1_a U + alpha D2_a U ) at point pt, with the AT stencils at PE edges;
+ * lev[m] = U^{n-m} (m = 0.. as deep as the delays need), keff = effective delay of every PE side. */
+static double rhs_point(const orc_cfg *g, const double *const *lev, const int32_t *keff, int64_t pt) {
+  const int64_t nx = g->n[0], ny = g->n[1];
+  const int64_t x = pt % nx, y = (pt / nx) % ny, z = pt / (nx * ny);
+  orc_tap taps[32];
+  double f = 0.0;
+  for (int a = 0; a < g->dim; ++a) {
+    int nt1 = point_taps(g, keff, x, y, z, a, 1, taps);
+    double d1 = eval_taps(g, lev, x, y, z, a, taps, nt1);
+    int nt2 = point_taps(g, keff, x, y, z, a, 2, taps);
+    double d2 = eval_taps(g, lev, x, y, z, a, taps, nt2);
+    const double beta1 = g->burgers ? lev[0][pt] : g->c[a];  /* Burgers: the advecting speed is u itself */
+    f = f + (-beta1 * d1 + g->alpha * d2);
+  }
+  return f;
+}
+
+/* The right-hand side at every point. */
 int orc_rhs(const orc_cfg *g, const double *const *lev, const int32_t *keff, double *f_out) {
   if (orc_check(g)) return -1;
-  const int64_t nx = g->n[0], ny = g->n[1], N = ntot(g);
+  const int64_t N = ntot(g);
 #ifdef _OPENMP
 #pragma omp parallel for schedule(static) num_threads(g_threads)
 #endif
-  for (int64_t pt = 0; pt < N; ++pt) {
-    const int64_t x = pt % nx, y = (pt / nx) % ny, z = pt / (nx * ny);
-    orc_tap taps[32];
-    double f = 0.0;
-    for (int a = 0; a < g->dim; ++a) {
-      int nt1 = point_taps(g, keff, x, y, z, a, 1, taps);
-      double d1 = eval_taps(g, lev, x, y, z, a, taps, nt1);
-      int nt2 = point_taps(g, keff, x, y, z, a, 2, taps);
-      double d2 = eval_taps(g, lev, x, y, z, a, taps, nt2);
-      const double beta1 = g->burgers ? lev[0][pt] : g->c[a];  /* Burgers: the advecting speed is u itself */
-      f = f + (-beta1 * d1 + g->alpha * d2);
-    }
-    f_out[pt] = f;
-  }
+  for (int64_t pt = 0; pt < N; ++pt) f_out[pt] = rhs_point(g, lev, keff, pt);
   return 0;
 }
 
@@ -540,6 +544,44 @@ int orc_run(const orc_cfg *g, const double *u0, int64_t nsteps, double *u_out, u
   }
   memcpy(u_out, ring + (nsteps % R) * N, sizeof(double) * (size_t)N);
   free(ring); free(fring); free(keff); free(lev);
+  return 0;
+}
+
+/* U^{nsteps} at the cells pos[0..npos-1] of a 1D forward-Euler run from Eq. "IC", computed only inside their domain
+ * of dependence.  Every stencil of the method (central, AT rows, rows expanded in space) reads cells at most
+ * reach = max(h, 3) away at the current or delayed levels (Sec. 2, Tables "atschemes-left/right"), so U^{n+1}_i
+ * needs only cells within reach of i, and the cells within reach (nsteps - n - 1) of a sampled cell are the only
+ * ones stepped at step n.  Each stepped value is computed by the same operations as in orc_run, so the samples equal
+ * orc_run's field bit for bit, at a cost that grows with nsteps^2 instead of N nsteps.  Returns -1 for 3D or
+ * multistep runs. */
+int orc_run_samples(const orc_cfg *g, int64_t nsteps, int64_t npos, const int64_t *pos, double *u_out) {
+  if (orc_check(g) || nsteps < 0 || npos < 0 || g->dim != 1 || g->tsteps > 1) return -1;
+  const int T = orc_time_width(g->order, g->scheme);
+  const int R = g->L + T;
+  const int64_t N = g->n[0], nb = orc_num_sides(g);
+  const int64_t reach = g->order / 2 > 3 ? g->order / 2 : 3;
+  for (int64_t q = 0; q < npos; ++q)
+    if (pos[q] < 0 || pos[q] >= N) return -1;
+  double *ring = (double *)malloc(sizeof(double) * (size_t)(R * N));
+  int32_t *keff = (int32_t *)malloc(sizeof(int32_t) * (size_t)nb);
+  const double **lev = (const double **)malloc(sizeof(double *) * (size_t)R);
+  if (!ring || !keff || !lev) { free(ring); free(keff); free(lev); return -2; }
+  orc_initial(g, ring);
+  for (int64_t n = 0; n < nsteps; ++n) {
+    draw_delays(g, n, T, NULL, keff);
+    for (int m = 0; m < R - 1; ++m) lev[m] = (n - m >= 0) ? ring + ((n - m) % R) * N : NULL;
+    double *next = ring + ((n + 1) % R) * N;
+    const int64_t w = reach * (nsteps - n - 1);
+    for (int64_t q = 0; q < npos; ++q) {
+      const int64_t width = 2 * w + 1 < N ? 2 * w + 1 : N;
+      for (int64_t c = 0; c < width; ++c) {
+        const int64_t i = wrap_add(pos[q], c - (width < N ? w : pos[q]), N);
+        next[i] = lev[0][i] + g->dt * rhs_point(g, lev, keff, i);
+      }
+    }
+  }
+  for (int64_t q = 0; q < npos; ++q) u_out[q] = ring[(nsteps % R) * N + pos[q]];
+  free(ring); free(keff); free(lev);
   return 0;
 }
 

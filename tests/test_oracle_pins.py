@@ -428,6 +428,28 @@ def test_error_stats_closed_forms(dim):
     assert st["rms"] == pytest.approx(abs(delta) * np.sqrt((N - n_int) / N), rel=1e-12)
 
 
+@pytest.mark.parametrize("case", ["at_o4", "at_o6", "std_o4", "space2_o2", "space1_o2", "burgers_o4"])
+def test_sampled_run_equals_the_full_run(case):
+    """run_samples steps each sampled cell only inside its domain of dependence (reach max(h, 3) per step); it must
+    give the full run's values bit for bit, including cells on PE edges and next to the periodic wrap."""
+    if case == "burgers_o4":
+        spec = W.paper_case(6, 256, 13, (0.4, 0.3, 0.3))
+        spec["tsteps"] = 1
+    else:
+        order = int(case[-1])
+        scheme = {"at": W.AT, "std": W.ASYNC_STD, "space2": W.AT_SPACE2, "space1": W.AT_SPACE1}[case.split("_")[0]]
+        c = 0.0 if scheme == W.AT_SPACE1 else 1.0
+        spec, _ = W.wl_1d(768, 12, order, 4, 0, 14, range(1, 6), scheme=scheme, c=c,
+                          r_alpha=0.02 if order == 6 else 0.1)
+    cfg = oracle.Config(spec)
+    n = spec["n"][0]
+    S = n // spec["pe"][0]
+    steps = 120
+    full, _, _ = oracle.run(cfg, steps, want_log=False)
+    pos = [0, 1, S - 1, S, 2 * S + 3, n // 2, n - 2, n - 1]
+    assert np.array_equal(oracle.run_samples(cfg, steps, pos), full.reshape(-1)[pos])
+
+
 # ----------------------------------------------------------------------------- adjoint
 def _J(cfg, nsteps, tgt, u0):
     u, _, _ = oracle.run(cfg, nsteps, want_log=False, u0=u0)

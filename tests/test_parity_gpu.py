@@ -156,6 +156,27 @@ def test_full_size_1d_n16m_delays_and_field():
     assert np.abs(u[idx] - want).max() <= TOL * np.abs(want).max()
 
 
+def test_full_size_1d_n16m_sampled_after_the_whole_run():
+    """N = 2^24, 4096 PEs, order 4, L = 4, all 1000 asynchronous steps in the launch shape bench.py picks: cells on
+    PE edges and inside PEs against the oracle, which steps each sampled cell inside its domain of dependence
+    only (the same values as a whole oracle run, bit for bit)."""
+    from paper_1702_00496_gb300 import Solver, autotune
+    spec, steps = W.workload("1d_n16m")
+    s = Solver(spec)
+    autotune.tune_forward(s, spec)
+    s.reset()
+    s.step(steps)
+    s.sync()
+    u = s.field().cpu().numpy().copy()
+    s.close()
+    S = spec["n"][0] // spec["pe"][0]
+    rng = np.random.default_rng(1)
+    pes = rng.choice(spec["pe"][0], 6, replace=False)
+    pos = sorted({int(p * S + o) for p in pes for o in (0, 1, S // 2, S - 2, S - 1)})
+    ref = oracle.run_samples(oracle.Config(spec), steps, pos)
+    assert np.abs(u[pos] - ref).max() <= TOL * np.abs(u).max()
+
+
 @pytest.mark.parametrize("order", [2, 4])
 def test_full_size_3d_512_prefix(order):
     """512^3 in 8^3 PEs: delay log of the 500-step run bit-exact; field after a 6-step prefix vs oracle."""
