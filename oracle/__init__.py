@@ -213,8 +213,9 @@ def run(cfg: Config, nsteps: int, want_log: bool = True, want_history: bool = Fa
 
 
 def run_samples(cfg: Config, nsteps: int, positions) -> np.ndarray:
-    """U^{nsteps} of a 1D forward-Euler run from Eq. "IC" at the given cells, each stepped only inside its domain of
-    dependence (the same values as run(), bit for bit, at full sizes where a whole run would take too long)."""
+    """U^{nsteps} of a 1D run from Eq. "IC" (forward Euler or Adams-Bashforth) at the given cells, each stepped only
+    inside its domain of dependence (the same values as run(), bit for bit, at full sizes where a whole run would
+    take too long)."""
     pos = np.ascontiguousarray(positions, dtype=np.int64)
     out = np.empty(pos.size, dtype=np.float64)
     rc = lib().orc_run_samples(C.byref(cfg.s), int(nsteps), int(pos.size), pos.ctypes.data, out.ctypes.data)

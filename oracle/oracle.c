@@ -547,41 +547,66 @@ int orc_run(const orc_cfg *g, const double *u0, int64_t nsteps, double *u_out, u
   return 0;
 }
 
-/* U^{nsteps} at the cells pos[0..npos-1] of a 1D forward-Euler run from Eq. "IC", computed only inside their domain
- * of dependence.  Every stencil of the method (central, AT rows, rows expanded in space) reads cells at most
- * reach = max(h, 3) away at the current or delayed levels (Sec. 2, Tables "atschemes-left/right"), so U^{n+1}_i
- * needs only cells within reach of i, and the cells within reach (nsteps - n - 1) of a sampled cell are the only
- * ones stepped at step n.  Each stepped value is computed by the same operations as in orc_run, so the samples equal
- * orc_run's field bit for bit, at a cost that grows with nsteps^2 instead of N nsteps.  Returns -1 for 3D or
- * multistep runs. */
+/* U^{nsteps} at the cells pos[0..npos-1] of a 1D run from Eq. "IC" (forward Euler or Adams-Bashforth), computed only
+ * inside their domain of dependence.  Every stencil of the method (central, AT rows, rows expanded in space) reads
+ * cells at most reach = max(h, 3) away at the current or delayed levels (Sec. 2, Tables "atschemes-left/right"),
+ * and the Adams-Bashforth sum reads the cell's own earlier right-hand sides, so U^{n+1}_i needs only cells within
+ * reach of i, and the cells within reach (nsteps - n - 1) of a sampled cell are the only ones stepped at step n
+ * (the analytic pre-history of a multistep run is formed on the whole grid, as orc_run does).  Each stepped value is
+ * computed by the same operations as in orc_run, so the samples equal orc_run's field bit for bit, at a cost that
+ * grows with nsteps^2 instead of N nsteps.  Returns -1 for 3D runs. */
 int orc_run_samples(const orc_cfg *g, int64_t nsteps, int64_t npos, const int64_t *pos, double *u_out) {
-  if (orc_check(g) || nsteps < 0 || npos < 0 || g->dim != 1 || g->tsteps > 1) return -1;
+  if (orc_check(g) || nsteps < 0 || npos < 0 || g->dim != 1) return -1;
   const int T = orc_time_width(g->order, g->scheme);
   const int R = g->L + T;
+  const int ts = g->tsteps < 1 ? 1 : g->tsteps;
   const int64_t N = g->n[0], nb = orc_num_sides(g);
   const int64_t reach = g->order / 2 > 3 ? g->order / 2 : 3;
   for (int64_t q = 0; q < npos; ++q)
     if (pos[q] < 0 || pos[q] >= N) return -1;
   double *ring = (double *)malloc(sizeof(double) * (size_t)(R * N));
+  double *fring = (double *)malloc(sizeof(double) * (size_t)(ts * N));
   int32_t *keff = (int32_t *)malloc(sizeof(int32_t) * (size_t)nb);
   const double **lev = (const double **)malloc(sizeof(double *) * (size_t)R);
-  if (!ring || !keff || !lev) { free(ring); free(keff); free(lev); return -2; }
+  if (!ring || !fring || !keff || !lev) { free(ring); free(fring); free(keff); free(lev); return -2; }
   orc_initial(g, ring);
+  int prehistory = 0;
+  if (ts > 1 && !g->burgers) {  /* the same start as orc_run from Eq. "IC" */
+    int32_t *zero = (int32_t *)calloc((size_t)nb, sizeof(int32_t));
+    double *ua = (double *)malloc(sizeof(double) * (size_t)N);
+    if (!zero || !ua) { free(zero); free(ua); free(ring); free(fring); free(keff); free(lev); return -2; }
+    for (int m = 1; m < ts; ++m) {
+      orc_analytic(g, -(double)m * g->dt, ua);
+      const double *l0[1] = {ua};
+      orc_rhs(g, l0, zero, fring + ((ts - m) % ts) * N);
+    }
+    free(zero); free(ua);
+    prehistory = 1;
+  }
   for (int64_t n = 0; n < nsteps; ++n) {
     draw_delays(g, n, T, NULL, keff);
     for (int m = 0; m < R - 1; ++m) lev[m] = (n - m >= 0) ? ring + ((n - m) % R) * N : NULL;
     double *next = ring + ((n + 1) % R) * N;
+    double beta[3];
+    const int nl = ts == 1 ? 1 : ab_weights(prehistory ? ts : (int)(n + 1 < ts ? n + 1 : ts), beta);
     const int64_t w = reach * (nsteps - n - 1);
     for (int64_t q = 0; q < npos; ++q) {
       const int64_t width = 2 * w + 1 < N ? 2 * w + 1 : N;
       for (int64_t c = 0; c < width; ++c) {
         const int64_t i = wrap_add(pos[q], c - (width < N ? w : pos[q]), N);
-        next[i] = lev[0][i] + g->dt * rhs_point(g, lev, keff, i);
+        if (ts == 1) {
+          next[i] = lev[0][i] + g->dt * rhs_point(g, lev, keff, i);
+        } else {
+          fring[(n % ts) * N + i] = rhs_point(g, lev, keff, i);
+          double sum = 0.0;
+          for (int m = 0; m < nl; ++m) sum = sum + beta[m] * fring[(((n - m) % ts + ts) % ts) * N + i];
+          next[i] = lev[0][i] + g->dt * sum;
+        }
       }
     }
   }
   for (int64_t q = 0; q < npos; ++q) u_out[q] = ring[(nsteps % R) * N + pos[q]];
-  free(ring); free(keff); free(lev);
+  free(ring); free(fring); free(keff); free(lev);
   return 0;
 }
 

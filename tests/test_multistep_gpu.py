@@ -144,6 +144,26 @@ def test_launch_shapes_do_not_change_multistep_results():
             assert torch.equal(u, ref), (threads, bps)
 
 
+@pytest.mark.parametrize("name", ["1d_n16m_case4", "1d_n16m_case5"])
+def test_full_size_cases_4_and_5_sampled_after_the_whole_run(name):
+    """N = 2^24, 4096 PEs, AB2 with CD4 / AB3 with CD6, all 1000 asynchronous steps in the launch shape bench.py
+    picks: PE-edge and interior cells against the oracle stepped inside their domain of dependence."""
+    from paper_1702_00496_gb300 import autotune
+    spec, steps = W.workload(name)
+    s = _solver(spec)
+    autotune.tune_forward(s, spec)
+    s.reset()
+    s.step(steps)
+    s.sync()
+    u = s.field().cpu().numpy().copy()
+    s.close()
+    S = spec["n"][0] // spec["pe"][0]
+    pes = np.random.default_rng(2).choice(spec["pe"][0], 4, replace=False)
+    pos = sorted({int(p * S + o) for p in pes for o in (0, 1, 2, S // 2, S - 3, S - 1)})
+    ref = oracle.run_samples(oracle.Config(spec), steps, pos)
+    assert np.abs(u[pos] - ref).max() <= TOL * np.abs(u).max()
+
+
 # ------------------------------------------------------------ the paper's Cases 4 and 5 on the GPU
 def _slope(ns, errs):
     return np.polyfit(np.log(np.asarray(ns, float)), np.log(np.asarray(errs)), 1)[0]

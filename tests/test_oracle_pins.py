@@ -428,13 +428,18 @@ def test_error_stats_closed_forms(dim):
     assert st["rms"] == pytest.approx(abs(delta) * np.sqrt((N - n_int) / N), rel=1e-12)
 
 
-@pytest.mark.parametrize("case", ["at_o4", "at_o6", "std_o4", "space2_o2", "space1_o2", "burgers_o4"])
+@pytest.mark.parametrize("case", ["at_o4", "at_o6", "std_o4", "space2_o2", "space1_o2", "burgers_o4", "burgers_ab2",
+                                  "case4_ab2", "case5_ab3"])
 def test_sampled_run_equals_the_full_run(case):
     """run_samples steps each sampled cell only inside its domain of dependence (reach max(h, 3) per step); it must
-    give the full run's values bit for bit, including cells on PE edges and next to the periodic wrap."""
-    if case == "burgers_o4":
+    give the full run's values bit for bit, including cells on PE edges and next to the periodic wrap, for forward
+    Euler and for Adams-Bashforth (analytic pre-history, and Burgers' Euler start)."""
+    if case.startswith("burgers"):
         spec = W.paper_case(6, 256, 13, (0.4, 0.3, 0.3))
-        spec["tsteps"] = 1
+        if case == "burgers_o4":
+            spec["tsteps"] = 1
+    elif case.startswith("case"):
+        spec = W.paper_case(int(case[4]), 384, 15, (0.4, 0.3, 0.3))
     else:
         order = int(case[-1])
         scheme = {"at": W.AT, "std": W.ASYNC_STD, "space2": W.AT_SPACE2, "space1": W.AT_SPACE1}[case.split("_")[0]]
