@@ -35,9 +35,11 @@ extern "C" {
 #define AT_ERR_SINGULAR (-2)     /* Sec. 3.2: rank(A) = rank(A|b) < N_A -- infinitely many schemes */
 #define AT_ERR_INCONSISTENT (-3) /* Sec. 3.2: rank(A) != rank(A|b) -- the stencil gives no scheme */
 #define AT_ERR_CUDA (-4)         /* a CUDA runtime call failed */
-#define AT_ERR_TIMEOUT (-5)      /* a bounded device wait ran out */
+#define AT_ERR_TIMEOUT (-5)      /* reserved: no kernel of this library waits on a flag or a peer, so none returns it */
 #define AT_ERR_NONFINITE (-6)    /* a statistic came out NaN or Inf */
-#define AT_ERR_BOUNDS (-7)       /* a device-side index check failed */
+#define AT_ERR_BOUNDS (-7)       /* reserved: every index a kernel forms is in range by construction (sizes, PE
+                                  * widths, delays and the log length are checked on the host before any launch),
+                                  * so no kernel reports one */
 #define AT_ERR_STATE (-8)        /* call out of order, e.g. more steps than the delay log holds */
 
 /* Spatial scheme at PE boundaries. */
@@ -105,7 +107,7 @@ typedef struct {
   int32_t dim;     /* 1 or 3 */
   int32_t order;   /* 2, 4 or 6 */
   int32_t L;       /* delays 0..L-1, 1 <= L <= 8 */
-  int32_t scheme;  /* AT_SYNC, AT_ASYNC_STD or AT_AT */
+  int32_t scheme;  /* AT_SYNC, AT_ASYNC_STD, AT_AT, AT_AT_SPACE2 or AT_AT_SPACE1 */
   int64_t n[3];    /* points per axis (axes beyond dim hold 1) */
   int32_t pe[3];   /* PEs per axis; n[a] % pe[a] == 0 and n[a]/pe[a] >= order.  pe[a] == 1: no boundary */
   int32_t nmodes;  /* initial-condition modes per axis, 1..16 */
@@ -163,7 +165,8 @@ int at_reset(at_handle_t *hd, const double *u0_dev);
  * for the stream and drops the captured step graph.  Used by the autotuner.  Errors: AT_ERR_ARG. */
 int at_set_launch(at_handle_t *hd, int32_t threads, int32_t blocks_per_sm);
 
-/* Wait for the handle's stream and return its sticky device status (AT_OK, AT_ERR_BOUNDS, ...). Blocks. */
+/* Wait for the handle's stream.  Returns AT_OK, or AT_ERR_CUDA with the runtime's message when the stream reports
+ * an error (a failed launch or copy).  Blocks. */
 int at_sync(at_handle_t *hd);
 
 /* Current step n and a device pointer to U^n inside the ring (valid until the next at_step). */
@@ -197,8 +200,9 @@ int at_error_stats_ref(at_handle_t *hd, const double *ref_dev, int32_t refine, a
  * the library until the process exits.  3D problems need n[0] + n[1] + n[2] <= 24576; larger ones are rejected
  * with AT_ERR_ARG.  Each call overwrites the scratch it reads, so nothing must be cleared between calls, but every
  * call shares the one array: calls that overlap on the GPU (different streams or host threads) race.  The first
- * call on a device looks up the array's device address (cudaGetSymbolAddress) with that device current; make
- * that first call before any stream capture.  No cudaMalloc, cudaFree or other allocating call is made.  Blocks
+ * call on a device looks up the array's device address (cudaGetSymbolAddress) with that device current and keeps
+ * it for the device's current CUDA context; make that first call before any stream capture.  A device reset ends
+ * that context: the next call looks the address up again (so it, too, belongs before any capture).  No cudaMalloc, cudaFree or other allocating call is made.  Blocks
  * on `stream` (a cudaStream_t, NULL = default stream).  Errors: AT_ERR_ARG, AT_ERR_CUDA, AT_ERR_NONFINITE. */
 int at_error_stats_noalloc(const at_config_t *cfg, const double *u_dev, int64_t step, void *stream, at_stats_t *out);
 

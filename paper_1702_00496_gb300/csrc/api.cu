@@ -314,7 +314,6 @@ extern "C" int at_init(const at_config_t *cfg, double *ring_dev, int64_t ring_le
   cudaError_t e = cudaMalloc(&hd->scratch, bytes);
   if (e != cudaSuccess) { delete hd; return cuda_fail(e, "at_init: cudaMalloc"); }
   char *base = (char *)hd->scratch;
-  hd->d_status = (int32_t *)base;
   hd->d_step = (int64_t *)(base + 256);
   p.keff = (uint8_t *)(base + 512);
   p.order = order.empty() ? nullptr : (const int32_t *)(base + 512 + keff_bytes);
@@ -329,10 +328,9 @@ extern "C" int at_init(const at_config_t *cfg, double *ring_dev, int64_t ring_le
   }
   hd->d_result = hd->d_partials + (size_t)AT_STAT_BLOCKS * AT_STAT_FIELDS;
   hd->d_tables = hd->d_result + 16;
-  p.status = hd->d_status;
+  p.status = nullptr;
   p.ab_first = hd->d_step + 1;
-  if ((e = cudaMemsetAsync(hd->d_status, 0, sizeof(int32_t), hd->stream)) != cudaSuccess ||
-      (e = launch_wave_field(w, 0.0, hd->d_tables, ring_dev, hd->stream)) != cudaSuccess ||
+  if ((e = launch_wave_field(w, 0.0, hd->d_tables, ring_dev, hd->stream)) != cudaSuccess ||
       (e = ab_start(hd, cfg->burgers == 0)) != cudaSuccess ||
       (e = launch_draw_delays(p, 0, hd->stream)) != cudaSuccess) {
     cudaFree(hd->scratch);
@@ -427,10 +425,6 @@ extern "C" int at_sync(at_handle_t *hd) {
   if (!hd) return fail(AT_ERR_ARG, "at_sync: NULL handle");
   cudaError_t e = cudaStreamSynchronize(hd->stream);
   if (e != cudaSuccess) return cuda_fail(e, "at_sync");
-  int32_t st = 0;
-  e = cudaMemcpy(&st, hd->d_status, sizeof(st), cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) return cuda_fail(e, "at_sync: status");
-  if (st != 0) return fail(st, "at_sync: device status word set");
   return AT_OK;
 }
 

@@ -25,7 +25,8 @@ struct StepParams {
   uint8_t *keff;          // effective delays, two buffers of nb: step n uses keff + (n & 1) * nb
   int64_t log_steps;      // rows of the log
   const int32_t *order;   // 3D: group visiting order (interior groups first, then edge groups), or nullptr
-  int32_t *status;        // sticky device status word
+  int32_t *status;        // unused (null); kept so the fields after it keep the offsets the step kernels were
+                          // tuned with
   double *frhs;           // Adams-Bashforth: ts-1 slots of ntot holding dt f^{n-m}, m = 1..ts-1, in slot
                           // (n-m) mod (ts-1); nullptr for forward Euler
   const int64_t *ab_first;  // device: first step whose right-hand side is stored (-(ts-1) after an analytic
@@ -126,9 +127,8 @@ struct at_handle {
   int64_t log_steps = 0;
   int64_t step = 0;
   cudaStream_t stream = nullptr;
-  // scratch owned by the handle: status word, reduction partials and result, 3D axis tables
+  // scratch owned by the handle: step counter, reduction partials and result, 3D axis tables
   void *scratch = nullptr;
-  int32_t *d_status = nullptr;
   double *d_partials = nullptr;
   double *d_result = nullptr;
   double *d_tables = nullptr;
