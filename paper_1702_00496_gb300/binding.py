@@ -363,8 +363,16 @@ def at_adjoint_backward(h, lam, grad_u0, want_alpha: bool = True):
 
 def at_error_stats_noalloc(cfg: Config, u, step: int, stream=None) -> dict:
     """Statistics of a device field u (CUDA float64 tensor of the problem cfg at `step`) without any allocation
-    inside the library (static device scratch)."""
+    inside the library (static device scratch).  The C entry point takes no length, so the tensor is checked here:
+    a CUDA, float64, contiguous tensor of at least n0*n1*n2 elements; the call runs with u's device current."""
+    import torch
+    ntot = int(cfg.s.n[0]) * int(cfg.s.n[1]) * int(cfg.s.n[2])
+    if not (isinstance(u, torch.Tensor) and u.is_cuda and u.dtype == torch.float64 and u.is_contiguous()
+            and u.numel() >= ntot):
+        raise ATError(AT_ERR_ARG, "at_error_stats_noalloc (binding)",
+                      f"u must be a contiguous CUDA float64 tensor of at least {ntot} elements")
     st = at_stats_t()
-    _check(load().at_error_stats_noalloc(C.byref(cfg.s), C.c_void_p(u.data_ptr()), int(step), _stream_ptr(stream),
-                                         C.byref(st)), "at_error_stats_noalloc")
+    with torch.cuda.device(u.device):
+        _check(load().at_error_stats_noalloc(C.byref(cfg.s), C.c_void_p(u.data_ptr()), int(step),
+                                             _stream_ptr(stream), C.byref(st)), "at_error_stats_noalloc")
     return st.as_dict()

@@ -9,6 +9,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
+
+#include <cuda.h>  // CUcontext and the driver's result type only: the two driver calls are looked up at run time
 
 #include "../../include/at.h"
 #include "internal.h"
@@ -24,8 +27,45 @@ constexpr int kScratchDoubles = kPartials + kResult + kMaxTables;
 
 __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
+// The array's device address, looked up with cudaGetSymbolAddress once per CUDA context and kept per device
+// together with the id of the context it belongs to.  A device reset (cudaDeviceReset by the caller or by
+// another library) destroys the context and the module image with it; the next call then sees a new context id
+// and looks the address up again instead of using the stale one.  The mutex makes the look-up safe when several
+// host threads call at once.
 constexpr int kMaxDevices = 64;
-double *g_scratch_addr[kMaxDevices] = {nullptr};
+struct ScratchAddr {
+  unsigned long long ctx_id;
+  double *addr;
+};
+ScratchAddr g_scratch_addr[kMaxDevices] = {};
+std::mutex g_scratch_mu;
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+std::once_flag g_driver_once;
+
+// Id of the context current on this thread (0 when none is, or the driver does not offer the calls).
+unsigned long long current_context_id() {
+  std::call_once(g_driver_once, [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f);
+  });
+  if (!g_ctx_get_current || !g_ctx_get_id) return 0;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return 0;
+  if (g_ctx_get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 int fail(int code, const char *msg) {
   at_internal_set_error(msg);
@@ -56,14 +96,26 @@ extern "C" int at_error_stats_noalloc(const at_config_t *cfg, const double *u_de
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "at_error_stats_noalloc: device");
   if (dev < 0 || dev >= kMaxDevices) return fail(AT_ERR_ARG, "at_error_stats_noalloc: device index beyond 63");
-  // once per device, with that device current: the device address of the static scratch
-  if (g_scratch_addr[dev] == nullptr) {
-    void *ptr = nullptr;
-    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess) return cuda_fail(e, "at_error_stats_noalloc: cudaGetSymbolAddress");
-    g_scratch_addr[dev] = static_cast<double *>(ptr);
+  // once per device and context, with that device current: the device address of the static scratch.  The
+  // runtime makes the device's primary context current on the first call that needs it; before that, no
+  // context id is known, and the address is looked up (which makes the context current) and cached after.
+  double *partials = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    unsigned long long ctx = current_context_id();
+    ScratchAddr &slot = g_scratch_addr[dev];
+    if (ctx != 0 && slot.addr != nullptr && slot.ctx_id == ctx) {
+      partials = slot.addr;
+    } else {
+      void *ptr = nullptr;
+      e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess) return cuda_fail(e, "at_error_stats_noalloc: cudaGetSymbolAddress");
+      partials = static_cast<double *>(ptr);
+      if (ctx == 0) ctx = current_context_id();
+      slot.ctx_id = ctx;
+      slot.addr = ctx != 0 ? partials : nullptr;  // without a context id nothing is cached
+    }
   }
-  double *partials = g_scratch_addr[dev];
   double *result = partials + kPartials;
   double *tables = result + kResult;
 

@@ -251,3 +251,29 @@ def test_ensemble_runs_are_validated_and_sized_per_member():
         assert e.value.code == B.AT_ERR_ARG
     with pytest.raises(ValueError):
         at_ensemble_sizes(cfgs, [1, 2])
+
+
+def test_noalloc_binding_refuses_a_host_field():
+    """at_error_stats_noalloc takes no length: the binding checks the tensor (CUDA, float64, contiguous, long
+    enough) before the call, so a host tensor never reaches the library."""
+    import torch
+    spec, _ = W.wl_1d(4096, 16, 4, 4, 0, 81, range(1, 6))
+    for bad in (torch.zeros(4096, dtype=torch.float64), np.zeros(4096)):
+        with pytest.raises(B.ATError) as e:
+            B.at_error_stats_noalloc(B.Config(spec), bad, 0)
+        assert e.value.code == B.AT_ERR_ARG
+
+
+def test_library_delay_word_reproduces_the_published_known_answer():
+    """The library's host copy of the delay generator (at_delay) against the first word of the all-zero
+    Philox4x32-10 known-answer vector (counter (0,0,0,0), key (0,0): step 0, side 0, seed 0; the other published
+    vectors have counter words that at_delay keeps at zero).  Two-bin thresholds at x0 and x0 + 1 fix the word
+    exactly."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    x0 = int(rows[0][6], 16)
+    assert [int(v, 16) for v in rows[0][:6]] == [0] * 6
+    assert P.at_delay(0, 0, 0, 2, np.array([x0], dtype=np.uint64)) == 1
+    assert P.at_delay(0, 0, 0, 2, np.array([x0 + 1], dtype=np.uint64)) == 0
+    for L in (2, 3, 4, 8):
+        assert P.at_delay(0, 0, 0, L) == (x0 * L) >> 32
