@@ -32,7 +32,7 @@ import workloads as W  # noqa: E402
 METRIC = "grid-point updates/s (FP64)"
 PEAK_FP64_FLOPS = 152 * 2 * 2 * 2.07e9  # 152 SMs x 2 FP64 FMA lanes/clk x 2 flop x 2.07 GHz max clock
 # DRAM bytes (read + write) per launch of the step kernel, the mean of two launches of one ncu capture of the current
-# kernel source (profiles/forward_group_kernel_1d_n16m*.md); None where no capture of the current source exists.
+# kernel source; None where no capture of the current source exists.
 MEASURED_TRAFFIC = {
     ("1d_n16m", "forward_group_kernel<1,2,false>"): 136.95e6 + 80.50e6,
     ("1d_n16m_case2", "forward_group_kernel<1,1,false>"): None,
@@ -394,6 +394,7 @@ def main():
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="ensemble: CTAs per SM (0: occupancy limit)")
     ap.add_argument("--skip-one-at-a-time", action="store_true")
     ap.add_argument("--retune", action="store_true", help="ignore the autotuner cache")
+    ap.add_argument("--launch", default="", help="forward step: fixed launch shape THREADS,BLOCKS_PER_SM (no tuning)")
     ap.add_argument("--adjoint-every", type=int, default=0,
                     help="adjoint: checkpoint interval (0: sqrt(T); >= T: every level resident, no recompute)")
     args = ap.parse_args()
@@ -427,7 +428,13 @@ def main():
     stream = torch.cuda.current_stream()
     solver = Solver(spec, log_steps=0, device=f"cuda:{local}", stream=stream)
     from paper_1702_00496_gb300 import autotune
-    launch = autotune.tune_forward(solver, spec, use_cache=not args.retune)
+    if args.launch:
+        launch = tuple(int(v) for v in args.launch.split(","))
+        from paper_1702_00496_gb300 import at_set_launch
+        at_set_launch(solver.h, *launch)
+        solver.reset()
+    else:
+        launch = autotune.tune_forward(solver, spec, use_cache=not args.retune)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device=f"cuda:{local}")  # 512 MiB > L2
     kern_ev = []
     burgers = bool(spec.get("burgers", 0))
