@@ -16,9 +16,11 @@
 // with q_{a,j} = dt cd2_j / dx_a^2 (the AT second derivative times dt); the kernel accumulates
 // <lambda^{n+1}, dt D2_AT U> per block, in a fixed block-to-cell assignment, so the sum is deterministic.
 //
-// Forward levels for the alpha term come from a segment buffer: the forward pass keeps a checkpoint of the
-// R-1 live levels every s steps (s ~ sqrt(steps)); the backward sweep restores one segment at a time, recomputes
-// its levels with the forward kernels, and runs the adjoint steps of that segment in reverse.
+// Forward levels for the alpha term come from a segment buffer: the forward pass keeps a checkpoint every s steps
+// (s ~ sqrt(steps)); the backward sweep restores one segment at a time, recomputes its levels with the forward
+// kernels, and runs the adjoint steps of that segment in reverse.  A checkpoint at step n0 holds U^{n0} in full and,
+// of the R-2 older levels the next steps read (Eq. "general_deriv_async": only buffer points are read at delayed
+// levels), only the cells within the buffer reach of a PE face -- the strips below.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -319,8 +321,8 @@ __device__ __forceinline__ void adj_axis_taps(const StepParams &f, int ax, const
     if (j == 0) continue;
     const int ia = wrap_coord(c - j, na);
     const int64_t base = i0 + (int64_t)(ia - c) * st;
-    const double2 e = LdgNC::ld2(ln + base), g = LdgNC::ld2(ln + base + 2);
-    const double lr[4] = {e.x, e.y, g.x, g.y};
+    const double4_32a e = LdgNC::ld4(ln + base);
+    const double lr[4] = {e.x, e.y, e.z, e.w};
     const double s = f.s[ax][j + H];
     const bool cross = (SIDE == 1 && j > H - CNT) || (SIDE == 2 && j < CNT - H);
 #pragma unroll
@@ -393,11 +395,7 @@ __device__ __forceinline__ void adjoint_group(const AdjParams &a, const uint8_t 
   constexpr int W = XWin<H>::W, NW = XWin<H>::N;
   double lv[NW];
   if (x0 >= W && x0 + 4 + W <= nx) {
-#pragma unroll
-    for (int t = 0; t < NW; t += 2) {
-      const double2 l = LdgNC::ld2(ln + i0 - W + t);
-      lv[t] = l.x; lv[t + 1] = l.y;
-    }
+    load_xwin<W, LdgNC>(ln + i0 - W, lv);
   } else {
 #pragma unroll
     for (int t = 0; t < NW; ++t) lv[t] = LdgNC::ld(ln + row + wrap_coord(x0 - W + t, nx));
@@ -414,8 +412,8 @@ __device__ __forceinline__ void adjoint_group(const AdjParams &a, const uint8_t 
   int kX[4] = {-1, -1, -1, -1};
   double id[4] = {f.zero, f.zero, f.zero, f.zero};
   if (AB) {
-    const double2 e0 = LdgNC::ld2(lnext + i0), e1 = LdgNC::ld2(lnext + i0 + 2);
-    id[0] = e0.x; id[1] = e0.y; id[2] = e1.x; id[3] = e1.y;
+    const double4_32a e0 = LdgNC::ld4(lnext + i0);
+    id[0] = e0.x; id[1] = e0.y; id[2] = e0.z; id[3] = e0.w;
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -446,21 +444,15 @@ __device__ __forceinline__ void adjoint_group(const AdjParams &a, const uint8_t 
   }
   const int64_t fresh = n - a.reach;
   const int snl = (int)(n % a.Rl);
-  double2 *cur = reinterpret_cast<double2 *>(a.lam + snl * N + i0);
+  double *cur = a.lam + snl * N + i0;
   if (a.reach == 0) {
-    cur[0] = make_double2(A[0], A[1]);
-    cur[1] = make_double2(A[2], A[3]);
+    st4(cur, A[0], A[1], A[2], A[3]);
     return;
   }
-  if (fresh >= 0) {
-    double2 *fr = reinterpret_cast<double2 *>(a.lam + slot_back(snl, a.reach, a.Rl) * N + i0);
-    fr[0] = make_double2(0.0, 0.0);
-    fr[1] = make_double2(0.0, 0.0);
-  }
+  if (fresh >= 0) st4(a.lam + slot_back(snl, a.reach, a.Rl) * N + i0, 0.0, 0.0, 0.0, 0.0);
   {
-    const double2 p0 = cur[0], p1 = cur[1];
-    cur[0] = make_double2(p0.x + A[0], p0.y + A[1]);
-    cur[1] = make_double2(p1.x + A[2], p1.y + A[3]);
+    const double4_32a p = LdCoherent::ld4(cur);
+    st4(cur, p.x + A[0], p.y + A[1], p.z + A[2], p.w + A[3]);
   }
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
@@ -468,17 +460,16 @@ __device__ __forceinline__ void adjoint_group(const AdjParams &a, const uint8_t 
     if (k <= 0) continue;
     for (int m = 0; m < f.T; ++m) {
       const double wk = f.w[k][m];
-      double2 *o = reinterpret_cast<double2 *>(a.lam + slot_back(snl, k + m, a.Rl) * N + i0);
-      const double2 p0 = o[0], p1 = o[1];
-      o[0] = make_double2(fma(wk, X[b][0], p0.x), fma(wk, X[b][1], p0.y));
-      o[1] = make_double2(fma(wk, X[b][2], p1.x), fma(wk, X[b][3], p1.y));
+      double *o = a.lam + slot_back(snl, k + m, a.Rl) * N + i0;
+      const double4_32a p = LdCoherent::ld4(o);
+      st4(o, fma(wk, X[b][0], p.x), fma(wk, X[b][1], p.y), fma(wk, X[b][2], p.z), fma(wk, X[b][3], p.w));
     }
   }
 }
 
 // Backward step n, one launch, which also draws the delays of step n-1.  MODE 0: every cell by the general path
-// (shapes without groups of four).  MODE 1: cells in groups of four x points (n[0] % 4 == 0, 16-byte aligned
-// slots); a group whose cells and neighbours all lie inside one PE and away from the domain ends takes the
+// (shapes without groups of four).  MODE 1: cells in groups of four x points (n[0] % 4 == 0, 32-byte aligned
+// slots, read and written with 32-byte accesses); a group whose cells and neighbours all lie inside one PE and away from the domain ends takes the
 // straight path, the others the edge path (adjoint_group).
 #ifndef AT_ADJ_MIN_BLOCKS
 #define AT_ADJ_MIN_BLOCKS 3
@@ -536,19 +527,12 @@ __global__ void __launch_bounds__(256, AdjBounds<MODE>::min_blocks) adjoint_step
       }
       constexpr int W = XWin<H>::W, NW = XWin<H>::N;
       double lv[NW], uv[NW];
-#pragma unroll
-      for (int t = 0; t < NW; t += 2) {
-        const double2 l = LdgNC::ld2(ln + i0 - W + t);
-        lv[t] = l.x; lv[t + 1] = l.y;
-        if (AL) {
-          const double2 u = LdgNC::ld2(un + i0 - W + t);
-          uv[t] = u.x; uv[t + 1] = u.y;
-        }
-      }
+      load_xwin<W, LdgNC>(ln + i0 - W, lv);
+      if (AL) load_xwin<W, LdgNC>(un + i0 - W, uv);
       double A[4], D[4], id[4] = {f.zero, f.zero, f.zero, f.zero};
       if (AB) {
-        const double2 e0 = LdgNC::ld2(lnext + i0), e1 = LdgNC::ld2(lnext + i0 + 2);
-        id[0] = e0.x; id[1] = e0.y; id[2] = e1.x; id[3] = e1.y;
+        const double4_32a e0 = LdgNC::ld4(lnext + i0);
+        id[0] = e0.x; id[1] = e0.y; id[2] = e0.z; id[3] = e0.w;
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -569,31 +553,25 @@ __global__ void __launch_bounds__(256, AdjBounds<MODE>::min_blocks) adjoint_step
 #pragma unroll
           for (int j = -H; j <= H; ++j) {
             if (j == 0) continue;
-            const double2 la = LdgNC::ld2(ln + i0 - j * st), lb = LdgNC::ld2(ln + i0 - j * st + 2);
-            double2 ua = make_double2(0.0, 0.0), ub = ua;
-            if (AL) { ua = LdgNC::ld2(un + i0 + j * st); ub = LdgNC::ld2(un + i0 + j * st + 2); }
+            const double4_32a la = LdgNC::ld4(ln + i0 - j * st);
+            double4_32a ua = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+            if (AL) ua = LdgNC::ld4(un + i0 + j * st);
             const double s = f.s[ax][j + H], qq = f.q[ax][j + H];
-            A[0] = fma(s, la.x, A[0]); A[1] = fma(s, la.y, A[1]); A[2] = fma(s, lb.x, A[2]); A[3] = fma(s, lb.y, A[3]);
-            if (AL) { D[0] = fma(qq, ua.x, D[0]); D[1] = fma(qq, ua.y, D[1]); D[2] = fma(qq, ub.x, D[2]); D[3] = fma(qq, ub.y, D[3]); }
+            A[0] = fma(s, la.x, A[0]); A[1] = fma(s, la.y, A[1]); A[2] = fma(s, la.z, A[2]); A[3] = fma(s, la.w, A[3]);
+            if (AL) { D[0] = fma(qq, ua.x, D[0]); D[1] = fma(qq, ua.y, D[1]); D[2] = fma(qq, ua.z, D[2]); D[3] = fma(qq, ua.w, D[3]); }
           }
         }
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) if (AL) galpha = fma(lv[q + W], D[q], galpha);
-      double2 *cur = reinterpret_cast<double2 *>(a.lam + (n % a.Rl) * N + i0);
+      double *cur = a.lam + (n % a.Rl) * N + i0;
       if (a.reach == 0) {
-        cur[0] = make_double2(A[0], A[1]);
-        cur[1] = make_double2(A[2], A[3]);
+        st4(cur, A[0], A[1], A[2], A[3]);
       } else {
-        const double2 p0 = cur[0], p1 = cur[1];
-        cur[0] = make_double2(p0.x + A[0], p0.y + A[1]);
-        cur[1] = make_double2(p1.x + A[2], p1.y + A[3]);
+        const double4_32a p = LdCoherent::ld4(cur);
+        st4(cur, p.x + A[0], p.y + A[1], p.z + A[2], p.w + A[3]);
         const int64_t fresh = n - a.reach;
-        if (fresh >= 0) {
-          double2 *fr = reinterpret_cast<double2 *>(a.lam + (fresh % a.Rl) * N + i0);
-          fr[0] = make_double2(0.0, 0.0);
-          fr[1] = make_double2(0.0, 0.0);
-        }
+        if (fresh >= 0) st4(a.lam + (fresh % a.Rl) * N + i0, 0.0, 0.0, 0.0, 0.0);
       }
     }
   }
@@ -628,6 +606,97 @@ __global__ void sum_blocks_kernel(const double *g_blk, int nblk, double *out) {
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if (lane == 0) *out = s;
   }
+}
+
+// Cells that any step reads at a delayed level: those within hw cells of a face of their own PE along a split axis
+// (a buffer point of a PE lies in the neighbour PE, at most hw cells from the face they share; hw = h for the
+// central and time-expanded rows and Burgers' equation, 3 for the rows expanded in space, whose (2,2,2)a row reads
+// i-1 .. i-3 across the edge).  They are enumerated without a list, as three disjoint boxes of a mixed-radix index:
+//   part Z: z in the strips of z (any y, x);
+//   part Y: z outside them, y in the strips of y (any x);
+//   part X: z and y outside, x in the strips of x.
+// Along an axis, strip coordinate t lies in PE t / w at offset t % w (w = min(2 hw, S) cells per PE: the first hw and
+// the last hw cells, or all S when 2 hw >= S); complement coordinate t in PE t / (S - 2 hw), hw cells in.  An axis
+// without PE boundaries has no strip cells.
+struct StripMap {
+  int32_t n[3], S[3], hw[3];
+  int64_t cs[3], cc[3];  // strip and complement coordinates per axis
+  int64_t part_z, part_y, total;
+};
+
+StripMap make_strips(const StepParams &p) {
+  StripMap m;
+  const int hw = p.scheme >= AT_AT_SPACE2 ? (p.h > 3 ? p.h : 3) : p.h;
+  for (int a = 0; a < 3; ++a) {
+    m.n[a] = p.n[a];
+    m.S[a] = p.S[a];
+    const bool split = a < p.dim && p.use_pe[a];
+    m.hw[a] = split ? hw : 0;
+    const int64_t w = 2 * (int64_t)hw < p.S[a] ? 2 * hw : p.S[a];
+    m.cs[a] = split ? (int64_t)p.pe[a] * w : 0;
+    m.cc[a] = (int64_t)p.n[a] - m.cs[a];
+  }
+  m.part_z = m.cs[2] * m.n[1] * m.n[0];
+  m.part_y = m.cc[2] * m.cs[1] * m.n[0];
+  m.total = m.part_z + m.part_y + m.cc[2] * m.cc[1] * m.cs[0];
+  return m;
+}
+
+__device__ __forceinline__ int strip_coord(const StripMap &m, int a, int64_t t) {
+  const int S = m.S[a], hw = m.hw[a];
+  if (2 * hw >= S) return (int)t;  // every cell of the axis
+  const int w = 2 * hw;
+  const int64_t pe = t / w;
+  const int r = (int)(t - pe * w);
+  return (int)(pe * S + (r < hw ? r : S - w + r));
+}
+
+__device__ __forceinline__ int comp_coord(const StripMap &m, int a, int64_t t) {
+  if (m.hw[a] == 0) return (int)t;
+  const int w = m.S[a] - 2 * m.hw[a];
+  const int64_t pe = t / w;
+  return (int)(pe * m.S[a] + m.hw[a] + (t - pe * w));
+}
+
+__device__ __forceinline__ int64_t strip_cell(const StripMap &m, int64_t j) {
+  const int64_t n0 = m.n[0], n1 = m.n[1];
+  int64_t x, y, z;
+  if (j < m.part_z) {
+    const int64_t row = j / n0;
+    x = j - row * n0;
+    y = row % n1;
+    z = strip_coord(m, 2, row / n1);
+  } else if (j - m.part_z < m.part_y) {
+    const int64_t k = j - m.part_z, row = k / n0;
+    x = k - row * n0;
+    y = strip_coord(m, 1, row % m.cs[1]);
+    z = comp_coord(m, 2, row / m.cs[1]);
+  } else {
+    const int64_t k = j - m.part_z - m.part_y, r = k / m.cs[0];
+    x = strip_coord(m, 0, k - r * m.cs[0]);
+    y = comp_coord(m, 1, r % m.cc[1]);
+    z = comp_coord(m, 2, r / m.cc[1]);
+  }
+  return (z * n1 + y) * n0 + x;
+}
+
+// PACK: packed[j] = field[cell(j)]; else field[cell(j)] = packed[j], for j < m.total.
+template <bool PACK>
+__global__ void strip_copy_kernel(double *__restrict__ field, double *__restrict__ packed, const StripMap m) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m.total; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = strip_cell(m, j);
+    if (PACK) packed[j] = field[c];
+    else field[c] = packed[j];
+  }
+}
+
+cudaError_t launch_strip_copy(bool pack, double *field, double *packed, const StripMap &m, cudaStream_t st) {
+  if (m.total == 0) return cudaSuccess;
+  const int64_t b = (m.total + 255) / 256;
+  const int blocks = (int)(b < 152 * 8 ? b : 152 * 8);
+  if (pack) strip_copy_kernel<true><<<blocks, 256, 0, st>>>(field, packed, m);
+  else strip_copy_kernel<false><<<blocks, 256, 0, st>>>(field, packed, m);
+  return cudaGetLastError();
 }
 
 const int kAdjThreads = 256;
@@ -672,7 +741,8 @@ void launch_alpha(const AdjParams &a, int64_t n, int nblk, bool grouped, cudaStr
 
 bool adjoint_grouped(const AdjParams &a) {
   return a.f.n[0] % 4 == 0 && (!a.f.use_pe[0] || a.f.S[0] % 4 == 0) && (a.f.dim == 1 || a.f.order != nullptr) &&
-         (reinterpret_cast<uintptr_t>(a.lam) % 16) == 0 && (reinterpret_cast<uintptr_t>(a.f.ring) % 16) == 0;
+         (reinterpret_cast<uintptr_t>(a.lam) % 32) == 0 && (reinterpret_cast<uintptr_t>(a.f.ring) % 32) == 0 &&
+         (a.mu == nullptr || (reinterpret_cast<uintptr_t>(a.mu) % 32) == 0);
 }
 
 // The straight (interior) path of the grouped kernel needs a group whose cells and stencil neighbours (the x window of W = h
@@ -730,8 +800,8 @@ int cuda_fail(cudaError_t e, const char *where) {
 namespace {
 
 // Workspace layout (doubles, each part rounded up to 32 doubles):
-//   checkpoints  nck x (R-1+ts-1) x ntot  levels n0-R+2 .. n0 and the ts-1 stored right-hand sides of every
-//                                         checkpoint n0 = 0, s, 2s, ...
+//   checkpoints  nck x ck_len             for every checkpoint n0 = 0, s, 2s, ...: U^{n0} (ntot), the strip cells of
+//                                         levels n0-R+2 .. n0-1 ((R-2) x nstrip), the ts-1 stored right-hand sides
 //   segment      (s + R - 1) x ntot       levels of the segment being replayed (level m in slot m mod depth)
 //   segment rhs  (ts - 1) x ntot          its stored right-hand sides (Adams-Bashforth)
 //   lambda       (R + ts - 1) x ntot      adjoint ring
@@ -739,7 +809,8 @@ namespace {
 //   g_blk        nblk                     per-block d J / d alpha accumulators, then the sum
 //   delays       2 x 2 x nb bytes         effective delays of the recompute and of the backward sweep
 struct AdjLayout {
-  int64_t s, nck, seg_depth, ck_fields, lam_slots, ck, seg, segf, lam, mu, gblk, keff, total;
+  int64_t s, nck, seg_depth, lam_slots, ck, seg, segf, lam, mu, gblk, keff, total;
+  int64_t nstrip, ck_len, ck_strips, ck_rhs;  // strip cells; one checkpoint's length and the offsets of its parts
 };
 
 int64_t up32(int64_t v) { return (v + 31) / 32 * 32; }
@@ -752,10 +823,13 @@ AdjLayout layout(const at_handle *hd, int64_t nsteps, int64_t every) {
   L.nck = nsteps > 0 ? (nsteps + L.s - 1) / L.s : 0;
   const int64_t nf = hd->sp.ts - 1;  // Adams-Bashforth: stored right-hand sides, part of the forward state
   L.seg_depth = L.s + R - 1;
-  L.ck_fields = R - 1 + nf;
+  L.nstrip = make_strips(hd->sp).total;
+  L.ck_strips = up32(N);
+  L.ck_rhs = L.ck_strips + up32((R > 2 ? R - 2 : 0) * L.nstrip);
+  L.ck_len = L.ck_rhs + nf * up32(N);
   L.lam_slots = R + nf;             // the adjoint levels n+1+m that mu still needs stay alive
   L.ck = 0;
-  L.seg = L.ck + up32(L.nck * L.ck_fields * N);
+  L.seg = L.ck + L.nck * L.ck_len;
   L.segf = L.seg + up32(L.seg_depth * N);
   L.lam = L.segf + up32(nf * N);
   L.mu = L.lam + up32(L.lam_slots * N);
@@ -794,7 +868,7 @@ extern "C" int at_adjoint_forward(at_handle_t *hd, int64_t nsteps, int64_t ckpt_
   if (hd->step != 0) return fail(AT_ERR_STATE, "at_adjoint_forward: the handle must be at step 0 (at_reset)");
   const AdjLayout L = layout(hd, nsteps, ckpt_every);
   if (work_len < L.total) return fail(AT_ERR_ARG, "at_adjoint_forward: workspace too small");
-  if (reinterpret_cast<uintptr_t>(work_dev) % 16) return fail(AT_ERR_ARG, "at_adjoint_forward: workspace not 16-byte aligned");
+  if (reinterpret_cast<uintptr_t>(work_dev) % 32) return fail(AT_ERR_ARG, "at_adjoint_forward: workspace not 32-byte aligned");
   // at_step's limits, checked before any step so a refused pass leaves the handle at step 0
   if (hd->sp.log && nsteps > hd->log_steps) return fail(AT_ERR_STATE, "at_adjoint_forward: delay log is full");
   if (nsteps > 0xFFFFFFFFll) return fail(AT_ERR_STATE, "at_adjoint_forward: step counter exceeds 32 bits");
@@ -824,19 +898,18 @@ extern "C" int at_adjoint_forward(at_handle_t *hd, int64_t nsteps, int64_t ckpt_
     hd->step = nsteps;
     hd->adj_resident = true;
   }
+  const StripMap strips = make_strips(hd->sp);
   for (int64_t c = 0; !hd->adj_resident && c < L.nck; ++c) {
     const int64_t n0 = c * L.s;
-    for (int64_t lev = n0 - R + 2; lev <= n0; ++lev) {
-      if (lev < 0) continue;
-      cudaError_t e = copy_field(work_dev + L.ck + (c * L.ck_fields + (lev - (n0 - R + 2))) * N,
-                                 hd->sp.ring + (lev % R) * N, N, hd->stream);
-      if (e != cudaSuccess) return cuda_fail(e, "at_adjoint_forward: checkpoint");
-    }
-    for (int64_t m = 0; m + 1 < hd->sp.ts; ++m) {  // the stored right-hand sides, slot by slot
-      cudaError_t e = copy_field(work_dev + L.ck + (c * L.ck_fields + R - 1 + m) * N, hd->sp.frhs + m * N, N,
-                                 hd->stream);
-      if (e != cudaSuccess) return cuda_fail(e, "at_adjoint_forward: checkpoint");
-    }
+    double *ck = work_dev + L.ck + c * L.ck_len;
+    cudaError_t e = copy_field(ck, hd->sp.ring + (n0 % R) * N, N, hd->stream);  // U^{n0} in full
+    for (int64_t lev = n0 - R + 2; lev < n0 && e == cudaSuccess; ++lev)  // older levels: the strip cells only
+      if (lev >= 0)
+        e = launch_strip_copy(true, hd->sp.ring + (lev % R) * N, ck + L.ck_strips + (lev - (n0 - R + 2)) * L.nstrip,
+                              strips, hd->stream);
+    for (int64_t m = 0; m + 1 < hd->sp.ts && e == cudaSuccess; ++m)  // the stored right-hand sides, slot by slot
+      e = copy_field(ck + L.ck_rhs + m * up32(N), hd->sp.frhs + m * N, N, hd->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "at_adjoint_forward: checkpoint");
     const int64_t todo = (n0 + L.s <= nsteps) ? L.s : nsteps - n0;
     int rc = at_step(hd, todo);
     if (rc) return rc;
@@ -861,6 +934,7 @@ extern "C" int at_adjoint_backward(at_handle_t *hd, const double *lambda_dev, do
   cudaStream_t st = hd->stream;
   cudaError_t e = cudaSuccess;
   const int nblk = adj_blocks();
+  const StripMap strips = make_strips(hd->sp);
   // segment parameters: forward levels in the segment buffer, no log, own delay buffers
   StepParams seg = hd->sp;
   seg.ring = w + L.seg;
@@ -905,12 +979,14 @@ extern "C" int at_adjoint_backward(at_handle_t *hd, const double *lambda_dev, do
   }
   for (int64_t c = L.nck - 1; c >= 0 && e == cudaSuccess; --c) {
     const int64_t n0 = c * L.s, n1 = (n0 + L.s < Ns) ? n0 + L.s : Ns;
-    for (int64_t lev = n0 - R + 2; need_fwd && lev <= n0 && e == cudaSuccess; ++lev) {
-      if (lev < 0) continue;
-      e = copy_field(seg.ring + (lev % seg.R) * N, w + L.ck + (c * L.ck_fields + (lev - (n0 - R + 2))) * N, N, st);
-    }
+    double *ck = w + L.ck + c * L.ck_len;
+    if (need_fwd) e = copy_field(seg.ring + (n0 % seg.R) * N, ck, N, st);
+    for (int64_t lev = n0 - R + 2; need_fwd && lev < n0 && e == cudaSuccess; ++lev)
+      if (lev >= 0)
+        e = launch_strip_copy(false, seg.ring + (lev % seg.R) * N, ck + L.ck_strips + (lev - (n0 - R + 2)) * L.nstrip,
+                              strips, st);
     for (int64_t m = 0; need_fwd && m + 1 < hd->sp.ts && e == cudaSuccess; ++m)
-      e = copy_field(seg.frhs + m * N, w + L.ck + (c * L.ck_fields + R - 1 + m) * N, N, st);
+      e = copy_field(seg.frhs + m * N, ck + L.ck_rhs + m * up32(N), N, st);
     // the forward levels serve the alpha term (and Burgers' transposed step): without them no recompute
     if (need_fwd && e == cudaSuccess) e = launch_draw_delays(seg, n0, st);
     for (int64_t n = n0; need_fwd && n + 1 < n1 && e == cudaSuccess; ++n) e = launch_forward_step(seg, n, nullptr, st);

@@ -58,12 +58,27 @@ def test_adjoint_matches_cpu_adjoint(name, make, nsteps):
     assert ga == pytest.approx(gao, rel=1e-10)
 
 
-def test_checkpoint_interval_does_not_change_the_gradient():
-    spec, _ = W.wl_1d(512, 8, 4, 4, 0, 71, (1, 2, 3))
-    target = np.zeros(512)
+CKPT_CASES = [
+    ("1d_o4", lambda: W.wl_1d(512, 8, 4, 4, 0, 71, (1, 2, 3))[0], 97, False),
+    # PEs of 16 x 12 x 8: the checkpoints keep the older levels on 4 of every S cells per axis only
+    ("3d_o4", lambda: W.wl_3d([32, 24, 16], [2, 2, 2], 4, 3, 0, 79, c=(0.3, 0.2, 0.1))[0], 31, False),
+    # Adams-Bashforth from a caller's field: the checkpoints also hold the stored right-hand sides
+    ("1d_ab2", lambda: W.wl_1d(512, 8, 4, 3, 0, 78, (1, 2, 3), r_alpha=0.05, tsteps=2)[0], 61, True),
+]
+
+
+@pytest.mark.parametrize("name,make,nsteps,callers_field", CKPT_CASES, ids=[c[0] for c in CKPT_CASES])
+def test_checkpoint_interval_does_not_change_the_gradient(name, make, nsteps, callers_field):
+    """Every checkpoint interval -- each step, sqrt(T), uneven segments, one segment with every level resident --
+    gives the same bits: a checkpoint restores U^{n0} and, of the older levels, the cells the steps read at delayed
+    levels (those within the buffer reach of a PE face), so the recomputed levels are the forward pass's."""
+    spec = make()
+    cfg = oracle.Config(spec)
+    target = np.zeros(cfg.shape)
+    u0 = oracle.initial(cfg) if callers_field else None
     ref = None
-    for every in (0, 1, 5, 13, 97):
-        J, g, ga, _ = _gpu_grad(spec, 97, target, every)
+    for every in (0, 1, 5, 13, nsteps):
+        J, g, ga, _ = _gpu_grad(spec, nsteps, target, every, u0=u0)
         if ref is None:
             ref = (J, g, ga)
         assert J == ref[0] and ga == ref[2] and np.array_equal(g, ref[1]), every

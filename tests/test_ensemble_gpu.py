@@ -86,14 +86,19 @@ def test_single_member_and_repeated_runs():
 
 
 def test_full_ensemble_workload_sampled():
-    """1024 realizations, N_r in {2^10..2^16}, P_r = N_r/64, L_r in {2,3,4}, 5000 steps, one launch: the
-    smallest and largest members against the oracle over the full run, all statistics finite."""
-    from paper_1702_00496_gb300 import Ensemble
+    """1024 realizations, N_r in {2^10..2^16}, P_r = N_r/64, L_r in {2,3,4}, 5000 steps, one launch in the launch
+    shape the autotuner picks for the bench: the first member of every (N_r, L_r) pair (21 members: every grid
+    size with every delay range) against the oracle over the full run, all statistics finite."""
+    from paper_1702_00496_gb300 import Ensemble, autotune
     specs, nsteps = W.ensemble_members()
-    ens = Ensemble(specs, nsteps, log=True)
+    threads, ctas = autotune.tune_ensemble(specs, [nsteps] * len(specs))
+    ens = Ensemble(specs, nsteps, log=True, threads=threads, ctas_per_sm=ctas)
     ens.run()
-    sizes = np.array([s["n"][0] for s in specs])
-    pick = [int(np.argmin(sizes)), int(np.argmax(sizes)), int(np.nonzero(sizes == 1 << 13)[0][0])]
+    first = {}
+    for r, s in enumerate(specs):
+        first.setdefault((s["n"][0], s["L"]), r)
+    pick = sorted(first.values())
+    assert len(pick) == 21
     per, groups = _check_members(ens, specs, nsteps, pick)
     assert len(groups) == 7 and sum(g["count"] for g in groups) == 1024
     assert all(np.isfinite(g["mean"]) and g["mean"] > 0 for g in groups)
