@@ -140,7 +140,7 @@ int at_num_sides(const at_config_t *cfg, int64_t *sides);
 
 /* Create a solver on caller-owned device memory and write U^0 (Eq. "IC"; the 3D field is the product
  * of per-axis sums) into ring slot 0.
- *   ring_dev : R * n0*n1*n2 doubles (R from at_ring_slots), 32-byte aligned for the vectorised kernels (any
+ *   ring_dev : R * n0*n1*n2 doubles (R from at_ring_slots), 16-byte aligned for the vectorised kernels (any
  *              other alignment runs the per-point kernel: the same results, slower); level m
  *              lives in slot m mod (L + T), the right-hand sides of Adams-Bashforth in the slots after those.
  *   log_dev  : log_steps * sides bytes, may be NULL when log_steps == 0; receives the raw delay of
@@ -233,7 +233,7 @@ int at_destroy(at_handle_t *hd);
  *   order 4, L = 3 that is 17.6 % of the cells, so a checkpoint takes 1.7 fields instead of 5; Adams-Bashforth
  *   checkpoints also hold the ts-1 stored right-hand sides in full.
  * at_adjoint_forward: from step 0 (after at_init or at_reset), run nsteps forward steps exactly as at_step and
- *   keep the checkpoints in work_dev (caller-owned, 32-byte aligned, untouched until at_adjoint_backward).  When
+ *   keep the checkpoints in work_dev (caller-owned, 16-byte aligned, untouched until at_adjoint_backward).  When
  *   one segment covers the run (ckpt_every >= nsteps; workspace about nsteps + R fields), the steps run inside the
  *   workspace, which then holds every level, and the backward sweep recomputes nothing.  Any later at_step or
  *   at_reset discards the recorded pass.  Errors: AT_ERR_ARG, AT_ERR_STATE (not at step 0, or nsteps beyond the
@@ -270,7 +270,7 @@ int at_adjoint_backward(at_handle_t *hd, const double *lambda_dev, double *grad_
  * at_ensemble_sizes: validates the members and runs and gives the doubles of ring and bytes of delay log they
  *   need (members stored one after another; member r's ring holds its own at_ring_slots slots, its log
  *   nsteps_r x sides_r bytes).
- * at_ensemble_create: members and runs are copied; ring_dev (ring_len doubles, 32-byte aligned) and the optional
+ * at_ensemble_create: members and runs are copied; ring_dev (ring_len doubles, 16-byte aligned) and the optional
  *   log_dev (log_len bytes, NULL for no log) are borrowed.  threads per CTA is 128, 256, 512 or 1024 (0: 1024);
  *   ctas_per_sm <= 0 takes the occupancy limit.  Every member starts from Eq. "IC" (with the analytic
  *   pre-history for Adams-Bashforth).  Errors: AT_ERR_ARG (non-1D member, n[0] or the PE width not a multiple

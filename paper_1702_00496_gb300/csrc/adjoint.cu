@@ -321,8 +321,8 @@ __device__ __forceinline__ void adj_axis_taps(const StepParams &f, int ax, const
     if (j == 0) continue;
     const int ia = wrap_coord(c - j, na);
     const int64_t base = i0 + (int64_t)(ia - c) * st;
-    const double4_32a e = LdgNC::ld4(ln + base);
-    const double lr[4] = {e.x, e.y, e.z, e.w};
+    const double2 e = LdgNC::ld2(ln + base), g = LdgNC::ld2(ln + base + 2);
+    const double lr[4] = {e.x, e.y, g.x, g.y};
     const double s = f.s[ax][j + H];
     const bool cross = (SIDE == 1 && j > H - CNT) || (SIDE == 2 && j < CNT - H);
 #pragma unroll
@@ -395,7 +395,11 @@ __device__ __forceinline__ void adjoint_group(const AdjParams &a, const uint8_t 
   constexpr int W = XWin<H>::W, NW = XWin<H>::N;
   double lv[NW];
   if (x0 >= W && x0 + 4 + W <= nx) {
-    load_xwin<W, LdgNC>(ln + i0 - W, lv);
+#pragma unroll
+    for (int t = 0; t < NW; t += 2) {
+      const double2 l = LdgNC::ld2(ln + i0 - W + t);
+      lv[t] = l.x; lv[t + 1] = l.y;
+    }
   } else {
 #pragma unroll
     for (int t = 0; t < NW; ++t) lv[t] = LdgNC::ld(ln + row + wrap_coord(x0 - W + t, nx));
@@ -412,8 +416,8 @@ __device__ __forceinline__ void adjoint_group(const AdjParams &a, const uint8_t 
   int kX[4] = {-1, -1, -1, -1};
   double id[4] = {f.zero, f.zero, f.zero, f.zero};
   if (AB) {
-    const double4_32a e0 = LdgNC::ld4(lnext + i0);
-    id[0] = e0.x; id[1] = e0.y; id[2] = e0.z; id[3] = e0.w;
+    const double2 e0 = LdgNC::ld2(lnext + i0), e1 = LdgNC::ld2(lnext + i0 + 2);
+    id[0] = e0.x; id[1] = e0.y; id[2] = e1.x; id[3] = e1.y;
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -444,15 +448,21 @@ __device__ __forceinline__ void adjoint_group(const AdjParams &a, const uint8_t 
   }
   const int64_t fresh = n - a.reach;
   const int snl = (int)(n % a.Rl);
-  double *cur = a.lam + snl * N + i0;
+  double2 *cur = reinterpret_cast<double2 *>(a.lam + snl * N + i0);
   if (a.reach == 0) {
-    st4(cur, A[0], A[1], A[2], A[3]);
+    cur[0] = make_double2(A[0], A[1]);
+    cur[1] = make_double2(A[2], A[3]);
     return;
   }
-  if (fresh >= 0) st4(a.lam + slot_back(snl, a.reach, a.Rl) * N + i0, 0.0, 0.0, 0.0, 0.0);
+  if (fresh >= 0) {
+    double2 *fr = reinterpret_cast<double2 *>(a.lam + slot_back(snl, a.reach, a.Rl) * N + i0);
+    fr[0] = make_double2(0.0, 0.0);
+    fr[1] = make_double2(0.0, 0.0);
+  }
   {
-    const double4_32a p = LdCoherent::ld4(cur);
-    st4(cur, p.x + A[0], p.y + A[1], p.z + A[2], p.w + A[3]);
+    const double2 p0 = cur[0], p1 = cur[1];
+    cur[0] = make_double2(p0.x + A[0], p0.y + A[1]);
+    cur[1] = make_double2(p1.x + A[2], p1.y + A[3]);
   }
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
@@ -460,16 +470,17 @@ __device__ __forceinline__ void adjoint_group(const AdjParams &a, const uint8_t 
     if (k <= 0) continue;
     for (int m = 0; m < f.T; ++m) {
       const double wk = f.w[k][m];
-      double *o = a.lam + slot_back(snl, k + m, a.Rl) * N + i0;
-      const double4_32a p = LdCoherent::ld4(o);
-      st4(o, fma(wk, X[b][0], p.x), fma(wk, X[b][1], p.y), fma(wk, X[b][2], p.z), fma(wk, X[b][3], p.w));
+      double2 *o = reinterpret_cast<double2 *>(a.lam + slot_back(snl, k + m, a.Rl) * N + i0);
+      const double2 p0 = o[0], p1 = o[1];
+      o[0] = make_double2(fma(wk, X[b][0], p0.x), fma(wk, X[b][1], p0.y));
+      o[1] = make_double2(fma(wk, X[b][2], p1.x), fma(wk, X[b][3], p1.y));
     }
   }
 }
 
 // Backward step n, one launch, which also draws the delays of step n-1.  MODE 0: every cell by the general path
-// (shapes without groups of four).  MODE 1: cells in groups of four x points (n[0] % 4 == 0, 32-byte aligned
-// slots, read and written with 32-byte accesses); a group whose cells and neighbours all lie inside one PE and away from the domain ends takes the
+// (shapes without groups of four).  MODE 1: cells in groups of four x points (n[0] % 4 == 0, 16-byte aligned
+// slots); a group whose cells and neighbours all lie inside one PE and away from the domain ends takes the
 // straight path, the others the edge path (adjoint_group).
 #ifndef AT_ADJ_MIN_BLOCKS
 #define AT_ADJ_MIN_BLOCKS 3
@@ -527,12 +538,19 @@ __global__ void __launch_bounds__(256, AdjBounds<MODE>::min_blocks) adjoint_step
       }
       constexpr int W = XWin<H>::W, NW = XWin<H>::N;
       double lv[NW], uv[NW];
-      load_xwin<W, LdgNC>(ln + i0 - W, lv);
-      if (AL) load_xwin<W, LdgNC>(un + i0 - W, uv);
+#pragma unroll
+      for (int t = 0; t < NW; t += 2) {
+        const double2 l = LdgNC::ld2(ln + i0 - W + t);
+        lv[t] = l.x; lv[t + 1] = l.y;
+        if (AL) {
+          const double2 u = LdgNC::ld2(un + i0 - W + t);
+          uv[t] = u.x; uv[t + 1] = u.y;
+        }
+      }
       double A[4], D[4], id[4] = {f.zero, f.zero, f.zero, f.zero};
       if (AB) {
-        const double4_32a e0 = LdgNC::ld4(lnext + i0);
-        id[0] = e0.x; id[1] = e0.y; id[2] = e0.z; id[3] = e0.w;
+        const double2 e0 = LdgNC::ld2(lnext + i0), e1 = LdgNC::ld2(lnext + i0 + 2);
+        id[0] = e0.x; id[1] = e0.y; id[2] = e1.x; id[3] = e1.y;
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -553,25 +571,31 @@ __global__ void __launch_bounds__(256, AdjBounds<MODE>::min_blocks) adjoint_step
 #pragma unroll
           for (int j = -H; j <= H; ++j) {
             if (j == 0) continue;
-            const double4_32a la = LdgNC::ld4(ln + i0 - j * st);
-            double4_32a ua = make_double4_32a(0.0, 0.0, 0.0, 0.0);
-            if (AL) ua = LdgNC::ld4(un + i0 + j * st);
+            const double2 la = LdgNC::ld2(ln + i0 - j * st), lb = LdgNC::ld2(ln + i0 - j * st + 2);
+            double2 ua = make_double2(0.0, 0.0), ub = ua;
+            if (AL) { ua = LdgNC::ld2(un + i0 + j * st); ub = LdgNC::ld2(un + i0 + j * st + 2); }
             const double s = f.s[ax][j + H], qq = f.q[ax][j + H];
-            A[0] = fma(s, la.x, A[0]); A[1] = fma(s, la.y, A[1]); A[2] = fma(s, la.z, A[2]); A[3] = fma(s, la.w, A[3]);
-            if (AL) { D[0] = fma(qq, ua.x, D[0]); D[1] = fma(qq, ua.y, D[1]); D[2] = fma(qq, ua.z, D[2]); D[3] = fma(qq, ua.w, D[3]); }
+            A[0] = fma(s, la.x, A[0]); A[1] = fma(s, la.y, A[1]); A[2] = fma(s, lb.x, A[2]); A[3] = fma(s, lb.y, A[3]);
+            if (AL) { D[0] = fma(qq, ua.x, D[0]); D[1] = fma(qq, ua.y, D[1]); D[2] = fma(qq, ub.x, D[2]); D[3] = fma(qq, ub.y, D[3]); }
           }
         }
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) if (AL) galpha = fma(lv[q + W], D[q], galpha);
-      double *cur = a.lam + (n % a.Rl) * N + i0;
+      double2 *cur = reinterpret_cast<double2 *>(a.lam + (n % a.Rl) * N + i0);
       if (a.reach == 0) {
-        st4(cur, A[0], A[1], A[2], A[3]);
+        cur[0] = make_double2(A[0], A[1]);
+        cur[1] = make_double2(A[2], A[3]);
       } else {
-        const double4_32a p = LdCoherent::ld4(cur);
-        st4(cur, p.x + A[0], p.y + A[1], p.z + A[2], p.w + A[3]);
+        const double2 p0 = cur[0], p1 = cur[1];
+        cur[0] = make_double2(p0.x + A[0], p0.y + A[1]);
+        cur[1] = make_double2(p1.x + A[2], p1.y + A[3]);
         const int64_t fresh = n - a.reach;
-        if (fresh >= 0) st4(a.lam + (fresh % a.Rl) * N + i0, 0.0, 0.0, 0.0, 0.0);
+        if (fresh >= 0) {
+          double2 *fr = reinterpret_cast<double2 *>(a.lam + (fresh % a.Rl) * N + i0);
+          fr[0] = make_double2(0.0, 0.0);
+          fr[1] = make_double2(0.0, 0.0);
+        }
       }
     }
   }
@@ -741,8 +765,7 @@ void launch_alpha(const AdjParams &a, int64_t n, int nblk, bool grouped, cudaStr
 
 bool adjoint_grouped(const AdjParams &a) {
   return a.f.n[0] % 4 == 0 && (!a.f.use_pe[0] || a.f.S[0] % 4 == 0) && (a.f.dim == 1 || a.f.order != nullptr) &&
-         (reinterpret_cast<uintptr_t>(a.lam) % 32) == 0 && (reinterpret_cast<uintptr_t>(a.f.ring) % 32) == 0 &&
-         (a.mu == nullptr || (reinterpret_cast<uintptr_t>(a.mu) % 32) == 0);
+         (reinterpret_cast<uintptr_t>(a.lam) % 16) == 0 && (reinterpret_cast<uintptr_t>(a.f.ring) % 16) == 0;
 }
 
 // The straight (interior) path of the grouped kernel needs a group whose cells and stencil neighbours (the x window of W = h
@@ -868,7 +891,7 @@ extern "C" int at_adjoint_forward(at_handle_t *hd, int64_t nsteps, int64_t ckpt_
   if (hd->step != 0) return fail(AT_ERR_STATE, "at_adjoint_forward: the handle must be at step 0 (at_reset)");
   const AdjLayout L = layout(hd, nsteps, ckpt_every);
   if (work_len < L.total) return fail(AT_ERR_ARG, "at_adjoint_forward: workspace too small");
-  if (reinterpret_cast<uintptr_t>(work_dev) % 32) return fail(AT_ERR_ARG, "at_adjoint_forward: workspace not 32-byte aligned");
+  if (reinterpret_cast<uintptr_t>(work_dev) % 16) return fail(AT_ERR_ARG, "at_adjoint_forward: workspace not 16-byte aligned");
   // at_step's limits, checked before any step so a refused pass leaves the handle at step 0
   if (hd->sp.log && nsteps > hd->log_steps) return fail(AT_ERR_STATE, "at_adjoint_forward: delay log is full");
   if (nsteps > 0xFFFFFFFFll) return fail(AT_ERR_STATE, "at_adjoint_forward: step counter exceeds 32 bits");

@@ -92,14 +92,13 @@ __device__ void run_member(const StepParams &p, uint8_t *keff_sh, int64_t nsteps
     double *out = p.ring + ((n + 1) % p.R) * p.ntot;
     if (n + 1 < nsteps) atfd::draw_sides(p, n + 1, threadIdx.x, blockDim.x, keff_sh + ((n + 1) & 1) * p.nb);
     const uint8_t *keff = keff_sh + (n & 1) * p.nb;
-    const int lab = AB && p.ts > 1 ? atfd::ab_levels(p, n) : 0;
     for (int k = threadIdx.x; k < groups; k += blockDim.x)
       if (SPACE && p.scheme >= AT_AT_SPACE2)
-        atfd::group_step<1, H, atfd::LdCoherent, AB, 2>(p, keff, un, out, n, lab,
-                                                        (int)(atfd::group_1d_order(p, k) << 2), 0, 0);
+        atfd::group_step<1, H, atfd::LdCoherent, AB, 2>(p, keff, un, out, n, (int)(atfd::group_1d_order(p, k) << 2),
+                                                        0, 0);
       else
-        atfd::group_update<1, H, atfd::LdCoherent, AB>(p, keff, un, out, n, lab,
-                                                       (int)(atfd::group_1d_order(p, k) << 2), 0, 0);
+        atfd::group_update<1, H, atfd::LdCoherent, AB>(p, keff, un, out, n, (int)(atfd::group_1d_order(p, k) << 2),
+                                                       0, 0);
     __syncthreads();
   }
 }
@@ -347,8 +346,8 @@ extern "C" int at_ensemble_create(const at_config_t *members, const at_member_t 
   int rc = at_ensemble_sizes(members, runs, count, &need_ring, &need_log);
   if (rc) return rc;
   if (!out || !ring_dev || ring_len < need_ring) return fail(AT_ERR_ARG, "at_ensemble_create: ring too small");
-  if (reinterpret_cast<uintptr_t>(ring_dev) % 32)
-    return fail(AT_ERR_ARG, "at_ensemble_create: ring not 32-byte aligned (the group kernels use 32-byte accesses)");
+  if (reinterpret_cast<uintptr_t>(ring_dev) % 16)
+    return fail(AT_ERR_ARG, "at_ensemble_create: ring not 16-byte aligned (the group kernels use 16-byte accesses)");
   if (log_dev && log_len < need_log) return fail(AT_ERR_ARG, "at_ensemble_create: log too small");
   if (threads == 0) threads = 1024;
   if (threads != 128 && threads != 256 && threads != 512 && threads != 1024)

@@ -39,19 +39,18 @@ __global__ void __launch_bounds__(512) forward_group_kernel(const StepParams p, 
   const uint8_t *keff = p.keff + (n & 1) * p.nb;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nthreads = (int64_t)gridDim.x * blockDim.x;
   draw_sides(p, n + 1, tid, nthreads, p.keff + ((n + 1) & 1) * p.nb);
-  const int lab = AB ? ab_levels(p, n) : 0;
   const int gx = p.n[0] >> 2;
   const int64_t groups = (int64_t)gx * p.n[1] * p.n[2];
   for (int64_t k = tid; k < groups; k += nthreads) {
     if (DIM == 1) {
       const int64_t g = group_1d_order(p, k);
-      group_step<1, H, LdgNC, AB, KIND>(p, keff, un, out, n, lab, (int)(g << 2), 0, 0);
+      group_step<1, H, LdgNC, AB, KIND>(p, keff, un, out, n, (int)(g << 2), 0, 0);
     } else {
       const int64_t g = p.order ? (int64_t)p.order[k] : k;
       const int64_t r = g / gx;
       const int x0 = (int)(g - r * gx) << 2;
       const int z = (int)(r / p.n[1]), y = (int)(r - (int64_t)z * p.n[1]);
-      group_step<3, H, LdgNC, AB, KIND>(p, keff, un, out, n, lab, x0, y, z);
+      group_step<3, H, LdgNC, AB, KIND>(p, keff, un, out, n, x0, y, z);
     }
   }
 }
@@ -77,16 +76,13 @@ __global__ void __launch_bounds__(512) forward_point_kernel(const StepParams p, 
   const uint8_t *keff = p.keff + (n & 1) * p.nb;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nthreads = (int64_t)gridDim.x * blockDim.x;
   draw_sides(p, n + 1, tid, nthreads, p.keff + ((n + 1) & 1) * p.nb);
-  const int lab = AB ? ab_levels(p, n) : 0;
   for (int64_t i = tid; i < p.ntot; i += nthreads) {
     int c[3];
     point_coords(p, DIM, i, c);
-    double a1[1], a2[1];
-    if (AB) ab_fetch<1>(p, n, lab, i, a1, a2);
     if (DIM == 1 && KIND == 1) {
       double r[1] = {point_update_burgers<H, LdgNC>(p, keff, un, n, i)};
       const double u[1] = {un[i]};
-      if (AB) ab_combine<1>(p, n, lab, i, u, a1, a2, r);
+      if (AB) ab_combine<1>(p, n, i, u, r);
       else r[0] = u[0] + r[0];
       out[i] = r[0];
       continue;
@@ -95,7 +91,7 @@ __global__ void __launch_bounds__(512) forward_point_kernel(const StepParams p, 
                                          : point_update<DIM, H, LdgNC>(p, keff, un, n, i, c)};
     if (AB) {
       const double u[1] = {un[i]};
-      ab_combine<1>(p, n, lab, i, u, a1, a2, r);
+      ab_combine<1>(p, n, i, u, r);
     }
     out[i] = r[0];
   }
@@ -151,10 +147,10 @@ cudaError_t launch_draw_delays(const StepParams &p, int64_t n, cudaStream_t st) 
 
 namespace {
 
-// groups of four x points must not straddle a PE and must start on 32 bytes (their 32-byte loads and stores)
+// groups of four x points must not straddle a PE and must start on 16 bytes
 bool grouped_shape(const StepParams &p, const void *base) {
-  return p.n[0] % 4 == 0 && (!p.use_pe[0] || p.S[0] % 4 == 0) && (reinterpret_cast<uintptr_t>(base) % 32) == 0 &&
-         (p.frhs == nullptr || (reinterpret_cast<uintptr_t>(p.frhs) % 32) == 0);
+  return p.n[0] % 4 == 0 && (!p.use_pe[0] || p.S[0] % 4 == 0) && (reinterpret_cast<uintptr_t>(base) % 16) == 0 &&
+         (p.frhs == nullptr || (reinterpret_cast<uintptr_t>(p.frhs) % 16) == 0);
 }
 
 template <int DIM, int H, bool AB>
@@ -213,7 +209,7 @@ cudaError_t launch_forward_step(const StepParams &p, int64_t n, const int64_t *n
 cudaError_t launch_sync_rhs(const StepParams &p, const double *u, double *out, cudaStream_t st) {
   StepParams q = p;
   q.use_pe[0] = q.use_pe[1] = q.use_pe[2] = 0;  // no PE boundary: central differences at every point
-  const bool grouped = grouped_shape(q, u) && (reinterpret_cast<uintptr_t>(out) % 32) == 0;
+  const bool grouped = grouped_shape(q, u) && (reinterpret_cast<uintptr_t>(out) % 16) == 0;
   const int64_t work = grouped ? q.ntot / 4 : q.ntot;
   const int64_t b = (work + 255) / 256, cap = (int64_t)sm_count() * 8;
   const int blocks = (int)(b < cap ? b : cap);

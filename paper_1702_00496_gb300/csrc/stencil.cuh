@@ -3,8 +3,7 @@
 //
 // A thread updates a group of four consecutive x points (x0 a multiple of 4) of one (y, z) row.  It loads
 // the level-n values its merged stencil needs -- the x window x0-W .. x0+3+W (W = h rounded up to even, so the
-// window starts on 16 bytes; its middle is read with 32-byte loads) and, in 3D, the four values of rows y +- j and
-// z +- j (one 32-byte load each) -- and replaces every value
+// window starts on 16 bytes) and, in 3D, the four values of rows y +- j and z +- j -- and replaces every value
 // that lies outside the group's PE (a buffer point, Sec. 2) by the halo value its PE side sees:
 //     u~ = sum_{m<T} w_m(k) U^{n-k-m}     (k: that side's effective delay for step n; k = 0 keeps U^n)
 // Groups never straddle a PE (PE widths are multiples of 4 on these paths), so each loaded value is either
@@ -25,47 +24,15 @@ namespace atfd {
 
 // Load policies.  LdgNC reads through the non-coherent read-only path: legal in the per-step kernels, whose
 // read slots are never written during the launch.  LdCoherent is a plain load, for kernels that read back what
-// they wrote earlier in the same launch (after a barrier).  ld4 reads four doubles with one 32-byte access (the
-// address must be 32-byte aligned): a warp's 32 lanes then read 1 KB of consecutive cells in 32 whole sectors,
-// where two 16-byte accesses per lane touch every sector twice, half of it each time.
+// they wrote earlier in the same launch (after a barrier).
 struct LdgNC {
   static __device__ __forceinline__ double ld(const double *p) { return __ldg(p); }
   static __device__ __forceinline__ double2 ld2(const double *p) { return __ldg(reinterpret_cast<const double2 *>(p)); }
-  static __device__ __forceinline__ double4_32a ld4(const double *p) {
-    double4_32a v;
-    asm("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];" : "=d"(v.x), "=d"(v.y), "=d"(v.z), "=d"(v.w) : "l"(p));
-    return v;
-  }
 };
 struct LdCoherent {
   static __device__ __forceinline__ double ld(const double *p) { return *p; }
   static __device__ __forceinline__ double2 ld2(const double *p) { return *reinterpret_cast<const double2 *>(p); }
-  static __device__ __forceinline__ double4_32a ld4(const double *p) { return *reinterpret_cast<const double4_32a *>(p); }
 };
-
-// Four consecutive doubles with one 32-byte store (p 32-byte aligned).
-__device__ __forceinline__ void st4(double *p, double a, double b, double c, double d) {
-  *reinterpret_cast<double4_32a *>(p) = make_double4_32a(a, b, c, d);
-}
-
-// The NW = 4 + 2W values of the x window x0-W .. x0+3+W (W = 2 or 4) starting at `src` = the window's first cell,
-// with x0 32-byte aligned: 32-byte loads where the window allows, 16-byte loads at the ends when W = 2.
-template <int W, class LD>
-__device__ __forceinline__ void load_xwin(const double *src, double *v) {
-  static_assert(W == 2 || W == 4, "x window half-width must be 2 or 4");
-  if constexpr (W == 2) {
-    const double2 a = LD::ld2(src);
-    const double4_32a b = LD::ld4(src + 2);
-    const double2 c = LD::ld2(src + 6);
-    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = b.z; v[5] = b.w; v[6] = c.x; v[7] = c.y;
-  } else {
-#pragma unroll
-    for (int t = 0; t < 12; t += 4) {
-      const double4_32a b = LD::ld4(src + t);
-      v[t] = b.x; v[t + 1] = b.y; v[t + 2] = b.z; v[t + 3] = b.w;
-    }
-  }
-}
 
 __device__ __forceinline__ int wrap_coord(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
@@ -132,7 +99,7 @@ struct XWin {
 };
 
 // The merged stencil of the four points x0..x0+3 of row (y, z) into r[4] (and their level-n values into uc[4]);
-// requires n[0] % 4 == 0 and a 32-byte aligned slot.  keff: effective delays of step n.  ALPHA = true evaluates
+// requires n[0] % 4 == 0 and a 16-byte aligned slot.  keff: effective delays of step n.  ALPHA = true evaluates
 // the alpha derivative of the step instead (coefficients q0, q: dt times the AT second derivative).
 template <int DIM, int H, class LD, bool ALPHA>
 __device__ __forceinline__ void group_eval(const StepParams &p, const uint8_t *__restrict__ keff,
@@ -152,7 +119,11 @@ __device__ __forceinline__ void group_eval(const StepParams &p, const uint8_t *_
   // x window: cells x0-W .. x0+3+W of the row
   double v[NW];
   if (x0 >= W && x0 + 4 + W <= nx) {
-    load_xwin<W, LD>(un + i0 - W, v);
+#pragma unroll
+    for (int t = 0; t < NW; t += 2) {
+      const double2 a = LD::ld2(un + i0 - W + t);
+      v[t] = a.x; v[t + 1] = a.y;
+    }
   } else {
 #pragma unroll
     for (int t = 0; t < NW; ++t) v[t] = LD::ld(un + row + wrap_coord(x0 - W + t, nx));
@@ -199,8 +170,8 @@ __device__ __forceinline__ void group_eval(const StepParams &p, const uint8_t *_
 #pragma unroll
           for (int q = 0; q < 4; ++q) w[q] = halo_value<LD>(p, base + q, sn, k);
         } else {
-          const double4_32a e = LD::ld4(un + base);
-          w[0] = e.x; w[1] = e.y; w[2] = e.z; w[3] = e.w;
+          const double2 e = LD::ld2(un + base), f = LD::ld2(un + base + 2);
+          w[0] = e.x; w[1] = e.y; w[2] = f.x; w[3] = f.y;
         }
         const double s = ALPHA ? p.q[a][j + H] : p.s[a][j + H];
 #pragma unroll
@@ -210,50 +181,44 @@ __device__ __forceinline__ void group_eval(const StepParams &p, const uint8_t *_
   }
 }
 
-// NP (1 or 4) consecutive stored right-hand sides (32-byte aligned for NP = 4).
+// NP consecutive stored right-hand sides (16-byte aligned for NP > 1).
 template <int NP>
 __device__ __forceinline__ void ab_load(const double *src, double a[NP]) {
-  static_assert(NP == 1 || NP == 4, "one point or a group of four");
   if constexpr (NP == 1) {
     a[0] = src[0];
   } else {
-    const double4_32a v = LdCoherent::ld4(src);
-    a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w;
-  }
-}
-
-// Levels of dt f stored for step n, at most ts: the Adams-Bashforth order of step n (read once per launch).
-__device__ __forceinline__ int ab_levels(const StepParams &p, int64_t n) {
-  const int64_t stored = n - *p.ab_first + 1;
-  return stored < p.ts ? (int)stored : p.ts;
-}
-
-// The stored right-hand sides step n reads at the NP consecutive points from i (32-byte aligned for NP = 4), with
-// l = ab_levels(p, n): dt f^{n-1} into a1 when l > 1, dt f^{n-2} into a2 when l > 2.  Loaded before the stencil,
-// so their latency overlaps its FMAs.
-template <int NP>
-__device__ __forceinline__ void ab_fetch(const StepParams &p, int64_t n, int l, int64_t i, double a1[NP],
-                                         double a2[NP]) {
-  const bool two = p.ts == 3;  // two stored slots, else one
-  if (l > 1) ab_load<NP>(p.frhs + (two ? ((n - 1) & 1) : 0) * p.ntot + i, a1);
-  if (l > 2) ab_load<NP>(p.frhs + (n & 1) * p.ntot + i, a2);
-}
-
-// Adams-Bashforth combination of the NP points from i: r holds dt f^n and becomes
-// U^{n+1} = U^n + sum_{m<l} beta_m dt f^{n-m}, formed as a chain of l FMAs onto U^n (a1, a2 from ab_fetch).  Then
-// dt f^n takes the slot of the oldest right-hand side (for AB2 the slot a1 came from), which only this thread
-// reads: the store comes after the loaded values have been used, so it never waits on a load of its own address.
-template <int NP>
-__device__ __forceinline__ void ab_combine(const StepParams &p, int64_t n, int l, int64_t i, const double u[NP],
-                                           const double a1[NP], const double a2[NP], double r[NP]) {
-  const double *beta = p.beta[l - 1];
-  double *f_now = p.frhs + (p.ts == 3 ? (n & 1) : 0) * p.ntot + i;  // dt f^{n-2} (AB3) or dt f^{n-1} (AB2)
-  double f[NP];
 #pragma unroll
-  for (int q = 0; q < NP; ++q) {
-    f[q] = r[q];
-    r[q] = fma(beta[0], r[q], u[q]);
+    for (int q = 0; q < NP; q += 2) {
+      const double2 v = *reinterpret_cast<const double2 *>(src + q);
+      a[q] = v.x; a[q + 1] = v.y;
+    }
   }
+}
+
+// Adams-Bashforth combination of NP consecutive points starting at i (16-byte aligned for NP = 4): r holds
+// dt f^n and becomes U^{n+1} = U^n + sum_{m<l} beta_m dt f^{n-m} (l = levels stored so far, at most ts), formed
+// as a chain of l FMAs onto U^n; dt f^n takes the slot of the oldest right-hand side, which only this thread
+// reads, after the read.
+template <int NP>
+__device__ __forceinline__ void ab_combine(const StepParams &p, int64_t n, int64_t i, const double u[NP],
+                                           double r[NP]) {
+  const int64_t stored = n - *p.ab_first + 1;
+  const int l = stored < p.ts ? (int)stored : p.ts;
+  const double *beta = p.beta[l - 1];
+  const bool two = p.ts == 3;  // two stored slots, else one
+  double *f_now = p.frhs + (two ? (n & 1) : 0) * p.ntot + i;          // dt f^{n-2} (AB3) or dt f^{n-1} (AB2)
+  const double *f_1 = p.frhs + (two ? ((n - 1) & 1) : 0) * p.ntot + i;  // dt f^{n-1}
+  double a1[NP], a2[NP];
+  if (l > 1) ab_load<NP>(f_1, a1);
+  if (l > 2) ab_load<NP>(f_now, a2);
+  if constexpr (NP == 1) {
+    f_now[0] = r[0];
+  } else {
+#pragma unroll
+    for (int q = 0; q < NP; q += 2) *reinterpret_cast<double2 *>(f_now + q) = make_double2(r[q], r[q + 1]);
+  }
+#pragma unroll
+  for (int q = 0; q < NP; ++q) r[q] = fma(beta[0], r[q], u[q]);
   if (l > 1) {
 #pragma unroll
     for (int q = 0; q < NP; ++q) r[q] = fma(beta[1], a1[q], r[q]);
@@ -262,25 +227,19 @@ __device__ __forceinline__ void ab_combine(const StepParams &p, int64_t n, int l
 #pragma unroll
     for (int q = 0; q < NP; ++q) r[q] = fma(beta[2], a2[q], r[q]);
   }
-  if constexpr (NP == 1) {
-    f_now[0] = f[0];
-  } else {
-    st4(f_now, f[0], f[1], f[2], f[3]);
-  }
 }
 
-// Update the four points x0..x0+3 of row (y, z) (the forward step; AB: Adams-Bashforth with lab = ab_levels(p, n)
-// stored levels, else forward Euler).
+// Update the four points x0..x0+3 of row (y, z) (the forward step; AB: Adams-Bashforth, else forward Euler).
 template <int DIM, int H, class LD, bool AB = false>
 __device__ __forceinline__ void group_update(const StepParams &p, const uint8_t *__restrict__ keff,
                                              const double *__restrict__ un, double *__restrict__ out, int64_t n,
-                                             int lab, int x0, int y, int z) {
-  double r[4], uc[4], a1[4], a2[4];
-  const int64_t i0 = (DIM == 3 ? ((int64_t)z * p.n[1] + y) * p.n[0] : 0) + x0;
-  if (AB) ab_fetch<4>(p, n, lab, i0, a1, a2);
+                                             int x0, int y, int z) {
+  double r[4], uc[4];
   group_eval<DIM, H, LD, false>(p, keff, un, n, x0, y, z, r, uc);
-  if (AB) ab_combine<4>(p, n, lab, i0, uc, a1, a2, r);
-  st4(out + i0, r[0], r[1], r[2], r[3]);
+  const int64_t i0 = (DIM == 3 ? ((int64_t)z * p.n[1] + y) * p.n[0] : 0) + x0;
+  if (AB) ab_combine<4>(p, n, i0, uc, r);
+  reinterpret_cast<double2 *>(out + i0)[0] = make_double2(r[0], r[1]);
+  reinterpret_cast<double2 *>(out + i0)[1] = make_double2(r[2], r[3]);
 }
 
 // One point of any shape (the fallback for point counts that are not a multiple of 4), same arithmetic.
@@ -327,7 +286,11 @@ __device__ __forceinline__ void group_eval_burgers(const StepParams &p, const ui
   const int pos0 = x0 - pidx[0] * p.S[0];
   double v[NW];
   if (x0 >= W && x0 + 4 + W <= nx) {
-    load_xwin<W, LD>(un + x0 - W, v);
+#pragma unroll
+    for (int t = 0; t < NW; t += 2) {
+      const double2 a = LD::ld2(un + x0 - W + t);
+      v[t] = a.x; v[t + 1] = a.y;
+    }
   } else {
 #pragma unroll
     for (int t = 0; t < NW; ++t) v[t] = LD::ld(un + wrap_coord(x0 - W + t, nx));
@@ -453,18 +416,18 @@ __device__ __forceinline__ bool group_at_space_edge(const StepParams &p, int x0,
 template <int DIM, int H, class LD, bool AB, int KIND = 0>
 __device__ __forceinline__ void group_step(const StepParams &p, const uint8_t *__restrict__ keff,
                                            const double *__restrict__ un, double *__restrict__ out, int64_t n,
-                                           int lab, int x0, int y, int z) {
+                                           int x0, int y, int z) {
   if (DIM == 1 && KIND == 1) {
-    double r[4], uc[4], a1[4], a2[4];
-    if (AB) ab_fetch<4>(p, n, lab, x0, a1, a2);
+    double r[4], uc[4];
     group_eval_burgers<H, LD>(p, keff, un, n, x0, r, uc);
     if (AB) {
-      ab_combine<4>(p, n, lab, x0, uc, a1, a2, r);
+      ab_combine<4>(p, n, x0, uc, r);
     } else {
 #pragma unroll
       for (int q = 0; q < 4; ++q) r[q] = uc[q] + r[q];
     }
-    st4(out + x0, r[0], r[1], r[2], r[3]);
+    reinterpret_cast<double2 *>(out + x0)[0] = make_double2(r[0], r[1]);
+    reinterpret_cast<double2 *>(out + x0)[1] = make_double2(r[2], r[3]);
     return;
   }
   if (KIND == 2 && H == 1 && !AB && group_at_space_edge<DIM>(p, x0, y, z)) {
@@ -476,10 +439,11 @@ __device__ __forceinline__ void group_step(const StepParams &p, const uint8_t *_
       c[0] = x0 + q;
       r[q] = point_update_space<DIM, LD>(p, keff, un, n, i0 + q, c);
     }
-    st4(out + i0, r[0], r[1], r[2], r[3]);
+    reinterpret_cast<double2 *>(out + i0)[0] = make_double2(r[0], r[1]);
+    reinterpret_cast<double2 *>(out + i0)[1] = make_double2(r[2], r[3]);
     return;
   }
-  group_update<DIM, H, LD, AB>(p, keff, un, out, n, lab, x0, y, z);
+  group_update<DIM, H, LD, AB>(p, keff, un, out, n, x0, y, z);
 }
 
 }  // namespace atfd
