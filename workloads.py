@@ -10,6 +10,7 @@ themselves, not stand-ins for a dataset):
   1d_n256      1D, N=256,  8 PEs,    CD2 + (1,2,2)b/(2,2,2)b, L=3, 2000 steps
   1d_n16m      1D, N=2^24, 4096 PEs, CD4 + (1,4,2)/(2,4,2),   L=4, 1000 steps
   3d_512_o2/4  3D, 512^3, 8x8x8 PEs,  order 2 or 4, L=3, dt = dx^2, 500 steps
+  3d_256_o2/4  the same PE shape (64^3) at 256^3 in 4x4x4 PEs (profiling captures that fit a few GB)
   ensemble     1024 1D realizations, N_r in {2^10..2^16}, P_r=N_r/64, L_r in {2,3,4}, 5000 steps
   adjoint_256  3D 256^3, 4x4x4 PEs, order 4, L=3, 2000 steps
   1d_n16m_case2  the paper's Case 2 scaled to N=2^24, 4096 PEs: CD2 + (2,1,2), Euler, diffusion, L=3, 1000 steps
@@ -86,6 +87,8 @@ def workload(name: str, scheme: int = AT):
         return wl_3d(512, 8, 2, 3, 500, 3, scheme)
     if name == "3d_512_o4":
         return wl_3d(512, 8, 4, 3, 500, 3, scheme)
+    if name == "3d_256_o2":
+        return wl_3d(256, 4, 2, 3, 500, 3, scheme)
     if name == "3d_256_o4":
         return wl_3d(256, 4, 4, 3, 500, 3, scheme)
     if name == "adjoint_256":
