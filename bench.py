@@ -51,6 +51,11 @@ MEASURED_TRAFFIC = {
 }
 
 
+# The ensemble kernel's DRAM read + write per point update: ncu on a 100-step launch of the 1024 members (21.16 GB
+# read, 13.72 GB written, 1.794e9 updates); the full 5000-step launch scales with its updates.
+ENSEMBLE_DRAM_BYTES_PER_UPDATE = (21.16e9 + 13.72e9) / 1.7944576e9
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -552,12 +557,15 @@ def measure_ensemble(args, local, specs, steps_list, T, groups_in, twins, warmup
                       "time_steps": T if T is not None else [min(steps_list), max(steps_list)],
                       "total_points": sum(s["n"][0] for s in specs), "point_updates": updates,
                       "launch": {"threads": threads, "ctas_per_sm": ctas},
-                      "l2": "not flushed: each member's ring (at most 3.5 MiB) stays on chip while its CTA runs"},
+                      "l2": "not flushed: the rings of the members running at once (152, up to 3.5 MiB each) "
+                            "exceed the L2, so every step streams them from HBM"},
            "one_at_a_time_ms": one, "speedup_vs_one_at_a_time": (one / ms) if one else None,
            "one_at_a_time_clocks": one_clocks, "groups": groups, "clocks": clocks, "gpu_launches": steps * 4}
     if T is not None:
         rec["roofline"] = roofline_alu(flop, 16 * updates, ms, 5 * updates, "ensemble_kernel (whole graph launch)",
-                                       local, clocks)
+                                       local, clocks, ENSEMBLE_DRAM_BYTES_PER_UPDATE * updates)
+        rec["roofline"]["traffic_note"] = ("DRAM read + write per update from one ncu capture of a 100-step launch of "
+                                           "the same members, scaled to this launch's updates")
     return rec
 
 
