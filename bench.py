@@ -48,6 +48,14 @@ MEASURED_TRAFFIC = {
     ("1d_n16m_case4", "forward_group_kernel<1,2,true>"): 271.91e6 + 209.17e6,
     ("1d_n16m_case5", "forward_group_kernel<1,3,true>"): 409.85e6 + 221.76e6,
     ("1d_n16m_case6", "forward_group_kernel<1,2,true>"): 271.83e6 + 209.14e6,
+    # 3D: captured at 256^3 (the same 64^3 PEs; a 512^3 ring is 5-6 GB) over launches 5 and 6 of a 10-step run,
+    # scaled to 512^3 by the 8x points
+    ("3d_512_o2", "forward_group_kernel<3,1,false>"): 8 * (370.01e6 + 116.13e6),
+    ("3d_512_o4", "forward_group_kernel<3,2,false>"): 8 * (475.21e6 + 122.36e6),
+}
+TRAFFIC_NOTES = {
+    "3d_512_o2": "DRAM read + write per launch from ncu at 256^3 in 4^3 PEs of 64^3, scaled by points to 512^3",
+    "3d_512_o4": "DRAM read + write per launch from ncu at 256^3 in 4^3 PEs of 64^3, scaled by points to 512^3",
 }
 
 
@@ -467,6 +475,8 @@ def measure_forward(spec, T, args, local, warmup, steps, world=1, e2e=False, flu
     out["roofline"] = roofline_alu(flops_per_update(spec) * ntot, bytes_per_update(spec) * ntot, kern_ms,
                                    fp64_ops_per_update(spec) * ntot, kname, local, clocks,
                                    MEASURED_TRAFFIC.get((workload, kname)), dgemm)
+    if workload in TRAFFIC_NOTES:
+        out["roofline"]["traffic_note"] = TRAFFIC_NOTES[workload]
     out["gpu_launches"] = steps * launches_per_run(spec, T)
     solver.close()
     del flush
@@ -632,6 +642,7 @@ def run_ensemble(args, rank: int, world: int, local: int):
 
 # --------------------------------------------------------------------------------------------- adjoint
 ADJ_FLOP_PER_CELL = 54  # 3D order 4, transposed step with the alpha term: 13 + 13 + 1 FMAs per cell
+ADJ_DRAM_BYTES_PER_LAUNCH = 1.67e9 + 0.32e9  # ncu, one backward step with the alpha term at 256^3
 
 
 def measure_adjoint(args, local, T, every, warmup, steps, rank=0, world=1, forward=True):
@@ -753,7 +764,9 @@ def adjoint_record(args, local, T, warmup, steps) -> dict:
                            "u0_only_forward_ratio": rs["adjoint_u0_only_ms"] / f_ms, "clocks": rs["clocks"]}
         rec["roofline"] = roofline_alu(ADJ_FLOP_PER_CELL * ntot, 8 * 8 * ntot, rs["backward_ms"] / T, 27 * ntot,
                                        "adjoint_step_kernel (transposed step with the alpha term, every level "
-                                       "resident)", local, rs["clocks"])
+                                       "resident)", local, rs["clocks"], ADJ_DRAM_BYTES_PER_LAUNCH)
+        rec["roofline"]["traffic_note"] = ("DRAM read + write of one backward step at 256^3 from one ncu capture "
+                                           "(1.67 GB read, 0.32 GB written)")
     else:
         rec["resident"] = {"skipped": f"needs {need / 1e9:.0f} GB free, {free / 1e9:.0f} GB free"}
         rec["roofline"] = None
