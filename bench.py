@@ -191,8 +191,8 @@ def bytes_per_update(spec) -> int:
 def launches_per_run(spec, T: int) -> int:
     """Kernels of this library one timed run launches: the reset (initial field, Adams-Bashforth pre-history and
     its history counter, the first delay draw), T forward steps (one counter update before the captured graphs,
-    each 50-step graph holding 50 step kernels and a counter kernel; the remainder launched one by one) and the
-    error statistics."""
+    each 50-step graph holding 50 step kernels -- a K-step block is K-1 zone launches and one block launch -- and a
+    counter kernel; the remainder launched one by one) and the error statistics."""
     dim, ts = spec["dim"], time_levels(spec)
     wave = 1 if dim == 1 else 2
     if spec.get("burgers", 0):  # no analytic pre-history: the history counter only
@@ -390,6 +390,8 @@ def measure_forward(spec, T, args, local, warmup, steps, world=1, e2e=False, flu
         solver.reset()
     else:
         launch = autotune.tune_forward(solver, spec, use_cache=not args.retune)
+    from paper_1702_00496_gb300 import at_set_fusion
+    kblock = at_set_fusion(solver.h, args.block_steps)  # 1D Euler: K-step blocks where the shape admits them
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float64, device=f"cuda:{local}") if flush_l2 else None
     kern_ev = []
     burgers = bool(spec.get("burgers", 0))
@@ -437,7 +439,7 @@ def measure_forward(spec, T, args, local, warmup, steps, world=1, e2e=False, flu
     kern_ms = sum(a.elapsed_time(b) for a, b in kern_ev) / (steps * T)
     ms = max_over_ranks(ms, world, f"cuda:{local}")
     out = {"value": aggregate_rate(ntot * T, world, ms / 1e3), "ms_per_step": ms, "launch": launch,
-           "clocks": clocks, "last": last, "ntot": ntot, "T": T}
+           "clocks": clocks, "last": last, "ntot": ntot, "T": T, "block_steps": kblock}
 
     if e2e:
         # end to end through the public API: pinned host field in, final field and statistics out
@@ -472,9 +474,21 @@ def measure_forward(spec, T, args, local, warmup, steps, world=1, e2e=False, flu
                       "h2d_bytes_per_step": 8 * ntot, "d2h_bytes_per_step": 8 * ntot + 8 * 9}
 
     kname = f"forward_group_kernel<{spec['dim']},{spec['order'] // 2},{'true' if time_levels(spec) > 1 else 'false'}>"
+    ops = fp64_ops_per_update(spec)
+    if kblock > 1:
+        # blocks of K steps: 2 h K + 1 FP64 operations per point and block away from PE boundaries
+        kname = (f"forward_block_kernel<{spec['order'] // 2},{kblock}> + forward_zone_kernel<{spec['order'] // 2}> "
+                 f"(blocks of {kblock} steps)")
+        ops = (spec["order"] * kblock + 1) / kblock
     out["roofline"] = roofline_alu(flops_per_update(spec) * ntot, bytes_per_update(spec) * ntot, kern_ms,
-                                   fp64_ops_per_update(spec) * ntot, kname, local, clocks,
+                                   ops * ntot, kname, local, clocks,
                                    MEASURED_TRAFFIC.get((workload, kname)), dgemm)
+    out["roofline"]["fp64_ops_per_update_executed"] = ops
+    if kblock > 1:
+        out["roofline"]["note"] = ("achieved counts the single step's algorithmic flop per update (1 multiply and "
+                                   "2 h FMAs); blocks of K steps execute 2 h K + 1 FP64 operations per point and "
+                                   "block away from PE boundaries (fp64_ops_per_update_executed), so the FP64 "
+                                   "lanes per clock use that count")
     if workload in TRAFFIC_NOTES:
         out["roofline"]["traffic_note"] = TRAFFIC_NOTES[workload]
     out["gpu_launches"] = steps * launches_per_run(spec, T)
@@ -491,7 +505,8 @@ def forward_record(name, spec, T, args, local, warmup, steps, cpu_steps, note=""
     rec = {"metric": METRIC, "value": r["value"], "unit": "updates/s", "ms_per_step": r["ms_per_step"],
            "steps": steps, "warmup": warmup,
            "config": {"workload": name, "points": ntot, "pes": spec["pe"], "order": spec["order"], "L": spec["L"],
-                      "time_steps_per_step": T, "launch": {"threads": r["launch"][0], "blocks_per_sm": r["launch"][1]},
+                      "time_steps_per_step": T, "block_steps": r["block_steps"],
+                      "launch": {"threads": r["launch"][0], "blocks_per_sm": r["launch"][1]},
                       "l2": ("inputs larger than L2 (ring of " + f"{8 * ntot * (spec['L'] + spec['order'] // 2 + 1) / 2**30:.1f} GiB)"
                              if 8 * ntot > 256 * 2**20 else "on-chip: the whole ring fits in L2")},
            "roofline": r["roofline"], "clocks": r["clocks"], "cpu_baseline": cpu,
@@ -871,6 +886,8 @@ def main():
     ap.add_argument("--skip-one-at-a-time", action="store_true")
     ap.add_argument("--retune", action="store_true", help="ignore the autotuner cache")
     ap.add_argument("--launch", default="", help="forward step: fixed launch shape THREADS,BLOCKS_PER_SM (no tuning)")
+    ap.add_argument("--block-steps", type=int, default=4,
+                    help="1D forward Euler: steps per block of at_step (at_set_fusion; 1 = single steps)")
     ap.add_argument("--adjoint-every", type=int, default=0,
                     help="adjoint: checkpoint interval (0: sqrt(T); >= T: every level resident, no recompute)")
     args = ap.parse_args()
@@ -917,6 +934,7 @@ def main():
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": args.workload, "points": ntot, "pes": spec["pe"], "order": spec["order"],
                            "L": spec["L"], "time_levels": time_levels(spec), "time_steps_per_step": T,
+                           "block_steps": r["block_steps"],
                            "l2": "flushed (512 MiB write) each step",
                            "replicas": world, "launch": {"threads": launch[0], "blocks_per_sm": launch[1]}},
                 "e2e": r["e2e"], "roofline": r["roofline"], "cpu_baseline": cpu, "clocks": r["clocks"],

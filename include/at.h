@@ -152,9 +152,24 @@ int at_init(const at_config_t *cfg, double *ring_dev, int64_t ring_len, uint8_t 
 
 /* Advance nsteps steps (the hot path; forward Euler or Adams-Bashforth per cfg->tsteps).  Each step draws the delays of every PE side,
  * extrapolates the halo each side reads from the delayed ring slots, and applies the fused stencil.
+ * 1D forward-Euler problems with the central or time-expanded rows advance in blocks of K steps where the shape
+ * allows it (at_set_fusion): inside a PE, away from its boundaries, K steps of the constant interior stencil are
+ * one stencil of half-width h K (the K-fold composition of its taps; exact in exact arithmetic, the rounding of
+ * each cell differs), and the cells near PE boundaries, which read delayed halo values, are stepped one step at a
+ * time; the delays, the delay log and the levels a later step reads at delayed levels are those of single steps.
+ * Blocks start at the first step of each call (and of each 50-step graph inside it), so the same steps split
+ * into other calls give results equal up to rounding, not bit for bit.
  * Enqueued on the handle's stream; returns without waiting.  Errors: AT_ERR_ARG, AT_ERR_STATE (the
  * delay log would overflow), AT_ERR_CUDA. */
 int at_step(at_handle_t *hd, int64_t nsteps);
+
+/* Block length of at_step for the following calls: the largest K <= k (1..4) the problem admits -- 1D, forward
+ * Euler, AT_SYNC / AT_ASYNC_STD / AT_AT, not Burgers, n0 and the PE width multiples of 4, ring 16-byte aligned,
+ * more ring slots than K, and PEs wide enough that the zones stepped one step at a time (under 10 h + 16 cells
+ * around each boundary for K = 4) do not meet -- written to *k_used (1: single steps).  at_init picks the largest
+ * admissible K <= 4.  k = 1 restores single steps.  Waits for the stream and drops the captured step graph.
+ * Errors: AT_ERR_ARG (k outside 1..4), AT_ERR_CUDA. */
+int at_set_fusion(at_handle_t *hd, int32_t k, int32_t *k_used);
 
 /* Restart at step 0: write U^0 into ring slot 0 -- Eq. "IC" when u0_dev is NULL, else a copy of the
  * caller's field u0_dev (n0*n1*n2 doubles, device) -- and rewind the step counter.  The delay process
@@ -232,8 +247,8 @@ int at_destroy(at_handle_t *hd);
  *   in space): the only cells a step reads at delayed levels (Eq. "general_deriv_async").  At 256^3 in 4^3 PEs,
  *   order 4, L = 3 that is 17.6 % of the cells, so a checkpoint takes 1.7 fields instead of 5; Adams-Bashforth
  *   checkpoints also hold the ts-1 stored right-hand sides in full.
- * at_adjoint_forward: from step 0 (after at_init or at_reset), run nsteps forward steps exactly as at_step and
- *   keep the checkpoints in work_dev (caller-owned, 16-byte aligned, untouched until at_adjoint_backward).  When
+ * at_adjoint_forward: from step 0 (after at_init or at_reset), run nsteps forward steps one at a time (as at_step
+ *   does with at_set_fusion(hd, 1, ...)) and keep the checkpoints in work_dev (caller-owned, 16-byte aligned, untouched until at_adjoint_backward).  When
  *   one segment covers the run (ckpt_every >= nsteps; workspace about nsteps + R fields), the steps run inside the
  *   workspace, which then holds every level, and the backward sweep recomputes nothing.  Any later at_step or
  *   at_reset discards the recorded pass.  Errors: AT_ERR_ARG, AT_ERR_STATE (not at step 0, or nsteps beyond the

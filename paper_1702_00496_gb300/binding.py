@@ -21,7 +21,7 @@ AT_SYNC, AT_ASYNC_STD, AT_AT, AT_AT_SPACE2, AT_AT_SPACE1 = 0, 1, 2, 3, 4
 # every entry point include/at.h declares (checked by the CPU test of the boundary)
 EXPORTS = (
     "at_coeffs", "at_stencil_taps", "at_solve_stencil", "at_delay", "at_ring_slots", "at_num_sides",
-    "at_init", "at_step", "at_reset", "at_set_launch", "at_sync", "at_state", "at_error_stats", "at_destroy", "at_last_error",
+    "at_init", "at_step", "at_reset", "at_set_launch", "at_set_fusion", "at_sync", "at_state", "at_error_stats", "at_destroy", "at_last_error",
     "at_error_stats_noalloc",
     "at_adjoint_workspace", "at_adjoint_forward", "at_adjoint_backward",
     "at_ensemble_sizes", "at_ensemble_create", "at_ensemble_run", "at_ensemble_stats", "at_ensemble_destroy",
@@ -100,6 +100,7 @@ def load(build_if_missing: bool = True):
     L.at_sync.argtypes = [vp]
     L.at_reset.argtypes = [vp, vp]
     L.at_set_launch.argtypes = [vp, i32, i32]
+    L.at_set_fusion.argtypes = [vp, i32, C.POINTER(i32)]
     L.at_state.argtypes = [vp, C.POINTER(i64), C.POINTER(vp)]
     L.at_error_stats.argtypes = [vp, C.POINTER(at_stats_t)]
     L.at_error_stats_ref.argtypes = [vp, vp, i32, C.POINTER(at_stats_t)]
@@ -239,6 +240,13 @@ def at_reset(h, u0=None) -> None:
 
 def at_set_launch(h, threads: int, blocks_per_sm: int) -> None:
     _check(load().at_set_launch(h, int(threads), int(blocks_per_sm)), "at_set_launch")
+
+
+def at_set_fusion(h, k: int) -> int:
+    """Block length of at_step: the largest admissible K <= k (1 = single steps); returns the K in use."""
+    used = C.c_int32()
+    _check(load().at_set_fusion(h, int(k), C.byref(used)), "at_set_fusion")
+    return used.value
 
 
 def at_sync(h) -> None:

@@ -933,9 +933,13 @@ extern "C" int at_adjoint_forward(at_handle_t *hd, int64_t nsteps, int64_t ckpt_
     for (int64_t m = 0; m + 1 < hd->sp.ts && e == cudaSuccess; ++m)  // the stored right-hand sides, slot by slot
       e = copy_field(ck + L.ck_rhs + m * up32(N), hd->sp.frhs + m * N, N, hd->stream);
     if (e != cudaSuccess) return cuda_fail(e, "at_adjoint_forward: checkpoint");
+    // single steps (no K-step blocks): the recompute of the backward sweep repeats exactly these launches
     const int64_t todo = (n0 + L.s <= nsteps) ? L.s : nsteps - n0;
-    int rc = at_step(hd, todo);
-    if (rc) return rc;
+    for (int64_t t = 0; t < todo; ++t) {
+      cudaError_t e = launch_forward_step(hd->sp, hd->step, nullptr, hd->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "at_adjoint_forward: step");
+      hd->step += 1;
+    }
   }
   hd->adj_nsteps = nsteps;
   hd->adj_every = L.s;

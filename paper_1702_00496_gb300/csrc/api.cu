@@ -330,6 +330,7 @@ extern "C" int at_init(const at_config_t *cfg, double *ring_dev, int64_t ring_le
   hd->d_tables = hd->d_result + 16;
   p.status = nullptr;
   p.ab_first = hd->d_step + 1;
+  fuse_setup(&p, fuse_max_k(p, ring_dev, AT_MAX_FUSE));
   if ((e = launch_wave_field(w, 0.0, hd->d_tables, ring_dev, hd->stream)) != cudaSuccess ||
       (e = ab_start(hd, cfg->burgers == 0)) != cudaSuccess ||
       (e = launch_draw_delays(p, 0, hd->stream)) != cudaSuccess) {
@@ -347,7 +348,10 @@ static int build_graph(at_handle *hd) {
   cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cuda_fail(e, "at_step: capture stream");
   e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-  for (int64_t g = 0; g < kGraphSteps && e == cudaSuccess; ++g) e = launch_forward_step(hd->sp, g, hd->d_step, cap);
+  int64_t g = 0;
+  const int64_t K = hd->sp.fuse_k;
+  for (; K > 1 && g + K <= kGraphSteps && e == cudaSuccess; g += K) e = launch_forward_block(hd->sp, g, hd->d_step, cap);
+  for (; g < kGraphSteps && e == cudaSuccess; ++g) e = launch_forward_step(hd->sp, g, hd->d_step, cap);
   if (e == cudaSuccess) e = launch_step_counter(hd->d_step, kGraphSteps, false, cap);
   cudaGraph_t graph = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
@@ -382,11 +386,32 @@ extern "C" int at_step(at_handle_t *hd, int64_t nsteps) {
       hd->step += kGraphSteps;
     }
   }
-  for (int64_t s = chunks * kGraphSteps; s < nsteps; ++s) {
+  int64_t s = chunks * kGraphSteps;
+  const int64_t K = hd->sp.fuse_k;
+  for (; K > 1 && s + K <= nsteps; s += K) {
+    if ((e = launch_forward_block(hd->sp, hd->step, nullptr, hd->stream)) != cudaSuccess)
+      return cuda_fail(e, "at_step: launch");
+    hd->step += K;
+  }
+  for (; s < nsteps; ++s) {
     if ((e = launch_forward_step(hd->sp, hd->step, nullptr, hd->stream)) != cudaSuccess)
       return cuda_fail(e, "at_step: launch");
     hd->step += 1;
   }
+  return AT_OK;
+}
+
+extern "C" int at_set_fusion(at_handle_t *hd, int32_t k, int32_t *k_used) {
+  if (!hd || k < 1 || k > AT_MAX_FUSE) return fail(AT_ERR_ARG, "at_set_fusion: k must be 1..4");
+  cudaError_t e = cudaStreamSynchronize(hd->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "at_set_fusion");
+  if (hd->exec) cudaGraphExecDestroy(hd->exec);
+  if (hd->graph) cudaGraphDestroy(hd->graph);
+  hd->exec = nullptr;
+  hd->graph = nullptr;
+  const int K = fuse_max_k(hd->sp, hd->sp.ring, k);
+  fuse_setup(&hd->sp, K);
+  if (k_used) *k_used = K;
   return AT_OK;
 }
 

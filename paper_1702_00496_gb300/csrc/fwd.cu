@@ -21,6 +21,9 @@
 // clock sustained for dependent FMA chains): each point costs the minimum 1 + 2 h dim FP64 operations, all of
 // them FMAs -- the chain starts with fma(s0, u_i, +0) on a runtime zero, because a DMUL occupies the FP64
 // pipe longer than a DFMA and the result is the same rounded product.
+#include <algorithm>
+#include <cstring>
+
 #include "stencil.cuh"
 
 namespace {
@@ -52,6 +55,85 @@ __global__ void __launch_bounds__(512) forward_group_kernel(const StepParams p, 
       const int z = (int)(r / p.n[1]), y = (int)(r - (int64_t)z * p.n[1]);
       group_step<3, H, LdgNC, AB, KIND>(p, keff, un, out, n, x0, y, z);
     }
+  }
+}
+
+// Blocks of K steps (1D forward Euler, central and time-expanded rows).  Away from PE boundaries the step is the
+// same linear stencil at every point and step, so K steps of it are one stencil of half-width h K: its taps ck are
+// the K-fold composition of the merged taps, and a group whose K-step stencil stays inside its PE gets U^{n+K}
+// from U^n with 2 h K + 1 FMAs per point instead of K (2 h + 1).  The cells near a PE boundary, whose buffer points
+// take the delayed halo values of every step, are advanced step by step: step j < K-1 of the block runs the step
+// kernel's arithmetic on the cells within zr[j] of each boundary (zones that shrink by at least h per step), and
+// the block launch gives the edge groups their last step from U^{n+K-1}.  The zones hold the face strips, so the
+// intermediate levels are in the ring wherever a later step reads a delayed level.  Each launch draws the delays of
+// the step after its own, so the delay log and the effective delays are those of single steps.
+
+// Step n of a block, on the groups within r cells of every PE boundary (r a multiple of 4; 2 r <= PE width).
+template <int H>
+__global__ void __launch_bounds__(512) forward_zone_kernel(const StepParams p, const int64_t n_off,
+                                                           const int64_t *n_base, const int r) {
+  const int64_t n = n_off + (n_base ? *n_base : 0);
+  const double *__restrict__ un = p.ring + (n % p.R) * p.ntot;
+  double *__restrict__ out = p.ring + ((n + 1) % p.R) * p.ntot;
+  const uint8_t *keff = p.keff + (n & 1) * p.nb;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nthreads = (int64_t)gridDim.x * blockDim.x;
+  draw_sides(p, n + 1, tid, nthreads, p.keff + ((n + 1) & 1) * p.nb);
+  const int gpb = r >> 1;  // groups per boundary: 2 r cells
+  const int64_t zone_groups = p.use_pe[0] ? (int64_t)p.pe[0] * gpb : 0;
+  for (int64_t q = tid; q < zone_groups; q += nthreads) {
+    const int64_t b = q / gpb;
+    const int t = (int)(q - b * gpb);
+    const int x0 = wrap_coord((int)(b * p.S[0]) - r + 4 * t, p.n[0]);
+    group_step<1, H, LdgNC, false, 0>(p, keff, un, out, n, x0, 0, 0);
+  }
+}
+
+// The last step m = n + K - 1 of a block: inner groups U^{n+K} = ck * U^n, edge groups the step from U^m.
+template <int H, int K>
+__global__ void __launch_bounds__(512) forward_block_kernel(const StepParams p, const int64_t n_off,
+                                                            const int64_t *n_base) {
+  constexpr int TK = H * K;                  // half-width of the composed stencil
+  constexpr int WK = (TK + 1) / 2 * 2;       // its x window, rounded to even cells (16-byte loads)
+  constexpr int NW = 4 + 2 * WK;
+  const int64_t m = n_off + (n_base ? *n_base : 0), n0 = m - (K - 1);
+  const double *__restrict__ u0 = p.ring + (n0 % p.R) * p.ntot;
+  const double *__restrict__ um = p.ring + (m % p.R) * p.ntot;
+  double *__restrict__ out = p.ring + ((m + 1) % p.R) * p.ntot;
+  const uint8_t *keff = p.keff + (m & 1) * p.nb;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nthreads = (int64_t)gridDim.x * blockDim.x;
+  draw_sides(p, m + 1, tid, nthreads, p.keff + ((m + 1) & 1) * p.nb);
+  const int nx = p.n[0];
+  const int64_t groups = nx >> 2;
+  const int64_t gS = p.use_pe[0] ? p.S[0] >> 2 : groups;
+  const int64_t n_inner = (groups / gS) * (gS - 2 * p.fe);
+  for (int64_t k = tid; k < groups; k += nthreads) {
+    const int x0 = (int)(group_1d_order_e(p, k, p.fe) << 2);
+    if (k >= n_inner) {
+      group_step<1, H, LdgNC, false, 0>(p, keff, um, out, m, x0, 0, 0);
+      continue;
+    }
+    double v[NW];
+    if (x0 >= WK && x0 + 4 + WK <= nx) {
+#pragma unroll
+      for (int t = 0; t < NW; t += 2) {
+        const double2 a = LdgNC::ld2(u0 + x0 - WK + t);
+        v[t] = a.x; v[t + 1] = a.y;
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < NW; ++t) v[t] = LdgNC::ld(u0 + wrap_coord(x0 - WK + t, nx));
+    }
+    double r[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      double acc = fma(p.ck[TK], v[q + WK], p.zero);
+#pragma unroll
+      for (int j = -TK; j <= TK; ++j)
+        if (j != 0) acc = fma(p.ck[j + TK], v[q + WK + j], acc);
+      r[q] = acc;
+    }
+    reinterpret_cast<double2 *>(out + x0)[0] = make_double2(r[0], r[1]);
+    reinterpret_cast<double2 *>(out + x0)[1] = make_double2(r[2], r[3]);
   }
 }
 
@@ -204,6 +286,96 @@ cudaError_t launch_forward_step(const StepParams &p, int64_t n, const int64_t *n
     else launch_h<3, false>(p, grouped, blocks, threads, n, n_base, st);
   }
   return cudaGetLastError();
+}
+
+namespace {
+
+template <int H, int K>
+void launch_block_typed(const StepParams &p, int blocks, int zblocks[], int threads, int64_t n_off,
+                        const int64_t *n_base, cudaStream_t st) {
+  for (int j = 0; j + 1 < K; ++j)
+    forward_zone_kernel<H><<<zblocks[j], threads, 0, st>>>(p, n_off + j, n_base, p.zr[j]);
+  forward_block_kernel<H, K><<<blocks, threads, 0, st>>>(p, n_off + K - 1, n_base);
+}
+
+template <int H>
+void launch_block_h(const StepParams &p, int blocks, int zblocks[], int threads, int64_t n_off, const int64_t *n_base,
+                    cudaStream_t st) {
+  if (p.fuse_k == 2) launch_block_typed<H, 2>(p, blocks, zblocks, threads, n_off, n_base, st);
+  else if (p.fuse_k == 3) launch_block_typed<H, 3>(p, blocks, zblocks, threads, n_off, n_base, st);
+  else launch_block_typed<H, 4>(p, blocks, zblocks, threads, n_off, n_base, st);
+}
+
+}  // namespace
+
+cudaError_t launch_forward_block(const StepParams &p, int64_t n_off, const int64_t *n_base, cudaStream_t st) {
+  const int threads = p.threads > 0 ? p.threads : 256;
+  const int max_blocks = sm_count() * (p.blocks_per_sm > 0 ? p.blocks_per_sm : 32);
+  const int64_t b = (p.ntot / 4 + threads - 1) / threads;
+  const int blocks = (int)(b < max_blocks ? b : max_blocks);
+  // zone launches: enough threads for the zone's groups and for the delay draws of every side
+  int zblocks[AT_MAX_FUSE];
+  for (int j = 0; j + 1 < p.fuse_k; ++j) {
+    const int64_t work = std::max<int64_t>(p.use_pe[0] ? (int64_t)p.pe[0] * (p.zr[j] >> 1) : 0, p.nb);
+    const int64_t zb = (work + threads - 1) / threads;
+    zblocks[j] = (int)(zb < max_blocks ? zb : max_blocks);
+    if (zblocks[j] < 1) zblocks[j] = 1;
+  }
+  if (p.h == 1) launch_block_h<1>(p, blocks, zblocks, threads, n_off, n_base, st);
+  else if (p.h == 2) launch_block_h<2>(p, blocks, zblocks, threads, n_off, n_base, st);
+  else launch_block_h<3>(p, blocks, zblocks, threads, n_off, n_base, st);
+  return cudaGetLastError();
+}
+
+// Zone radii of a K-step block: the edge groups of the last step reach 4 ceil(h K / 4) cells in from each PE end and
+// read U^{n+K-1} h cells further; each earlier step's zone reaches h cells further than the next one's (multiples
+// of 4, so zones are whole groups).
+static void fuse_radii(int h, int K, int *fe, int zr[]) {
+  const int reach = (h * K + 3) / 4 * 4;
+  *fe = reach / 4;
+  int r = reach;
+  for (int j = K - 2; j >= 0; --j) {
+    r = (r + h + 3) / 4 * 4;
+    zr[j] = r;
+  }
+}
+
+int fuse_max_k(const StepParams &p, const void *ring, int kmax) {
+  if (p.dim != 1 || p.scheme > AT_AT || p.burgers || p.ts != 1 || !grouped_shape(p, ring)) return 1;
+  for (int K = kmax < AT_MAX_FUSE ? kmax : AT_MAX_FUSE; K >= 2; --K) {
+    if (p.R <= K) continue;  // U^n must stay in the ring while U^{n+K} is written
+    int fe, zr[AT_MAX_FUSE];
+    fuse_radii(p.h, K, &fe, zr);
+    const int WK = (p.h * K + 1) / 2 * 2;
+    if (p.n[0] < 2 * (4 + 2 * WK)) continue;  // the composed window stays within one wrap of the domain
+    if (p.use_pe[0] && (2 * zr[0] > p.S[0] || p.S[0] / 4 <= 2 * fe)) continue;
+    return K;
+  }
+  return 1;
+}
+
+void fuse_setup(StepParams *p, int k) {
+  p->fuse_k = k > 1 ? k : 0;
+  p->fe = 0;
+  std::memset(p->zr, 0, sizeof(p->zr));
+  std::memset(p->ck, 0, sizeof(p->ck));
+  if (k <= 1) return;
+  const int h = p->h;
+  fuse_radii(h, k, &p->fe, p->zr);
+  if (!p->use_pe[0]) p->fe = 0;
+  // K-fold composition of the merged taps (s0 at the centre), in a fixed order
+  double s[2 * AT_MAX_H + 1], c[2 * AT_MAX_H * AT_MAX_FUSE + 1] = {1.0}, t[2 * AT_MAX_H * AT_MAX_FUSE + 1];
+  for (int j = -h; j <= h; ++j) s[j + h] = j == 0 ? p->s0 : p->s[0][j + h];
+  int w = 0;  // c holds taps -w .. w at c[0 .. 2w]
+  for (int step = 0; step < k; ++step) {
+    const int w2 = w + h;
+    for (int i = 0; i <= 2 * w2; ++i) t[i] = 0.0;
+    for (int i = 0; i <= 2 * w; ++i)
+      for (int j = 0; j <= 2 * h; ++j) t[i + j] += c[i] * s[j];
+    w = w2;
+    for (int i = 0; i <= 2 * w; ++i) c[i] = t[i];
+  }
+  for (int i = 0; i <= 2 * w; ++i) p->ck[i] = c[i];
 }
 
 cudaError_t launch_sync_rhs(const StepParams &p, const double *u, double *out, cudaStream_t st) {

@@ -15,6 +15,7 @@
 #define AT_MAX_KROT 64
 #define AT_STAT_FIELDS 9
 #define AT_STAT_BLOCKS 1024
+#define AT_MAX_FUSE 4
 
 void at_internal_set_error(const char *msg);
 
@@ -70,6 +71,13 @@ struct StepParams {
   // part dt c2 / dx_a^2 of each merged edge-row tap of the rows expanded in space.
   double qc[3];
   double eq[3][2][AT_MAX_ETAPS];
+  // K-step blocks of the 1D forward-Euler step (central and time-expanded rows, groups of four), fuse_k = K > 1:
+  // step j < K-1 of a block computes only the cells within zr[j] of every PE boundary, step K-1 the edge groups
+  // (fe per PE end) from U^{n+K-1} and every other group from U^n with ck, the K-fold composition of the merged
+  // interior taps (index j + h K).
+  int32_t fuse_k, fe;
+  int32_t zr[AT_MAX_FUSE];
+  double ck[2 * AT_MAX_H * AT_MAX_FUSE + 1];
 };
 
 // The modes of one axis at one time t, prepared on the host for the recurrences over k: sorted by wavenumber,
@@ -105,6 +113,11 @@ int at_prepare_params(const at_config_t *cfg, double *ring_dev, uint8_t *log_dev
 // One forward step n = n_off + (*n_base if n_base else 0): reading the base from device memory lets a
 // captured graph of consecutive steps be replayed at any step.
 cudaError_t launch_forward_step(const StepParams &p, int64_t n_off, const int64_t *n_base, cudaStream_t st);
+// The fuse_k steps n .. n+fuse_k-1 of a block (n = n_off + *n_base): zone launches, then the block launch.
+cudaError_t launch_forward_block(const StepParams &p, int64_t n_off, const int64_t *n_base, cudaStream_t st);
+// Largest block length K <= kmax (1: none) that the problem admits, and the block parameters for K (host).
+int fuse_max_k(const StepParams &p, const void *ring, int kmax);
+void fuse_setup(StepParams *p, int k);
 // *n_base = v (set) or *n_base += v.
 cudaError_t launch_step_counter(int64_t *n_base, int64_t v, bool set, cudaStream_t st);
 // Draw the delays of step n into keff + (n & 1) * nb (and log row n): the set-up before a first step.

@@ -83,6 +83,21 @@ __device__ __forceinline__ int64_t group_1d_order(const StepParams &p, int64_t k
   return (int64_t)(kk >> 1) * gS + ((kk & 1) ? gS - 1 : 0);
 }
 
+// The same order with e edge groups at each PE end (e = 1 is group_1d_order): the gS - 2e inner groups of every PE
+// first, then the 2e edge groups of every PE.  k < number of groups; requires gS > 2e.
+__device__ __forceinline__ int64_t group_1d_order_e(const StepParams &p, int64_t k, int e) {
+  const uint32_t gS = (uint32_t)(p.use_pe[0] ? p.S[0] >> 2 : p.n[0] >> 2);
+  if (e == 0) return k;
+  const uint32_t inner = gS - 2 * e, npe = (uint32_t)(p.n[0] >> 2) / gS, uk = (uint32_t)k;
+  const uint32_t n_int = npe * inner;
+  if (uk < n_int) {
+    const uint32_t pe = uk / inner;
+    return (int64_t)pe * gS + e + (uk - pe * inner);
+  }
+  const uint32_t kk = uk - n_int, pe = kk / (2 * e), r = kk - pe * (2 * e);
+  return (int64_t)pe * gS + (r < (uint32_t)e ? r : gS - 2 * e + r);
+}
+
 // Side index of face (axis a, lo/hi) of the PE with index (px, py, pz).
 template <int DIM>
 __device__ __forceinline__ int64_t side_of(const StepParams &p, const int pidx[3], int a, int hi) {

@@ -60,12 +60,14 @@ def test_mixed_ensemble_matches_oracle(threads, ctas):
 
 
 def test_ensemble_is_bitwise_the_single_problem_path():
-    from paper_1702_00496_gb300 import Ensemble, Solver
+    """Each member equals the single-problem path run in single steps (the engine steps one step at a time)."""
+    from paper_1702_00496_gb300 import Ensemble, Solver, at_set_fusion
     specs = _members(5, [256, 1024], [3, 4], [4], seed0=900)
     ens = Ensemble(specs, 250)
     ens.run()
     for r, spec in enumerate(specs):
         s = Solver(spec)
+        at_set_fusion(s.h, 1)
         s.step(250)
         s.sync()
         assert torch.equal(ens.field(r), s.field().reshape(-1)), r

@@ -19,9 +19,11 @@ TOL = 1e-12
 THREADS = os.cpu_count() or 1
 
 
-def _gpu_run(spec, nsteps, log=True):
-    from paper_1702_00496_gb300 import Solver
+def _gpu_run(spec, nsteps, log=True, single_steps=False):
+    from paper_1702_00496_gb300 import Solver, at_set_fusion
     s = Solver(spec, log_steps=nsteps if log else 0)
+    if single_steps:
+        at_set_fusion(s.h, 1)
     s.step(nsteps)
     s.sync()
     u = s.field().cpu().numpy().copy()
@@ -76,12 +78,16 @@ def test_1d_minimum_pe_width(order):
 
 
 def test_single_delay_level_equals_synchronous_run():
+    """L = 1: every delay is 0, so the AT scheme is the synchronous one, bit for bit in single steps (the AT ring
+    admits 3-step blocks, the synchronous one none) and to rounding in blocks."""
     spec, _ = W.wl_1d(512, 8, 4, 1, 0, 6, (1, 2))
-    u_at, d, _ = _gpu_run(spec, 100)
+    u_at, d, _ = _gpu_run(spec, 100, single_steps=True)
+    u_blk, _, _ = _gpu_run(spec, 100)
     assert not d.any()
     spec["scheme"] = W.SYNC
     u_sync, _, _ = _gpu_run(spec, 100)
     assert np.array_equal(u_at, u_sync)
+    assert np.linalg.norm(u_blk - u_sync) / np.linalg.norm(u_sync) <= 1e-13
 
 
 @pytest.mark.parametrize("modes", [range(1, 17), range(9, 25)], ids=["k_to_16", "k_9_to_24"])
