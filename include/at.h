@@ -166,7 +166,9 @@ int at_step(at_handle_t *hd, int64_t nsteps);
 /* Block length of at_step for the following calls: the largest K <= k (1..4) the problem admits -- 1D, forward
  * Euler, AT_SYNC / AT_ASYNC_STD / AT_AT, not Burgers, n0 and the PE width multiples of 4, ring 16-byte aligned,
  * more ring slots than K, and PEs wide enough that the zones stepped one step at a time (under 10 h + 16 cells
- * around each boundary for K = 4) do not meet -- written to *k_used (1: single steps).  at_init picks the largest
+ * around each boundary for K = 4) do not meet and that a block saves at least 5 % of the FP64 operations of K
+ * single steps (PEs of at least 144 cells for order 4 and K = 4, 72 for order 2) -- written to *k_used (1: single
+ * steps).  at_init picks the largest
  * admissible K <= 4.  k = 1 restores single steps.  Waits for the stream and drops the captured step graph.
  * Errors: AT_ERR_ARG (k outside 1..4), AT_ERR_CUDA. */
 int at_set_fusion(at_handle_t *hd, int32_t k, int32_t *k_used);

@@ -349,6 +349,13 @@ int fuse_max_k(const StepParams &p, const void *ring, int kmax) {
     const int WK = (p.h * K + 1) / 2 * 2;
     if (p.n[0] < 2 * (4 + 2 * WK)) continue;  // the composed window stays within one wrap of the domain
     if (p.use_pe[0] && (2 * zr[0] > p.S[0] || p.S[0] / 4 <= 2 * fe)) continue;
+    if (p.use_pe[0]) {  // FP64 operations per PE and block against K single steps: blocks must save 5 %
+      const int64_t S = p.S[0], taps = 2 * p.h + 1;
+      int64_t zone = 0;
+      for (int j = 0; j + 1 < K; ++j) zone += 2 * zr[j];
+      const int64_t block = zone * taps + (S - 8 * fe) * (2 * p.h * K + 1) + 8 * fe * taps;
+      if (20 * block > 19 * K * S * taps) continue;
+    }
     return K;
   }
   return 1;

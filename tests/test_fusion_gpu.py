@@ -32,7 +32,10 @@ def test_block_length_follows_the_shape():
     assert _k_used(W.wl_1d(1 << 14, 16, 4, 4, 0, 1, (1, 2))[0], 2) == 2
     assert _k_used(W.wl_1d(1 << 14, 16, 4, 1, 0, 1, (1, 2))[0]) == 3          # R = L + T = 4: K < R
     assert _k_used(W.wl_1d(1 << 14, 16, 4, 1, 0, 1, (1, 2), scheme=W.SYNC)[0]) == 1  # R = 2
-    assert _k_used(W.wl_1d(256, 16, 4, 4, 0, 1, (1, 2))[0]) == 2               # PEs of 16 cells: K = 2 zones fit
+    assert _k_used(W.wl_1d(256, 16, 4, 4, 0, 1, (1, 2))[0]) == 1               # PEs of 16 cells: zones cost more
+    assert _k_used(W.wl_1d(64 * 16, 16, 4, 4, 0, 1, (1, 2))[0]) == 1           # PEs of 64: blocks would save < 5 %
+    assert _k_used(W.wl_1d(144 * 16, 16, 4, 4, 0, 1, (1, 2))[0]) == 4          # PEs of 144: they save 5 %
+    assert _k_used(W.wl_1d(128 * 16, 16, 4, 4, 0, 1, (1, 2))[0]) == 3
     assert _k_used(W.wl_1d(1 << 14, 16, 4, 3, 0, 1, (1, 2), tsteps=2, r_alpha=0.05)[0]) == 1  # Adams-Bashforth
     assert _k_used(W.wl_1d(1 << 14, 16, 2, 3, 0, 1, (1, 2), scheme=W.AT_SPACE2)[0]) == 1      # rows in space
     assert _k_used(W.wl_1d(1002, 6, 4, 4, 0, 1, (1, 2))[0]) == 1               # not groups of four
@@ -59,8 +62,9 @@ BLOCK_CASES = [
     ("o4_std", lambda: W.wl_1d(4096, 16, 4, 4, 0, 34, range(1, 5), scheme=W.ASYNC_STD)[0]),
     ("o4_sync_L5", lambda: W.wl_1d(4096, 16, 4, 5, 0, 35, range(1, 5), scheme=W.SYNC)[0]),
     ("o4_unsplit", lambda: W.wl_1d(2048, 1, 4, 4, 0, 36, range(1, 5))[0]),
-    ("o4_zone_limit", lambda: W.wl_1d(40 * 16, 16, 4, 4, 0, 37, range(1, 5))[0]),   # PEs of 2 zr[0] = 40 cells
-    ("o2_zone_limit", lambda: W.wl_1d(32 * 8, 8, 2, 3, 0, 38, range(1, 5))[0]),     # the 1d_n256 workload's shape
+    ("o4_narrowest", lambda: W.wl_1d(144 * 16, 16, 4, 4, 0, 37, range(1, 5))[0]),   # narrowest PEs with K = 4
+    ("o2_narrowest", lambda: W.wl_1d(72 * 8, 8, 2, 3, 0, 38, range(1, 5))[0]),
+    ("o4_k3", lambda: W.wl_1d(128 * 16, 16, 4, 4, 0, 40, range(1, 5))[0]),
 ]
 
 

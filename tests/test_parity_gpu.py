@@ -78,8 +78,8 @@ def test_1d_minimum_pe_width(order):
 
 
 def test_single_delay_level_equals_synchronous_run():
-    """L = 1: every delay is 0, so the AT scheme is the synchronous one, bit for bit in single steps (the AT ring
-    admits 3-step blocks, the synchronous one none) and to rounding in blocks."""
+    """L = 1: every delay is 0, so the AT scheme is the synchronous one, bit for bit in single steps, and to
+    rounding in at_step's blocks wherever the shape admits them."""
     spec, _ = W.wl_1d(512, 8, 4, 1, 0, 6, (1, 2))
     u_at, d, _ = _gpu_run(spec, 100, single_steps=True)
     u_blk, _, _ = _gpu_run(spec, 100)
