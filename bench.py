@@ -188,19 +188,25 @@ def bytes_per_update(spec) -> int:
     return 16 + (8 * ts if ts > 1 else 0)
 
 
-def launches_per_run(spec, T: int) -> int:
+def launches_per_run(spec, T: int, K: int = 1) -> int:
     """Kernels of this library one timed run launches: the reset (initial field, Adams-Bashforth pre-history and
     its history counter, the first delay draw), T forward steps (one counter update before the captured graphs,
-    each 50-step graph holding 50 step kernels -- a K-step block is K-1 zone launches and one block launch -- and a
-    counter kernel; the remainder launched one by one) and the error statistics."""
+    each graph of G = 50 steps -- 48 in blocks of K = 4 or 3: whole blocks -- holding its step kernels, a block
+    being one zone launch and one block launch, and a counter kernel; the remainder launched one by one) and the
+    error statistics."""
     dim, ts = spec["dim"], time_levels(spec)
     wave = 1 if dim == 1 else 2
     if spec.get("burgers", 0):  # no analytic pre-history: the history counter only
         reset = wave + 1 + (1 if ts > 1 else 0)
     else:
         reset = wave + 1 + (((ts - 1) * (wave + 1) + 1) if ts > 1 else 0)
-    chunks = T // 50
-    step = (1 + 51 * chunks if chunks else 0) + (T - 50 * chunks)
+    G = 50 // K * K if K > 1 else 50
+
+    def launches(steps):
+        return (steps // K) * 2 + steps % K if K > 1 else steps
+
+    chunks = T // G
+    step = (1 + (launches(G) + 1) * chunks if chunks else 0) + launches(T - G * chunks)
     stats = 2 if dim == 1 else 3
     return reset + step + stats
 
@@ -477,8 +483,8 @@ def measure_forward(spec, T, args, local, warmup, steps, world=1, e2e=False, flu
     ops = fp64_ops_per_update(spec)
     if kblock > 1:
         # blocks of K steps: 2 h K + 1 FP64 operations per point and block away from PE boundaries
-        kname = (f"forward_block_kernel<{spec['order'] // 2},{kblock}> + forward_zone_kernel<{spec['order'] // 2}> "
-                 f"(blocks of {kblock} steps)")
+        kname = (f"forward_block_kernel<{spec['order'] // 2},{kblock}> + forward_zones_kernel<{spec['order'] // 2},"
+                 f"{kblock}> (blocks of {kblock} steps)")
         ops = (spec["order"] * kblock + 1) / kblock
     out["roofline"] = roofline_alu(flops_per_update(spec) * ntot, bytes_per_update(spec) * ntot, kern_ms,
                                    ops * ntot, kname, local, clocks,
@@ -491,7 +497,7 @@ def measure_forward(spec, T, args, local, warmup, steps, world=1, e2e=False, flu
                                    "lanes per clock use that count")
     if workload in TRAFFIC_NOTES:
         out["roofline"]["traffic_note"] = TRAFFIC_NOTES[workload]
-    out["gpu_launches"] = steps * launches_per_run(spec, T)
+    out["gpu_launches"] = steps * launches_per_run(spec, T, kblock)
     solver.close()
     del flush
     return out

@@ -157,8 +157,8 @@ int at_init(const at_config_t *cfg, double *ring_dev, int64_t ring_len, uint8_t 
  * one stencil of half-width h K (the K-fold composition of its taps; exact in exact arithmetic, the rounding of
  * each cell differs), and the cells near PE boundaries, which read delayed halo values, are stepped one step at a
  * time; the delays, the delay log and the levels a later step reads at delayed levels are those of single steps.
- * Blocks start at the first step of each call (and of each 50-step graph inside it), so the same steps split
- * into other calls give results equal up to rounding, not bit for bit.
+ * Blocks start at the first step of each call (and of each captured graph inside it, 48 steps for K = 4), so the
+ * same steps split into other calls give results equal up to rounding, not bit for bit.
  * Enqueued on the handle's stream; returns without waiting.  Errors: AT_ERR_ARG, AT_ERR_STATE (the
  * delay log would overflow), AT_ERR_CUDA. */
 int at_step(at_handle_t *hd, int64_t nsteps);

@@ -343,16 +343,22 @@ extern "C" int at_init(const at_config_t *cfg, double *ring_dev, int64_t ring_le
   return AT_OK;
 }
 
+// Steps per captured graph: kGraphSteps, rounded down to whole blocks of K steps when at_step runs blocks.
+static int64_t graph_steps(const at_handle *hd) {
+  const int64_t K = hd->sp.fuse_k;
+  return K > 1 ? kGraphSteps / K * K : kGraphSteps;
+}
+
 static int build_graph(at_handle *hd) {
   cudaStream_t cap;
   cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cuda_fail(e, "at_step: capture stream");
   e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   int64_t g = 0;
-  const int64_t K = hd->sp.fuse_k;
-  for (; K > 1 && g + K <= kGraphSteps && e == cudaSuccess; g += K) e = launch_forward_block(hd->sp, g, hd->d_step, cap);
-  for (; g < kGraphSteps && e == cudaSuccess; ++g) e = launch_forward_step(hd->sp, g, hd->d_step, cap);
-  if (e == cudaSuccess) e = launch_step_counter(hd->d_step, kGraphSteps, false, cap);
+  const int64_t K = hd->sp.fuse_k, G = graph_steps(hd);
+  for (; K > 1 && g + K <= G && e == cudaSuccess; g += K) e = launch_forward_block(hd->sp, g, hd->d_step, cap);
+  for (; g < G && e == cudaSuccess; ++g) e = launch_forward_step(hd->sp, g, hd->d_step, cap);
+  if (e == cudaSuccess) e = launch_step_counter(hd->d_step, G, false, cap);
   cudaGraph_t graph = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
   if (e == cudaSuccess) e = e2;
@@ -373,7 +379,7 @@ extern "C" int at_step(at_handle_t *hd, int64_t nsteps) {
   if (hd->sp.log && hd->step + nsteps > hd->log_steps) return fail(AT_ERR_STATE, "at_step: delay log is full");
   if (hd->step + nsteps > 0xFFFFFFFFll) return fail(AT_ERR_STATE, "at_step: step counter exceeds 32 bits");
   cudaError_t e;
-  const int64_t chunks = nsteps / kGraphSteps;
+  const int64_t G = graph_steps(hd), chunks = nsteps / G;
   if (chunks > 0) {
     if (!hd->exec) {
       int rc = build_graph(hd);
@@ -383,10 +389,10 @@ extern "C" int at_step(at_handle_t *hd, int64_t nsteps) {
       return cuda_fail(e, "at_step: counter");
     for (int64_t c = 0; c < chunks; ++c) {
       if ((e = cudaGraphLaunch(hd->exec, hd->stream)) != cudaSuccess) return cuda_fail(e, "at_step: graph launch");
-      hd->step += kGraphSteps;
+      hd->step += G;
     }
   }
-  int64_t s = chunks * kGraphSteps;
+  int64_t s = chunks * G;
   const int64_t K = hd->sp.fuse_k;
   for (; K > 1 && s + K <= nsteps; s += K) {
     if ((e = launch_forward_block(hd->sp, hd->step, nullptr, hd->stream)) != cudaSuccess)

@@ -62,29 +62,53 @@ __global__ void __launch_bounds__(512) forward_group_kernel(const StepParams p, 
 // same linear stencil at every point and step, so K steps of it are one stencil of half-width h K: its taps ck are
 // the K-fold composition of the merged taps, and a group whose K-step stencil stays inside its PE gets U^{n+K}
 // from U^n with 2 h K + 1 FMAs per point instead of K (2 h + 1).  The cells near a PE boundary, whose buffer points
-// take the delayed halo values of every step, are advanced step by step: step j < K-1 of the block runs the step
-// kernel's arithmetic on the cells within zr[j] of each boundary (zones that shrink by at least h per step), and
-// the block launch gives the edge groups their last step from U^{n+K-1}.  The zones hold the face strips, so the
-// intermediate levels are in the ring wherever a later step reads a delayed level.  Each launch draws the delays of
-// the step after its own, so the delay log and the effective delays are those of single steps.
+// take the delayed halo values of every step, are advanced step by step: the zone launch runs steps n .. n+K-2 of
+// the step kernel's arithmetic on the cells within zr[j] of each boundary (zones that shrink by at least h per
+// step), and the block launch gives the edge groups their last step from U^{n+K-1}.  The zones hold the face
+// strips, so the intermediate levels are in the ring wherever a later step reads a delayed level.  The delays of
+// steps n+1 .. n+K-1 are drawn by the zone launch and the delays of step n+K by the block launch, so the delay log
+// and the effective delays are those of single steps.
 
-// Step n of a block, on the groups within r cells of every PE boundary (r a multiple of 4; 2 r <= PE width).
-template <int H>
-__global__ void __launch_bounds__(512) forward_zone_kernel(const StepParams p, const int64_t n_off,
-                                                           const int64_t *n_base, const int r) {
+// Zone launch of the block starting at step n: a warp per PE boundary runs steps n .. n+K-2 on its zone.  A zone
+// lies within S/2 of its boundary, so its cells read across that boundary only: the warp draws the delays of the two
+// sides facing it (the right side of the PE before, the left side of the PE after) for steps n+1 .. n+K-1 itself,
+// into the effective-delay buffer (whose slot for each step and side only this warp uses) and the log, and the
+// steps are separated by __syncwarp, so the loads are coherent ones.  Without PE boundaries warp 0 only draws.
+template <int H, int K>
+__global__ void __launch_bounds__(128) forward_zones_kernel(const StepParams p, const int64_t n_off,
+                                                            const int64_t *n_base) {
+  // the block launch that follows may start now: its inner groups read only U^n, and it waits for this grid before
+  // its edge groups and its delay draws
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int64_t n = n_off + (n_base ? *n_base : 0);
-  const double *__restrict__ un = p.ring + (n % p.R) * p.ntot;
-  double *__restrict__ out = p.ring + ((n + 1) % p.R) * p.ntot;
-  const uint8_t *keff = p.keff + (n & 1) * p.nb;
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nthreads = (int64_t)gridDim.x * blockDim.x;
-  draw_sides(p, n + 1, tid, nthreads, p.keff + ((n + 1) & 1) * p.nb);
-  const int gpb = r >> 1;  // groups per boundary: 2 r cells
-  const int64_t zone_groups = p.use_pe[0] ? (int64_t)p.pe[0] * gpb : 0;
-  for (int64_t q = tid; q < zone_groups; q += nthreads) {
-    const int64_t b = q / gpb;
-    const int t = (int)(q - b * gpb);
-    const int x0 = wrap_coord((int)(b * p.S[0]) - r + 4 * t, p.n[0]);
-    group_step<1, H, LdgNC, false, 0>(p, keff, un, out, n, x0, 0, 0);
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t P = p.pe[0], nbound = p.use_pe[0] ? P : 0;
+  for (int64_t b = warp; b < (nbound > 0 ? nbound : 1); b += nwarps) {
+    const int64_t sides[2] = {nbound ? 2 * ((b + P - 1) % P) + 1 : 0, nbound ? 2 * b : 1};
+    for (int j = 0; j + 1 < K; ++j) {
+      const int64_t st = n + j;  // the step this round computes; it draws the delays of step st + 1
+      if (lane < 2) {
+        const int64_t side = sides[lane];
+        int raw = 0;
+        if (p.scheme != 0)
+          raw = delay_draw(p.seed, (uint32_t)(st + 1), (uint32_t)side, p.L, p.use_thr ? p.thr : nullptr);
+        p.keff[((st + 1) & 1) * p.nb + side] = (uint8_t)delay_clamp(raw, st + 1, p.T);
+        if (p.log != nullptr && st + 1 < p.log_steps) p.log[(st + 1) * p.nb + side] = (uint8_t)raw;
+      }
+      if (nbound) {
+        const double *un = p.ring + (st % p.R) * p.ntot;
+        double *out = p.ring + ((st + 1) % p.R) * p.ntot;
+        const uint8_t *keff = p.keff + (st & 1) * p.nb;
+        const int r = p.zr[j], ng = r >> 1;
+        for (int t = lane; t < ng; t += 32) {
+          const int x0 = wrap_coord((int)(b * p.S[0]) - r + 4 * t, p.n[0]);
+          group_step<1, H, LdCoherent, false, 0>(p, keff, un, out, st, x0, 0, 0);
+        }
+      }
+      __syncwarp();
+    }
   }
 }
 
@@ -101,17 +125,15 @@ __global__ void __launch_bounds__(512) forward_block_kernel(const StepParams p, 
   double *__restrict__ out = p.ring + ((m + 1) % p.R) * p.ntot;
   const uint8_t *keff = p.keff + (m & 1) * p.nb;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nthreads = (int64_t)gridDim.x * blockDim.x;
-  draw_sides(p, m + 1, tid, nthreads, p.keff + ((m + 1) & 1) * p.nb);
   const int nx = p.n[0];
   const int64_t groups = nx >> 2;
   const int64_t gS = p.use_pe[0] ? p.S[0] >> 2 : groups;
   const int64_t n_inner = (groups / gS) * (gS - 2 * p.fe);
-  for (int64_t k = tid; k < groups; k += nthreads) {
+  // Inner groups first: they read U^n only, so they may run while the zone launch (this block's steps n .. m-1 near
+  // the PE boundaries, launched with a programmatic dependency) still does.  Then wait for it: the edge groups read
+  // its U^m, and the delays of step m+1 go into the buffer slot its first step reads.
+  for (int64_t k = tid; k < n_inner; k += nthreads) {
     const int x0 = (int)(group_1d_order_e(p, k, p.fe) << 2);
-    if (k >= n_inner) {
-      group_step<1, H, LdgNC, false, 0>(p, keff, um, out, m, x0, 0, 0);
-      continue;
-    }
     double v[NW];
     if (x0 >= WK && x0 + 4 + WK <= nx) {
 #pragma unroll
@@ -135,6 +157,10 @@ __global__ void __launch_bounds__(512) forward_block_kernel(const StepParams p, 
     reinterpret_cast<double2 *>(out + x0)[0] = make_double2(r[0], r[1]);
     reinterpret_cast<double2 *>(out + x0)[1] = make_double2(r[2], r[3]);
   }
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  draw_sides(p, m + 1, tid, nthreads, p.keff + ((m + 1) & 1) * p.nb);
+  for (int64_t k = n_inner + tid; k < groups; k += nthreads)
+    group_step<1, H, LdgNC, false, 0>(p, keff, um, out, m, (int)(group_1d_order_e(p, k, p.fe) << 2), 0, 0);
 }
 
 __device__ __forceinline__ void point_coords(const StepParams &p, int dim, int64_t i, int c[3]) {
@@ -291,15 +317,24 @@ cudaError_t launch_forward_step(const StepParams &p, int64_t n, const int64_t *n
 namespace {
 
 template <int H, int K>
-void launch_block_typed(const StepParams &p, int blocks, int zblocks[], int threads, int64_t n_off,
+void launch_block_typed(const StepParams &p, int blocks, int zblocks, int threads, int64_t n_off,
                         const int64_t *n_base, cudaStream_t st) {
-  for (int j = 0; j + 1 < K; ++j)
-    forward_zone_kernel<H><<<zblocks[j], threads, 0, st>>>(p, n_off + j, n_base, p.zr[j]);
-  forward_block_kernel<H, K><<<blocks, threads, 0, st>>>(p, n_off + K - 1, n_base);
+  forward_zones_kernel<H, K><<<zblocks, 128, 0, st>>>(p, n_off, n_base);
+  // the block launch depends programmatically on the zone launch (it waits for it inside, before its edge groups)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, forward_block_kernel<H, K>, p, n_off + K - 1, n_base);
 }
 
 template <int H>
-void launch_block_h(const StepParams &p, int blocks, int zblocks[], int threads, int64_t n_off, const int64_t *n_base,
+void launch_block_h(const StepParams &p, int blocks, int zblocks, int threads, int64_t n_off, const int64_t *n_base,
                     cudaStream_t st) {
   if (p.fuse_k == 2) launch_block_typed<H, 2>(p, blocks, zblocks, threads, n_off, n_base, st);
   else if (p.fuse_k == 3) launch_block_typed<H, 3>(p, blocks, zblocks, threads, n_off, n_base, st);
@@ -313,14 +348,9 @@ cudaError_t launch_forward_block(const StepParams &p, int64_t n_off, const int64
   const int max_blocks = sm_count() * (p.blocks_per_sm > 0 ? p.blocks_per_sm : 32);
   const int64_t b = (p.ntot / 4 + threads - 1) / threads;
   const int blocks = (int)(b < max_blocks ? b : max_blocks);
-  // zone launches: enough threads for the zone's groups and for the delay draws of every side
-  int zblocks[AT_MAX_FUSE];
-  for (int j = 0; j + 1 < p.fuse_k; ++j) {
-    const int64_t work = std::max<int64_t>(p.use_pe[0] ? (int64_t)p.pe[0] * (p.zr[j] >> 1) : 0, p.nb);
-    const int64_t zb = (work + threads - 1) / threads;
-    zblocks[j] = (int)(zb < max_blocks ? zb : max_blocks);
-    if (zblocks[j] < 1) zblocks[j] = 1;
-  }
+  const int64_t nwarps = p.use_pe[0] ? p.pe[0] : 1;  // zone launch: one warp per PE boundary, four per block
+  const int64_t zb = (nwarps + 3) / 4;
+  const int zblocks = (int)(zb < max_blocks ? zb : max_blocks);
   if (p.h == 1) launch_block_h<1>(p, blocks, zblocks, threads, n_off, n_base, st);
   else if (p.h == 2) launch_block_h<2>(p, blocks, zblocks, threads, n_off, n_base, st);
   else launch_block_h<3>(p, blocks, zblocks, threads, n_off, n_base, st);

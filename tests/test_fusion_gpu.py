@@ -70,8 +70,8 @@ BLOCK_CASES = [
 
 @pytest.mark.parametrize("name,make", BLOCK_CASES, ids=[c[0] for c in BLOCK_CASES])
 def test_blocks_match_single_steps_and_the_oracle(name, make):
-    """Blocks of K = 4 (or less where the shape demands) against single steps: 103 steps = two 50-step graphs
-    (12 blocks and 2 single steps each) and 3 single steps; and against the oracle."""
+    """Blocks of K = 4 (or less where the shape demands) against single steps: 103 steps = two 48-step graphs
+    of 12 blocks, one more block and 3 single steps (K = 4); and against the oracle."""
     spec = make()
     nsteps = 103
     u1, d1, k1 = _run(spec, nsteps, 1)
