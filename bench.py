@@ -43,6 +43,9 @@ FP64_FMA_LANES_PER_SM = 2  # FP64 FMA lanes per SM per clock on GB300 (nominal)
 # kernel source; None where no capture of the current source exists.
 MEASURED_TRAFFIC = {
     ("1d_n16m", "forward_group_kernel<1,2,false>"): 136.95e6 + 80.50e6,
+    # blocks of 4 steps: one block launch (137.3 MB read, 82.9 MB written) and one zone launch (4.6 MB read) per
+    # block, per step
+    ("1d_n16m", "blocks of 4"): (137.3e6 + 82.9e6 + 4.6e6) / 4,
     ("1d_n16m_case2", "forward_group_kernel<1,1,false>"): None,
     ("1d_n16m_case3", "forward_group_kernel<1,1,false>"): 135.27e6 + 80.13e6,
     ("1d_n16m_case4", "forward_group_kernel<1,2,true>"): 271.91e6 + 209.17e6,
@@ -481,14 +484,20 @@ def measure_forward(spec, T, args, local, warmup, steps, world=1, e2e=False, flu
 
     kname = f"forward_group_kernel<{spec['dim']},{spec['order'] // 2},{'true' if time_levels(spec) > 1 else 'false'}>"
     ops = fp64_ops_per_update(spec)
+    bytes_update = bytes_per_update(spec)
+    traffic = MEASURED_TRAFFIC.get((workload, kname))
     if kblock > 1:
-        # blocks of K steps: 2 h K + 1 FP64 operations per point and block away from PE boundaries
+        # blocks of K steps: 2 h K + 1 FP64 operations per point and block away from PE boundaries; U^n is read and
+        # U^{n+K} written once per block
+        traffic = MEASURED_TRAFFIC.get((workload, f"blocks of {kblock}"))
         kname = (f"forward_block_kernel<{spec['order'] // 2},{kblock}> + forward_zones_kernel<{spec['order'] // 2},"
                  f"{kblock}> (blocks of {kblock} steps)")
         ops = (spec["order"] * kblock + 1) / kblock
-    out["roofline"] = roofline_alu(flops_per_update(spec) * ntot, bytes_per_update(spec) * ntot, kern_ms,
-                                   ops * ntot, kname, local, clocks,
-                                   MEASURED_TRAFFIC.get((workload, kname)), dgemm)
+        bytes_update = 16 / kblock
+    out["roofline"] = roofline_alu(flops_per_update(spec) * ntot, bytes_update * ntot, kern_ms,
+                                   ops * ntot, kname, local, clocks, traffic, dgemm)
+    if kblock > 1:
+        out["roofline"]["traffic_note"] = "DRAM read + write per step (a block launch and a zone launch per K steps, ncu)"
     out["roofline"]["fp64_ops_per_update_executed"] = ops
     if kblock > 1:
         out["roofline"]["note"] = ("achieved counts the single step's algorithmic flop per update (1 multiply and "
