@@ -73,7 +73,8 @@ __global__ void __launch_bounds__(512) forward_group_kernel(const StepParams p, 
 // lies within S/2 of its boundary, so its cells read across that boundary only: the warp draws the delays of the two
 // sides facing it (the right side of the PE before, the left side of the PE after) for steps n+1 .. n+K-1 itself,
 // into the effective-delay buffer (whose slot for each step and side only this warp uses) and the log, and the
-// steps are separated by __syncwarp, so the loads are coherent ones.  Without PE boundaries warp 0 only draws.
+// steps are separated by __syncwarp, so the loads are coherent ones.  A zone group reads only the delay of the side
+// it reaches across (its own), never one that another warp may be writing.  Without PE boundaries warp 0 only draws.
 template <int H, int K>
 __global__ void __launch_bounds__(128) forward_zones_kernel(const StepParams p, const int64_t n_off,
                                                             const int64_t *n_base) {
@@ -104,7 +105,7 @@ __global__ void __launch_bounds__(128) forward_zones_kernel(const StepParams p, 
         const int r = p.zr[j], ng = r >> 1;
         for (int t = lane; t < ng; t += 32) {
           const int x0 = wrap_coord((int)(b * p.S[0]) - r + 4 * t, p.n[0]);
-          group_step<1, H, LdCoherent, false, 0>(p, keff, un, out, st, x0, 0, 0);
+          group_update<1, H, LdCoherent, false, true>(p, keff, un, out, st, x0, 0, 0);
         }
       }
       __syncwarp();

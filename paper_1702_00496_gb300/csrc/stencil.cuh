@@ -115,8 +115,10 @@ struct XWin {
 
 // The merged stencil of the four points x0..x0+3 of row (y, z) into r[4] (and their level-n values into uc[4]);
 // requires n[0] % 4 == 0 and a 16-byte aligned slot.  keff: effective delays of step n.  ALPHA = true evaluates
-// the alpha derivative of the step instead (coefficients q0, q: dt times the AT second derivative).
-template <int DIM, int H, class LD, bool ALPHA>
+// the alpha derivative of the step instead (coefficients q0, q: dt times the AT second derivative).  OWN_SIDES = true
+// reads the delay of an x side only when the group reaches that side's buffer points (for callers whose other
+// sides' delays may be in flight).
+template <int DIM, int H, class LD, bool ALPHA, bool OWN_SIDES = false>
 __device__ __forceinline__ void group_eval(const StepParams &p, const uint8_t *__restrict__ keff,
                                            const double *__restrict__ un, int64_t n, int x0, int y, int z,
                                            double r[4], double uc[4]) {
@@ -146,7 +148,8 @@ __device__ __forceinline__ void group_eval(const StepParams &p, const uint8_t *_
 #pragma unroll
   for (int q = 0; q < 4; ++q) uc[q] = v[W + q];
   if (p.use_pe[0] && (pos[0] < H || pos[0] + 3 >= p.S[0] - H)) {
-    const int kl = keff[side_of<DIM>(p, pidx, 0, 0)], kr = keff[side_of<DIM>(p, pidx, 0, 1)];
+    const bool lo = !OWN_SIDES || pos[0] < H, hi = !OWN_SIDES || pos[0] + 3 >= p.S[0] - H;
+    const int kl = lo ? keff[side_of<DIM>(p, pidx, 0, 0)] : 0, kr = hi ? keff[side_of<DIM>(p, pidx, 0, 1)] : 0;
 #pragma unroll
     for (int t = W - H; t <= W + 3 + H; ++t) {
       const int rel = pos[0] - W + t;
@@ -245,12 +248,12 @@ __device__ __forceinline__ void ab_combine(const StepParams &p, int64_t n, int64
 }
 
 // Update the four points x0..x0+3 of row (y, z) (the forward step; AB: Adams-Bashforth, else forward Euler).
-template <int DIM, int H, class LD, bool AB = false>
+template <int DIM, int H, class LD, bool AB = false, bool OWN_SIDES = false>
 __device__ __forceinline__ void group_update(const StepParams &p, const uint8_t *__restrict__ keff,
                                              const double *__restrict__ un, double *__restrict__ out, int64_t n,
                                              int x0, int y, int z) {
   double r[4], uc[4];
-  group_eval<DIM, H, LD, false>(p, keff, un, n, x0, y, z, r, uc);
+  group_eval<DIM, H, LD, false, OWN_SIDES>(p, keff, un, n, x0, y, z, r, uc);
   const int64_t i0 = (DIM == 3 ? ((int64_t)z * p.n[1] + y) * p.n[0] : 0) + x0;
   if (AB) ab_combine<4>(p, n, i0, uc, r);
   reinterpret_cast<double2 *>(out + i0)[0] = make_double2(r[0], r[1]);
