@@ -81,15 +81,32 @@ __global__ void __launch_bounds__(128) forward_zones_kernel(const StepParams p, 
   // the block launch that follows may start now: its inner groups read only U^n, and it waits for this grid before
   // its edge groups and its delay draws
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  // Each warp holds its boundary's region -- cells b - RR .. b + RR - 1, RR = zr[0] + h -- at levels n .. n+K-1 in
+  // shared memory: U^n is read once, each step's zone is computed from the level before it there, and only levels
+  // before n (the delayed halo levels at the face strips) are read from the ring.  The arithmetic is the step
+  // kernel's: the centre tap, then the taps in offset order, a buffer point's value extrapolated over the delayed
+  // levels w_m(k) in the order m = 0 .. T-1.
+  constexpr int CELLS = 64;  // 2 RR <= 2 (zr[0] + h) <= 54 for h <= 3, K <= 4
+  __shared__ double lev[4][K][CELLS];
   const int64_t n = n_off + (n_base ? *n_base : 0);
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t P = p.pe[0], nbound = p.use_pe[0] ? P : 0;
+  const int nx = p.n[0], RR = p.zr[0] + H;
   for (int64_t b = warp; b < (nbound > 0 ? nbound : 1); b += nwarps) {
     const int64_t sides[2] = {nbound ? 2 * ((b + P - 1) % P) + 1 : 0, nbound ? 2 * b : 1};
+    const int base = (int)(b * p.S[0]) - RR;  // cell of local index 0 (before wrapping)
+    if (nbound)
+      for (int i = lane; i < 2 * RR; i += 32) lev[wb][0][i] = p.ring[(n % p.R) * p.ntot + wrap_coord(base + i, nx)];
+    __syncwarp();
     for (int j = 0; j + 1 < K; ++j) {
       const int64_t st = n + j;  // the step this round computes; it draws the delays of step st + 1
+      const uint8_t *keff = p.keff + (st & 1) * p.nb;
+      // delays of step st seen across this boundary: by the cells left of it (the right side of the PE before) and
+      // by the cells right of it (the left side of the PE after); read before this round's draw of step st + 1
+      const int k_lo = nbound ? keff[sides[0]] : 0, k_hi = nbound ? keff[sides[1]] : 0;
+      __syncwarp();
       if (lane < 2) {
         const int64_t side = sides[lane];
         int raw = 0;
@@ -99,13 +116,33 @@ __global__ void __launch_bounds__(128) forward_zones_kernel(const StepParams p, 
         if (p.log != nullptr && st + 1 < p.log_steps) p.log[(st + 1) * p.nb + side] = (uint8_t)raw;
       }
       if (nbound) {
-        const double *un = p.ring + (st % p.R) * p.ntot;
         double *out = p.ring + ((st + 1) % p.R) * p.ntot;
-        const uint8_t *keff = p.keff + (st & 1) * p.nb;
-        const int r = p.zr[j], ng = r >> 1;
-        for (int t = lane; t < ng; t += 32) {
-          const int x0 = wrap_coord((int)(b * p.S[0]) - r + 4 * t, p.n[0]);
-          group_update<1, H, LdCoherent, false, true>(p, keff, un, out, st, x0, 0, 0);
+        const int r = p.zr[j];
+        for (int i = RR - r + lane; i < RR + r; i += 32) {
+          const bool left = i < RR;
+          double acc = fma(p.s0, lev[wb][j][i], p.zero);
+#pragma unroll
+          for (int t = -H; t <= H; ++t) {
+            if (t == 0) continue;
+            const int ii = i + t;
+            double v = lev[wb][j][ii];
+            const int k = left == (ii < RR) ? 0 : (left ? k_lo : k_hi);  // a tap across the boundary: buffer point
+            if (k > 0) {
+              const int cell = wrap_coord(base + ii, nx);
+              double h = 0.0;
+#pragma unroll
+              for (int m = 0; m < AT_MAX_T; ++m) {
+                if (m >= p.T) break;
+                const int64_t q = st - k - m;  // level read: in shared memory from n on, else in the ring
+                const double u = q >= n ? lev[wb][q - n][ii] : p.ring[(q % p.R) * p.ntot + cell];
+                h = m == 0 ? fma(p.w[k][0], u, p.zero) : fma(p.w[k][m], u, h);
+              }
+              v = h;
+            }
+            acc = fma(p.s[0][t + H], v, acc);
+          }
+          lev[wb][j + 1][i] = acc;
+          out[wrap_coord(base + i, nx)] = acc;
         }
       }
       __syncwarp();
