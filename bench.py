@@ -43,9 +43,9 @@ FP64_FMA_LANES_PER_SM = 2  # FP64 FMA lanes per SM per clock on GB300 (nominal)
 # kernel source; None where no capture of the current source exists.
 MEASURED_TRAFFIC = {
     ("1d_n16m", "forward_group_kernel<1,2,false>"): 136.95e6 + 80.50e6,
-    # blocks of 4 steps: one block launch (137.3 MB read, 82.9 MB written) and one zone launch (4.6 MB read) per
+    # blocks of 4 steps: one block launch (137.4 MB read, 79.2 MB written) and one zone launch (4.6 MB read) per
     # block, per step
-    ("1d_n16m", "blocks of 4"): (137.3e6 + 82.9e6 + 4.6e6) / 4,
+    ("1d_n16m", "blocks of 4"): (137.4e6 + 79.2e6 + 4.6e6) / 4,
     ("1d_n16m_case2", "forward_group_kernel<1,1,false>"): None,
     ("1d_n16m_case3", "forward_group_kernel<1,1,false>"): 135.27e6 + 80.13e6,
     ("1d_n16m_case4", "forward_group_kernel<1,2,true>"): 271.91e6 + 209.17e6,
