@@ -42,19 +42,19 @@ FP64_FMA_LANES_PER_SM = 2  # FP64 FMA lanes per SM per clock on GB300 (nominal)
 # DRAM bytes (read + write) per launch of the step kernel, the mean of two launches of one ncu capture of the current
 # kernel source; None where no capture of the current source exists.
 MEASURED_TRAFFIC = {
-    ("1d_n16m", "forward_group_kernel<1,2,false>"): 136.95e6 + 80.50e6,
+    ("1d_n16m", "forward_group_kernel<1,2,0>"): 136.95e6 + 80.50e6,
     # blocks of 4 steps: one block launch (137.4 MB read, 79.2 MB written) and one zone launch (4.6 MB read) per
     # block, per step
     ("1d_n16m", "blocks of 4"): (137.4e6 + 79.2e6 + 4.6e6) / 4,
-    ("1d_n16m_case2", "forward_group_kernel<1,1,false>"): None,
-    ("1d_n16m_case3", "forward_group_kernel<1,1,false>"): 135.27e6 + 80.13e6,
-    ("1d_n16m_case4", "forward_group_kernel<1,2,true>"): 271.91e6 + 209.17e6,
-    ("1d_n16m_case5", "forward_group_kernel<1,3,true>"): 409.85e6 + 221.76e6,
-    ("1d_n16m_case6", "forward_group_kernel<1,2,true>"): 271.83e6 + 209.14e6,
+    ("1d_n16m_case2", "forward_group_kernel<1,1,0>"): None,
+    ("1d_n16m_case3", "forward_group_kernel<1,1,0>"): 135.27e6 + 80.13e6,
+    ("1d_n16m_case4", "forward_group_kernel<1,2,2>"): None,
+    ("1d_n16m_case5", "forward_group_kernel<1,3,1>"): 409.85e6 + 221.76e6,
+    ("1d_n16m_case6", "forward_group_kernel<1,2,1>"): 271.83e6 + 209.14e6,
     # 3D: captured at 256^3 (the same 64^3 PEs; a 512^3 ring is 5-6 GB) over launches 5 and 6 of a 10-step run,
     # scaled to 512^3 by the 8x points
-    ("3d_512_o2", "forward_group_kernel<3,1,false>"): 8 * (370.01e6 + 116.13e6),
-    ("3d_512_o4", "forward_group_kernel<3,2,false>"): 8 * (475.21e6 + 122.36e6),
+    ("3d_512_o2", "forward_group_kernel<3,1,0>"): 8 * (370.01e6 + 116.13e6),
+    ("3d_512_o4", "forward_group_kernel<3,2,0>"): 8 * (475.21e6 + 122.36e6),
 }
 TRAFFIC_NOTES = {
     "3d_512_o2": "DRAM read + write per launch from ncu at 256^3 in 4^3 PEs of 64^3, scaled by points to 512^3",
@@ -482,7 +482,11 @@ def measure_forward(spec, T, args, local, warmup, steps, world=1, e2e=False, flu
         out["e2e"] = {"value": aggregate_rate(ntot * T, world, e2e_s), "unit": "updates/s",
                       "h2d_bytes_per_step": 8 * ntot, "d2h_bytes_per_step": 8 * ntot + 8 * 9}
 
-    kname = f"forward_group_kernel<{spec['dim']},{spec['order'] // 2},{'true' if time_levels(spec) > 1 else 'false'}>"
+    # the step kernel's first template arguments: dimension, h, and 0 forward Euler / 1 Adams-Bashforth / 2 AB2 in
+    # its steady form (1D, linear)
+    ab = 0 if time_levels(spec) == 1 else (2 if time_levels(spec) == 2 and spec["dim"] == 1 and not spec.get("burgers")
+                                           else 1)
+    kname = f"forward_group_kernel<{spec['dim']},{spec['order'] // 2},{ab}>"
     ops = fp64_ops_per_update(spec)
     bytes_update = bytes_per_update(spec)
     traffic = MEASURED_TRAFFIC.get((workload, kname))

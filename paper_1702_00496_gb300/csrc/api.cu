@@ -204,6 +204,7 @@ static cudaError_t ab_start(at_handle *hd, bool analytic) {
   const StepParams &p = hd->sp;
   if (p.ts <= 1) return cudaSuccess;
   const int ns = p.ts - 1;
+  hd->sp.ab_steady = analytic ? 0 : ns;
   cudaError_t e = cudaSuccess;
   if (analytic) {
     double *tmp = p.ring + p.ntot;
@@ -379,7 +380,15 @@ extern "C" int at_step(at_handle_t *hd, int64_t nsteps) {
   if (hd->sp.log && hd->step + nsteps > hd->log_steps) return fail(AT_ERR_STATE, "at_step: delay log is full");
   if (hd->step + nsteps > 0xFFFFFFFFll) return fail(AT_ERR_STATE, "at_step: step counter exceeds 32 bits");
   cudaError_t e;
-  const int64_t G = graph_steps(hd), chunks = nsteps / G;
+  int64_t s = 0;
+  // the start of a multistep run from a caller's field, where the weights change from step to step, runs in single
+  // launches; the captured graphs hold steps of the steady form
+  for (; s < nsteps && hd->sp.ts > 1 && hd->step < hd->sp.ab_steady; ++s) {
+    if ((e = launch_forward_step(hd->sp, hd->step, nullptr, hd->stream)) != cudaSuccess)
+      return cuda_fail(e, "at_step: launch");
+    hd->step += 1;
+  }
+  const int64_t G = graph_steps(hd), chunks = (nsteps - s) / G;
   if (chunks > 0) {
     if (!hd->exec) {
       int rc = build_graph(hd);
@@ -392,7 +401,7 @@ extern "C" int at_step(at_handle_t *hd, int64_t nsteps) {
       hd->step += G;
     }
   }
-  int64_t s = chunks * G;
+  s += chunks * G;
   const int64_t K = hd->sp.fuse_k;
   for (; K > 1 && s + K <= nsteps; s += K) {
     if ((e = launch_forward_block(hd->sp, hd->step, nullptr, hd->stream)) != cudaSuccess)

@@ -33,7 +33,7 @@ using namespace atfd;
 // Grouped kernel: a thread updates four consecutive x points per iteration (grid-stride); every thread
 // also draws the delays of one slice of the PE sides for step n+1 into the other half of the double-buffered
 // delay array, so the next launch finds them ready.
-template <int DIM, int H, bool AB, int KIND>
+template <int DIM, int H, int AB, int KIND>
 __global__ void __launch_bounds__(512) forward_group_kernel(const StepParams p, const int64_t n_off,
                                                             const int64_t *n_base) {
   const int64_t n = n_off + (n_base ? *n_base : 0);
@@ -299,12 +299,15 @@ bool grouped_shape(const StepParams &p, const void *base) {
          (p.frhs == nullptr || (reinterpret_cast<uintptr_t>(p.frhs) % 16) == 0);
 }
 
-template <int DIM, int H, bool AB>
+// AB: 0 forward Euler, 1 Adams-Bashforth, 2 AB2 with both levels stored (the 1D linear grouped step only; Burgers'
+// step, 3D and the per-point fallback take the general form: Burgers' AB2 step measured 462 against 406 us in it).
+template <int DIM, int H, int AB>
 void launch_typed(const StepParams &p, bool grouped, int blocks, int threads, int64_t n, const int64_t *n_base,
                   cudaStream_t st) {
+  constexpr int ABG = AB ? 1 : 0;
   if (DIM == 1 && p.burgers) {
-    if (grouped) forward_group_kernel<1, H, AB, 1><<<blocks, threads, 0, st>>>(p, n, n_base);
-    else forward_point_kernel<1, H, AB, 1><<<blocks, threads, 0, st>>>(p, n, n_base);
+    if (grouped) forward_group_kernel<1, H, ABG, 1><<<blocks, threads, 0, st>>>(p, n, n_base);
+    else forward_point_kernel<1, H, ABG != 0, 1><<<blocks, threads, 0, st>>>(p, n, n_base);
     return;
   }
   if constexpr (H == 1 && !AB) {
@@ -314,11 +317,11 @@ void launch_typed(const StepParams &p, bool grouped, int blocks, int threads, in
       return;
     }
   }
-  if (grouped) forward_group_kernel<DIM, H, AB, 0><<<blocks, threads, 0, st>>>(p, n, n_base);
-  else forward_point_kernel<DIM, H, AB, 0><<<blocks, threads, 0, st>>>(p, n, n_base);
+  if (grouped) forward_group_kernel<DIM, H, DIM == 1 ? AB : ABG, 0><<<blocks, threads, 0, st>>>(p, n, n_base);
+  else forward_point_kernel<DIM, H, AB != 0, 0><<<blocks, threads, 0, st>>>(p, n, n_base);
 }
 
-template <int DIM, bool AB>
+template <int DIM, int AB>
 void launch_h(const StepParams &p, bool grouped, int blocks, int threads, int64_t n, const int64_t *n_base,
               cudaStream_t st) {
   if (p.h == 1) launch_typed<DIM, 1, AB>(p, grouped, blocks, threads, n, n_base, st);
@@ -341,13 +344,15 @@ cudaError_t launch_forward_step(const StepParams &p, int64_t n, const int64_t *n
   const int64_t work = grouped ? p.ntot / 4 : p.ntot;
   const int64_t b = (work + threads - 1) / threads;
   const int blocks = (int)(b < max_blocks ? b : max_blocks);
-  const bool ab = p.ts > 1;
+  // a launch inside a captured graph (n_base set) runs only at steps at or after ab_steady
+  const bool ab = p.ts > 1, steady = p.ts == 2 && (n_base != nullptr || n >= p.ab_steady);
   if (p.dim == 1) {
-    if (ab) launch_h<1, true>(p, grouped, blocks, threads, n, n_base, st);
-    else launch_h<1, false>(p, grouped, blocks, threads, n, n_base, st);
+    if (steady) launch_h<1, 2>(p, grouped, blocks, threads, n, n_base, st);
+    else if (ab) launch_h<1, 1>(p, grouped, blocks, threads, n, n_base, st);
+    else launch_h<1, 0>(p, grouped, blocks, threads, n, n_base, st);
   } else {
-    if (ab) launch_h<3, true>(p, grouped, blocks, threads, n, n_base, st);
-    else launch_h<3, false>(p, grouped, blocks, threads, n, n_base, st);
+    if (ab) launch_h<3, 1>(p, grouped, blocks, threads, n, n_base, st);
+    else launch_h<3, 0>(p, grouped, blocks, threads, n, n_base, st);
   }
   return cudaGetLastError();
 }

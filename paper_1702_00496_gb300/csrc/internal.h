@@ -78,6 +78,10 @@ struct StepParams {
   int32_t fuse_k, fe;
   int32_t zr[AT_MAX_FUSE];
   double ck[2 * AT_MAX_H * AT_MAX_FUSE + 1];
+  // Host: the first step whose Adams-Bashforth combination has all ts levels stored (0 after the analytic
+  // pre-history, ts-1 from a caller's field); from it on the weights are beta[ts-1] at every step, and AB2 steps
+  // take the combination's steady form.
+  int64_t ab_steady;
 };
 
 // The modes of one axis at one time t, prepared on the host for the recurrences over k: sorted by wavenumber,

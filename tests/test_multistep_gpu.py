@@ -128,6 +128,26 @@ def test_graph_chunks_and_single_launches_agree():
     b.close()
 
 
+@pytest.mark.parametrize("tsteps", [2, 3])
+def test_steady_form_is_bitwise_the_general_combination(tsteps):
+    """Once both levels are stored, a single problem's AB2 steps take the combination's steady form (the weights
+    read as kernel parameters); the ensemble engine takes the general form, which looks the number of stored
+    levels up at every step.  The operations are the same, so the bits are: members against single problems, 130
+    steps (graphs and single launches); AB3 takes the general form on both sides."""
+    from paper_1702_00496_gb300 import Ensemble
+    specs = [W.wl_1d(n, n // 16, order, L, 0, 950 + r, range(1, 5), r_alpha=0.02, tsteps=tsteps)[0]
+             for r, (n, order, L) in enumerate([(256, 4, 3), (1024, 6, 4), (512, 2, 3)])]
+    ens = Ensemble(specs, 130)
+    ens.run()
+    for r, spec in enumerate(specs):
+        s = _solver(spec)
+        s.step(130)
+        s.sync()
+        assert torch.equal(ens.field(r), s.field().reshape(-1)), r
+        s.close()
+    ens.close()
+
+
 def test_launch_shapes_do_not_change_multistep_results():
     from paper_1702_00496_gb300 import at_set_launch
     for spec in (W.wl_1d(4096, 16, 6, 4, 0, 93, range(1, 6), r_alpha=0.01, tsteps=3)[0],
