@@ -48,7 +48,7 @@ MEASURED_TRAFFIC = {
     ("1d_n16m", "blocks of 4"): (137.4e6 + 79.2e6 + 4.6e6) / 4,
     ("1d_n16m_case2", "forward_group_kernel<1,1,0>"): None,
     ("1d_n16m_case3", "forward_group_kernel<1,1,0>"): 135.27e6 + 80.13e6,
-    ("1d_n16m_case4", "forward_group_kernel<1,2,2>"): None,
+    ("1d_n16m_case4", "forward_group_kernel<1,2,2>"): 271.86e6 + 208.75e6,
     ("1d_n16m_case5", "forward_group_kernel<1,3,1>"): 409.85e6 + 221.76e6,
     ("1d_n16m_case6", "forward_group_kernel<1,2,1>"): 271.83e6 + 209.14e6,
     # 3D: captured at 256^3 (the same 64^3 PEs; a 512^3 ring is 5-6 GB) over launches 5 and 6 of a 10-step run,

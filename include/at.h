@@ -159,6 +159,9 @@ int at_init(const at_config_t *cfg, double *ring_dev, int64_t ring_len, uint8_t 
  * time; the delays, the delay log and the levels a later step reads at delayed levels are those of single steps.
  * Blocks start at the first step of each call (and of each captured graph inside it, 48 steps for K = 4), so the
  * same steps split into other calls give results equal up to rounding, not bit for bit.
+ * Adams-Bashforth runs from a caller's field take their first ts-1 steps (fewer stored levels, other weights) as
+ * single launches; every later step -- every step after the analytic pre-history -- has all ts levels (with ts = 2
+ * its weights are then read as kernel parameters: the same operations, the same bits).
  * Enqueued on the handle's stream; returns without waiting.  Errors: AT_ERR_ARG, AT_ERR_STATE (the
  * delay log would overflow), AT_ERR_CUDA. */
 int at_step(at_handle_t *hd, int64_t nsteps);
