@@ -101,10 +101,10 @@ __global__ void __launch_bounds__(128) forward_zones_kernel(const StepParams p, 
       for (int i = lane; i < 2 * RR; i += 32) lev[wb][0][i] = p.ring[(n % p.R) * p.ntot + wrap_coord(base + i, nx)];
     __syncwarp();
     for (int j = 0; j + 1 < K; ++j) {
-      const int64_t st = n + j;  // the step this round computes; it draws the delays of step st + 1
+      const int64_t st = n + j;  // the step this pass computes; it draws the delays of step st + 1
       const uint8_t *keff = p.keff + (st & 1) * p.nb;
       // delays of step st seen across this boundary: by the cells left of it (the right side of the PE before) and
-      // by the cells right of it (the left side of the PE after); read before this round's draw of step st + 1
+      // by the cells right of it (the left side of the PE after); read before this pass's draw of step st + 1
       const int k_lo = nbound ? keff[sides[0]] : 0, k_hi = nbound ? keff[sides[1]] : 0;
       __syncwarp();
       if (lane < 2) {
