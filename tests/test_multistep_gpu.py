@@ -114,10 +114,12 @@ def test_reset_restores_the_analytic_prehistory():
     s.close()
 
 
-def test_graph_chunks_and_single_launches_agree():
+@pytest.mark.parametrize("tsteps,order", [(3, 6), (2, 4)])
+def test_graph_chunks_and_single_launches_agree(tsteps, order):
     """300 steps in one call (six captured 50-step graphs) and in calls of 7 and 293 (single launches, then
-    graphs starting mid-history) give the same bits: the integrator reads its history level from the device."""
-    spec, _ = W.wl_1d(8192, 32, 6, 4, 0, 92, range(1, 6), r_alpha=0.01, tsteps=3)
+    graphs starting mid-history) give the same bits: the integrator reads its history level from the device (AB3),
+    or every step has both levels and takes the steady form in graphs and single launches alike (AB2)."""
+    spec, _ = W.wl_1d(8192, 32, order, 4, 0, 92, range(1, 6), r_alpha=0.01, tsteps=tsteps)
     a = _solver(spec)
     a.step(300)
     b = _solver(spec)
@@ -126,6 +128,29 @@ def test_graph_chunks_and_single_launches_agree():
     assert torch.equal(a.field(), b.field())
     a.close()
     b.close()
+
+
+def test_ab2_from_a_callers_field_across_call_splits():
+    """From a caller's field the first AB2 step has one stored level (the general form, a single launch); the rest
+    take the steady form.  One call of 300 steps against calls of 1, 1, 49 and 249 (the start-up step alone, then
+    graphs from mid-run): the same bits; and against the oracle."""
+    spec, _ = W.wl_1d(8192, 32, 4, 3, 0, 95, range(1, 6), r_alpha=0.02, tsteps=2)
+    rng = np.random.default_rng(6)
+    u0 = oracle.initial(oracle.Config(spec)) + 0.01 * rng.standard_normal(8192)
+    u0_dev = torch.as_tensor(u0, device="cuda")
+    a = _solver(spec)
+    a.reset(u0_dev)
+    a.step(300)
+    b = _solver(spec)
+    b.reset(u0_dev)
+    for n in (1, 1, 49, 249):
+        b.step(n)
+    assert torch.equal(a.field(), b.field())
+    u = a.field().cpu().numpy().copy()
+    a.close()
+    b.close()
+    ref, _, _ = oracle.run(oracle.Config(spec), 300, threads=THREADS, u0=u0, want_log=False)
+    assert np.linalg.norm(u - ref) / np.linalg.norm(ref) <= TOL
 
 
 @pytest.mark.parametrize("tsteps", [2, 3])
@@ -151,6 +176,7 @@ def test_steady_form_is_bitwise_the_general_combination(tsteps):
 def test_launch_shapes_do_not_change_multistep_results():
     from paper_1702_00496_gb300 import at_set_launch
     for spec in (W.wl_1d(4096, 16, 6, 4, 0, 93, range(1, 6), r_alpha=0.01, tsteps=3)[0],
+                 W.wl_1d(4096, 16, 4, 4, 0, 96, range(1, 6), r_alpha=0.02, tsteps=2)[0],
                  W.wl_3d([32, 24, 16], [4, 3, 2], 4, 3, 0, 94, c=(0.3, 0.2, 0.1), tsteps=2)[0]):
         ref = None
         for threads, bps in ((256, 32), (128, 4), (512, 16)):
